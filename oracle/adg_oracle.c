@@ -1,0 +1,762 @@
+/*
+ * adg_oracle.c -- plain FP64 CPU ADER-DG.  TEST INFRASTRUCTURE ONLY: the tests,
+ * the smoke check and the benchmark's CPU-baseline leg are its only users; the
+ * CUDA library never links, loads or calls it, and it shares no code with it.
+ *
+ * Everything is written in the order and notation of arXiv 2504.06889, Sec. 2:
+ * no blocking, fusion or reordering beyond what the equations state.  Loops are
+ * over (cell, time node k, variable v, spatial node i) in the obvious way.
+ *
+ * Readings where the paper is silent (listed with the design notes):
+ *   - reference element [0,1]^d in space and [0,1] in time, GL support points;
+ *   - Picard starts from q = Q^n constant in time and runs a fixed number of
+ *     sweeps (default N+1);
+ *   - the Riemann problem is solved once per face on the time-averaged traces;
+ *     the Rusanov speed is one scalar per face: max over face nodes and sides;
+ *   - dt^n is computed from Q^n with eq. (CFL_condition), C_CFL given, d kept.
+ */
+#include "adg_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* 1D tables.  Sec. 2, eq. (piecewise_solution): Lagrange polynomials with    */
+/* Gauss-Legendre support points.  GL nodes by Newton on P_n (long double).   */
+/* ------------------------------------------------------------------------ */
+
+static void legendre_and_deriv(int n, long double x, long double* P, long double* dP) {
+  long double p0 = 1.0L, p1 = x;
+  if (n == 0) {
+    *P = 1.0L;
+    *dP = 0.0L;
+    return;
+  }
+  for (int k = 1; k < n; ++k) {
+    long double p2 = ((2.0L * k + 1.0L) * x * p1 - (long double)k * p0) / (k + 1.0L);
+    p0 = p1;
+    p1 = p2;
+  }
+  *P = p1;                                  /* P_n   */
+  *dP = n * (x * p1 - p0) / (x * x - 1.0L); /* P_n'  */
+}
+
+double or_lagrange(int n, const double* xi, int j, double x) {
+  double r = 1.0;
+  for (int m = 0; m < n; ++m)
+    if (m != j) r *= (x - xi[m]) / (xi[j] - xi[m]);
+  return r;
+}
+
+/* psi_j'(x) by the product rule: sum over l != j of 1/(xi_j-xi_l) * prod_{m != j,l} */
+static long double lagrange_deriv(int n, const long double* xi, int j, long double x) {
+  long double s = 0.0L;
+  for (int l = 0; l < n; ++l) {
+    if (l == j) continue;
+    long double t = 1.0L / (xi[j] - xi[l]);
+    for (int m = 0; m < n; ++m)
+      if (m != j && m != l) t *= (x - xi[m]) / (xi[j] - xi[m]);
+    s += t;
+  }
+  return s;
+}
+
+static long double lagrange_ld(int n, const long double* xi, int j, long double x) {
+  long double r = 1.0L;
+  for (int m = 0; m < n; ++m)
+    if (m != j) r *= (x - xi[m]) / (xi[j] - xi[m]);
+  return r;
+}
+
+void or_tables(int n, double* xi, double* w, double* D, double* psi0, double* psi1, double* K1,
+               double* K1inv) {
+  long double X[OR_MAXN], W[OR_MAXN];
+  const long double pi = 3.141592653589793238462643383279502884L;
+  for (int j = 0; j < n; ++j) {
+    /* standard initial guess, then Newton on [-1,1] */
+    long double x = cosl(pi * (j + 0.75L) / (n + 0.5L));
+    for (int it = 0; it < 100; ++it) {
+      long double P, dP;
+      legendre_and_deriv(n, x, &P, &dP);
+      long double dx = P / dP;
+      x -= dx;
+      if (fabsl(dx) < 1e-19L) break;
+    }
+    long double P, dP;
+    legendre_and_deriv(n, x, &P, &dP);
+    long double wstd = 2.0L / ((1.0L - x * x) * dP * dP);
+    /* map [-1,1] -> [0,1]; cos ordering is descending, store ascending */
+    X[n - 1 - j] = (x + 1.0L) / 2.0L;
+    W[n - 1 - j] = wstd / 2.0L;
+  }
+  for (int j = 0; j < n; ++j) {
+    xi[j] = (double)X[j];
+    w[j] = (double)W[j];
+    psi0[j] = (double)lagrange_ld(n, X, j, 0.0L);
+    psi1[j] = (double)lagrange_ld(n, X, j, 1.0L);
+  }
+  /* D[a][b] = psi_b'(xi_a) */
+  long double Dl[OR_MAXN][OR_MAXN];
+  for (int a = 0; a < n; ++a)
+    for (int b = 0; b < n; ++b) {
+      Dl[a][b] = lagrange_deriv(n, X, b, X[a]);
+      D[a * n + b] = (double)Dl[a][b];
+    }
+  /* Eq. (Picard), time part divided by the spatial mass:
+   *   K1[k][l] = psi_k(1) psi_l(1) - int_0^1 psi_k'(tau) psi_l(tau) dtau
+   *            = psi_k(1) psi_l(1) - w_l psi_k'(xi_l)        (GL exact for degree 2N-1) */
+  long double A[OR_MAXN][2 * OR_MAXN];
+  for (int k = 0; k < n; ++k)
+    for (int l = 0; l < n; ++l) {
+      long double v = lagrange_ld(n, X, k, 1.0L) * lagrange_ld(n, X, l, 1.0L) - W[l] * Dl[l][k];
+      K1[k * n + l] = (double)v;
+      A[k][l] = v;
+      A[k][n + l] = (k == l) ? 1.0L : 0.0L;
+    }
+  /* Gauss-Jordan with partial pivoting */
+  for (int c = 0; c < n; ++c) {
+    int p = c;
+    for (int r = c + 1; r < n; ++r)
+      if (fabsl(A[r][c]) > fabsl(A[p][c])) p = r;
+    if (p != c)
+      for (int j = 0; j < 2 * n; ++j) {
+        long double t = A[c][j];
+        A[c][j] = A[p][j];
+        A[p][j] = t;
+      }
+    long double piv = A[c][c];
+    for (int j = 0; j < 2 * n; ++j) A[c][j] /= piv;
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      long double f = A[r][c];
+      if (f != 0.0L)
+        for (int j = 0; j < 2 * n; ++j) A[r][j] -= f * A[c][j];
+    }
+  }
+  for (int k = 0; k < n; ++k)
+    for (int l = 0; l < n; ++l) K1inv[k * n + l] = (double)A[k][n + l];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Mesh setup                                                                 */
+/* ------------------------------------------------------------------------ */
+
+int or_nvar(int pde, int dim) {
+  switch (pde) {
+    case OR_ACOUSTIC: return 1 + dim;          /* p, v_1..v_d */
+    case OR_ELASTIC: return dim == 3 ? 9 : 5;  /* stresses (Voigt), velocities */
+    case OR_EULER: return 2 + dim;             /* rho, rho v_1..v_d, E */
+    case OR_SWE: return 3;                     /* h, hu, hv (flat bathymetry) */
+  }
+  return -1;
+}
+
+int or_setup(or_mesh* M, int dim, int N, const int* m, const double* lo, const double* hi, int pde,
+             const double* params, int nparams, double cfl, int picard_iters) {
+  memset(M, 0, sizeof(*M));
+  if (dim < 2 || dim > 3 || N < 0 || N + 1 > OR_MAXN) return -1;
+  if (pde == OR_SWE && dim != 2) return -1;
+  M->dim = dim;
+  M->N = N;
+  M->n = N + 1;
+  M->pde = pde;
+  M->nvar = or_nvar(pde, dim);
+  for (int d = 0; d < 3; ++d) {
+    M->m[d] = d < dim ? m[d] : 1;
+    M->lo[d] = d < dim ? lo[d] : 0.0;
+    M->h[d] = d < dim ? (hi[d] - lo[d]) / m[d] : 1.0;
+  }
+  for (int j = 0; j < nparams && j < 8; ++j) M->pp[j] = params[j];
+  M->cfl = cfl;
+  M->picard_iters = picard_iters > 0 ? picard_iters : N + 1;
+  M->use_ck = 0;
+  M->cell_c = NULL;
+  /* or_tables stores n x n matrices with row stride n; the mesh keeps stride OR_MAXN */
+  {
+    double D[OR_MAXN * OR_MAXN], K1[OR_MAXN * OR_MAXN], K1i[OR_MAXN * OR_MAXN];
+    or_tables(M->n, M->xi, M->w, D, M->psi0, M->psi1, K1, K1i);
+    int n = M->n;
+    for (int a = 0; a < n; ++a)
+      for (int b = 0; b < n; ++b) {
+        M->D[a][b] = D[a * n + b];
+        M->K1[a][b] = K1[a * n + b];
+        M->K1inv[a][b] = K1i[a * n + b];
+      }
+  }
+  return 0;
+}
+
+void or_set_cell_c(or_mesh* M, const double* cell_c) { M->cell_c = cell_c; }
+
+/* ------------------------------------------------------------------------ */
+/* PDE fluxes, Sec. 4.  F_dir(q) and the spectral radius of dF_dir/dq.        */
+/* ------------------------------------------------------------------------ */
+
+void or_flux(const or_mesh* M, int cell, const double* q, int dir, double* F) {
+  const int V = M->nvar, d = M->dim;
+  for (int v = 0; v < V; ++v) F[v] = 0.0;
+  if (M->pde == OR_ACOUSTIC) {
+    /* eq. (acoustic): p_t + K div v = 0, rho v_t + grad p = 0;  F_dir = A_dir Q */
+    double rho = M->pp[0], K = M->pp[1];
+    if (M->cell_c) K = rho * M->cell_c[cell] * M->cell_c[cell];
+    F[0] = K * q[1 + dir];
+    F[1 + dir] = q[0] / rho;
+  } else if (M->pde == OR_ELASTIC) {
+    /* eq. (lin_elastic) with the matrices of eq. (elastic_matrices); the 3D
+     * velocity-stress system is the same construction in three directions. */
+    double rho = M->pp[0], cp = M->pp[1], cs = M->pp[2];
+    double mu = rho * cs * cs, lam = rho * cp * cp - 2.0 * mu;
+    if (d == 2) {
+      /* Q = (sxx, syy, sxy, vx, vy) */
+      double sxx = q[0], syy = q[1], sxy = q[2], vx = q[3], vy = q[4];
+      if (dir == 0) {
+        F[0] = -(lam + 2.0 * mu) * vx;
+        F[1] = -lam * vx;
+        F[2] = -mu * vy;
+        F[3] = -sxx / rho;
+        F[4] = -sxy / rho;
+      } else {
+        F[0] = -lam * vy;
+        F[1] = -(lam + 2.0 * mu) * vy;
+        F[2] = -mu * vx;
+        F[3] = -sxy / rho;
+        F[4] = -syy / rho;
+      }
+    } else {
+      /* Q = (sxx, syy, szz, sxy, syz, sxz, vx, vy, vz) */
+      double s[3][3];
+      s[0][0] = q[0];
+      s[1][1] = q[1];
+      s[2][2] = q[2];
+      s[0][1] = s[1][0] = q[3];
+      s[1][2] = s[2][1] = q[4];
+      s[0][2] = s[2][0] = q[5];
+      const double* vel = q + 6;
+      /* sigma_t = lam (div v) I + mu (grad v + grad v^T); flux along dir carries
+       * -(lam v_dir I + mu (e_dir v^T + v e_dir^T)) */
+      double T[3][3];
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+          double e_a = (a == dir) ? 1.0 : 0.0, e_b = (b == dir) ? 1.0 : 0.0;
+          T[a][b] = -((a == b ? lam * vel[dir] : 0.0) + mu * (e_a * vel[b] + vel[a] * e_b));
+        }
+      F[0] = T[0][0];
+      F[1] = T[1][1];
+      F[2] = T[2][2];
+      F[3] = T[0][1];
+      F[4] = T[1][2];
+      F[5] = T[0][2];
+      /* rho v_t = div sigma: flux along dir is -sigma[:,dir]/rho */
+      for (int a = 0; a < 3; ++a) F[6 + a] = -s[a][dir] / rho;
+    }
+  } else if (M->pde == OR_EULER) {
+    /* eq. (euler_eq): Q = (rho, rho v, E), p = (gamma-1)(E - rho |v|^2 / 2),
+     * F_dir = (rho v_dir, rho v v_dir + p e_dir, v_dir (E + p)) */
+    double gamma = M->pp[0];
+    double rho = q[0], E = q[1 + d];
+    double vel[3] = {0, 0, 0}, v2 = 0.0;
+    for (int a = 0; a < d; ++a) {
+      vel[a] = q[1 + a] / rho;
+      v2 += vel[a] * vel[a];
+    }
+    double p = (gamma - 1.0) * (E - 0.5 * rho * v2);
+    F[0] = q[1 + dir];
+    for (int a = 0; a < d; ++a) F[1 + a] = q[1 + a] * vel[dir] + (a == dir ? p : 0.0);
+    F[1 + d] = vel[dir] * (E + p);
+  } else if (M->pde == OR_SWE) {
+    /* Sec. 4.4 with flat bathymetry: the hydrostatic non-conservative term
+     * g h grad(b + h) reduces to grad(g h^2 / 2), so F_dir = (h v_dir,
+     * h v v_dir + g h^2/2 e_dir) */
+    double g = M->pp[0];
+    double h = q[0];
+    double vel[2] = {q[1] / h, q[2] / h};
+    F[0] = q[1 + dir];
+    for (int a = 0; a < 2; ++a) F[1 + a] = q[1 + a] * vel[dir] + (a == dir ? 0.5 * g * h * h : 0.0);
+  }
+}
+
+double or_speed(const or_mesh* M, int cell, const double* q, int dir) {
+  const int d = M->dim;
+  if (M->pde == OR_ACOUSTIC) {
+    double rho = M->pp[0], K = M->pp[1];
+    if (M->cell_c) return fabs(M->cell_c[cell]);
+    return sqrt(K / rho);
+  }
+  if (M->pde == OR_ELASTIC) {
+    return fabs(M->pp[1]); /* c_p is the largest elastic wave speed */
+  }
+  if (M->pde == OR_EULER) {
+    double gamma = M->pp[0];
+    double rho = q[0], E = q[1 + d], v2 = 0.0;
+    for (int a = 0; a < d; ++a) v2 += (q[1 + a] / rho) * (q[1 + a] / rho);
+    double p = (gamma - 1.0) * (E - 0.5 * rho * v2);
+    return fabs(q[1 + dir] / rho) + sqrt(gamma * p / rho);
+  }
+  if (M->pde == OR_SWE) {
+    double g = M->pp[0];
+    return fabs(q[1 + dir] / q[0]) + sqrt(g * q[0]);
+  }
+  return 0.0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Exact solutions / initial data (Sec. 4 scenarios and the synthetic ones)  */
+/* ------------------------------------------------------------------------ */
+
+void or_exact(const or_mesh* M, int scen, const double* sp, int nsp, const double* x, double t,
+              double* Q) {
+  const int V = M->nvar, d = M->dim;
+  (void)nsp;
+  for (int v = 0; v < V; ++v) Q[v] = 0.0;
+  if (scen == OR_SC_PLANAR) {
+    /* sp = [Q0[V], nw, {amp, kx, ky, kz, omega, r[V]} x nw];
+     * Q = Q0 + sum amp sin(k.x - omega t) r  (planar wave, Sec. 4.2.1) */
+    for (int v = 0; v < V; ++v) Q[v] = sp[v];
+    int nw = (int)sp[V];
+    const double* p = sp + V + 1;
+    for (int j = 0; j < nw; ++j, p += 5 + V) {
+      double kx = 0.0;
+      for (int a = 0; a < d; ++a) kx += p[1 + a] * x[a];
+      double s = p[0] * sin(kx - p[4] * t);
+      for (int v = 0; v < V; ++v) Q[v] += s * p[5 + v];
+    }
+  } else if (scen == OR_SC_EULER_WAVE) {
+    /* sp = [rho0, A, k[3], u[3], p0]: rho = rho0 + A sin(k.(x - u t)), constant u, p */
+    double gamma = M->pp[0];
+    double ph = 0.0, u2 = 0.0;
+    for (int a = 0; a < d; ++a) {
+      ph += sp[2 + a] * (x[a] - sp[5 + a] * t);
+      u2 += sp[5 + a] * sp[5 + a];
+    }
+    double rho = sp[0] + sp[1] * sin(ph);
+    Q[0] = rho;
+    for (int a = 0; a < d; ++a) Q[1 + a] = rho * sp[5 + a];
+    Q[1 + d] = sp[8] / (gamma - 1.0) + 0.5 * rho * u2;
+  } else if (scen == OR_SC_SWE_MODES) {
+    /* sp = [h0, a0, kx0, ky0, nm, {a, kx, ky, phi} x nm], at rest (t ignored:
+     * this scenario has no closed form for t > 0) */
+    double h = sp[0] + sp[1] * sin(sp[2] * x[0]) * sin(sp[3] * x[1]);
+    int nm = (int)sp[4];
+    const double* p = sp + 5;
+    for (int j = 0; j < nm; ++j, p += 4) h += p[0] * sin(p[1] * x[0] + p[2] * x[1] + p[3]);
+    Q[0] = h;
+  } else if (scen == OR_SC_GAUSS_PULSE) {
+    /* sp = [x0[3], sigma, amp]: p = amp exp(-|x - x0|^2 / (2 sigma^2)), periodic
+     * distance on the mesh box, v = 0 (t ignored) */
+    double r2 = 0.0;
+    for (int a = 0; a < d; ++a) {
+      double L = M->h[a] * M->m[a];
+      double dx = x[a] - sp[a];
+      dx -= L * floor(dx / L + 0.5);
+      r2 += dx * dx;
+    }
+    Q[0] = sp[4] * exp(-r2 / (2.0 * sp[3] * sp[3]));
+  }
+}
+
+static void node_coords(const or_mesh* M, int c, int i, double* x) {
+  int cc[3] = {c % M->m[0], (c / M->m[0]) % M->m[1], c / (M->m[0] * M->m[1])};
+  int ii[3] = {i % M->n, (i / M->n) % M->n, i / (M->n * M->n)};
+  for (int a = 0; a < 3; ++a) x[a] = a < M->dim ? M->lo[a] + (cc[a] + M->xi[ii[a]]) * M->h[a] : 0.0;
+}
+
+static int ipow(int b, int e) {
+  int r = 1;
+  while (e-- > 0) r *= b;
+  return r;
+}
+
+static int ncells(const or_mesh* M) { return M->m[0] * M->m[1] * M->m[2]; }
+
+/* Sec. 4.5: Q_h^* interpolates the exact solution at the GL nodes */
+void or_interpolate(const or_mesh* M, int scen, const double* sp, int nsp, double t, double* Q) {
+  const int V = M->nvar, NS = ipow(M->n, M->dim), C = ncells(M);
+#pragma omp parallel for schedule(static)
+  for (int c = 0; c < C; ++c)
+    for (int i = 0; i < NS; ++i) {
+      double x[3], q[OR_MAXV];
+      node_coords(M, c, i, x);
+      or_exact(M, scen, sp, nsp, x, t, q);
+      for (int v = 0; v < V; ++v) Q[((size_t)c * V + v) * NS + i] = q[v];
+    }
+}
+
+static double node_weight(const or_mesh* M, int i) {
+  double W = 1.0;
+  int r = i;
+  for (int a = 0; a < M->dim; ++a) {
+    W *= M->w[r % M->n];
+    r /= M->n;
+  }
+  return W;
+}
+
+/* eq. (L2gauss): sqrt(sum_c sum_i sum_v V_c w_i (Q*_v - Q_h,v)^2), per variable
+ * in out[0..V-1] and over all variables in out[V]. */
+void or_l2_error(const or_mesh* M, const double* Q, int scen, const double* sp, int nsp, double t,
+                 double* out) {
+  const int V = M->nvar, NS = ipow(M->n, M->dim), C = ncells(M);
+  double Vc = 1.0;
+  for (int a = 0; a < M->dim; ++a) Vc *= M->h[a];
+  double acc[OR_MAXV] = {0};
+  for (int c = 0; c < C; ++c)
+    for (int i = 0; i < NS; ++i) {
+      double x[3], q[OR_MAXV];
+      node_coords(M, c, i, x);
+      or_exact(M, scen, sp, nsp, x, t, q);
+      double W = node_weight(M, i);
+      for (int v = 0; v < V; ++v) {
+        double e = q[v] - Q[((size_t)c * V + v) * NS + i];
+        acc[v] += Vc * W * e * e;
+      }
+    }
+  double tot = 0.0;
+  for (int v = 0; v < V; ++v) {
+    out[v] = sqrt(acc[v]);
+    tot += acc[v];
+  }
+  out[V] = sqrt(tot);
+}
+
+/* the same norm between two discrete states */
+void or_l2_diff(const or_mesh* M, const double* Qa, const double* Qb, double* out) {
+  const int V = M->nvar, NS = ipow(M->n, M->dim), C = ncells(M);
+  double Vc = 1.0;
+  for (int a = 0; a < M->dim; ++a) Vc *= M->h[a];
+  double acc[OR_MAXV] = {0};
+  for (int c = 0; c < C; ++c)
+    for (int i = 0; i < NS; ++i) {
+      double W = node_weight(M, i);
+      for (int v = 0; v < V; ++v) {
+        size_t o = ((size_t)c * V + v) * NS + i;
+        double e = Qa[o] - Qb[o];
+        acc[v] += Vc * W * e * e;
+      }
+    }
+  double tot = 0.0;
+  for (int v = 0; v < V; ++v) {
+    out[v] = sqrt(acc[v]);
+    tot += acc[v];
+  }
+  out[V] = sqrt(tot);
+}
+
+/* integral of each variable over the domain (GL quadrature, exact for Q_h) */
+void or_totals(const or_mesh* M, const double* Q, double* tot) {
+  const int V = M->nvar, NS = ipow(M->n, M->dim), C = ncells(M);
+  double Vc = 1.0;
+  for (int a = 0; a < M->dim; ++a) Vc *= M->h[a];
+  for (int v = 0; v < V; ++v) tot[v] = 0.0;
+  for (int c = 0; c < C; ++c)
+    for (int v = 0; v < V; ++v)
+      for (int i = 0; i < NS; ++i) tot[v] += Vc * node_weight(M, i) * Q[((size_t)c * V + v) * NS + i];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Predictor, Sec. 2.1.  Eq. (Picard) divided by the spatial mass h^d prod w: */
+/*   sum_l K1[k][l] q_{l,i} + dt w_k R_{k,i} = psi_k(0) Q_i,                  */
+/*   R_{k,i} = sum_dir (1/h_dir) sum_a D[i_dir][a] F_dir(q_{k, i[dir<-a]}).    */
+/* Picard: q^(r) = K1^{-1} (psi(0) Q - dt w o R(q^(r-1))), q^(0) = Q.          */
+/* ------------------------------------------------------------------------ */
+
+static int node_dir_index(const or_mesh* M, int i, int dir) { return (i / ipow(M->n, dir)) % M->n; }
+
+static int node_with(const or_mesh* M, int i, int dir, int a) {
+  int s = ipow(M->n, dir);
+  return i - node_dir_index(M, i, dir) * s + a * s;
+}
+
+/* R[(k*V+v)*NS+i] for the space-time field q[(k*V+v)*NS+i] */
+static void space_derivative_of_flux(const or_mesh* M, int cell, const double* q, int nt,
+                                     double* R) {
+  const int n = M->n, V = M->nvar, d = M->dim, NS = ipow(n, d);
+  double* F = (double*)malloc(sizeof(double) * (size_t)nt * d * V * NS);
+  for (int k = 0; k < nt; ++k)
+    for (int i = 0; i < NS; ++i) {
+      double qv[OR_MAXV], Fv[OR_MAXV];
+      for (int v = 0; v < V; ++v) qv[v] = q[(k * V + v) * NS + i];
+      for (int dir = 0; dir < d; ++dir) {
+        or_flux(M, cell, qv, dir, Fv);
+        for (int v = 0; v < V; ++v) F[((k * d + dir) * V + v) * NS + i] = Fv[v];
+      }
+    }
+  (void)n;
+  for (int k = 0; k < nt; ++k)
+    for (int v = 0; v < V; ++v)
+      for (int i = 0; i < NS; ++i) {
+        double r = 0.0;
+        for (int dir = 0; dir < d; ++dir) {
+          double s = 0.0;
+          int idir = node_dir_index(M, i, dir);
+          for (int a = 0; a < M->n; ++a)
+            s += M->D[idir][a] * F[((k * d + dir) * V + v) * NS + node_with(M, i, dir, a)];
+          r += s / M->h[dir];
+        }
+        R[(k * V + v) * NS + i] = r;
+      }
+  free(F);
+}
+
+void or_predictor_cell(const or_mesh* M, int cell, const double* Qc, double dt, int iters,
+                       double* q) {
+  const int n = M->n, V = M->nvar, NS = ipow(n, M->dim);
+  for (int k = 0; k < n; ++k)
+    for (int v = 0; v < V; ++v)
+      for (int i = 0; i < NS; ++i) q[(k * V + v) * NS + i] = Qc[v * NS + i];
+  double* R = (double*)malloc(sizeof(double) * (size_t)n * V * NS);
+  for (int r = 0; r < iters; ++r) {
+    space_derivative_of_flux(M, cell, q, n, R);
+    for (int v = 0; v < V; ++v)
+      for (int i = 0; i < NS; ++i) {
+        double rhs[OR_MAXN];
+        for (int l = 0; l < n; ++l) rhs[l] = M->psi0[l] * Qc[v * NS + i] - dt * M->w[l] * R[(l * V + v) * NS + i];
+        for (int k = 0; k < n; ++k) {
+          double s = 0.0;
+          for (int l = 0; l < n; ++l) s += M->K1inv[k][l] * rhs[l];
+          q[(k * V + v) * NS + i] = s;
+        }
+      }
+  }
+  free(R);
+}
+
+/* Cauchy-Kowalevskaya predictor for linear PDEs (Sec. 2.1, last paragraph):
+ * q(tau) = sum_{m=0}^{N} (tau dt)^m / m! d_t^m Q, d_t^{m+1} Q = -sum_dir d_dir F_dir(d_t^m Q). */
+void or_ck_cell(const or_mesh* M, int cell, const double* Qc, double dt, double* q) {
+  const int n = M->n, V = M->nvar, NS = ipow(n, M->dim), N = M->N;
+  double* dQ = (double*)malloc(sizeof(double) * (size_t)(N + 1) * V * NS);
+  memcpy(dQ, Qc, sizeof(double) * (size_t)V * NS);
+  for (int m = 0; m < N; ++m) {
+    space_derivative_of_flux(M, cell, dQ + (size_t)m * V * NS, 1, dQ + (size_t)(m + 1) * V * NS);
+    for (int j = 0; j < V * NS; ++j) dQ[(size_t)(m + 1) * V * NS + j] *= -1.0;
+  }
+  for (int k = 0; k < n; ++k)
+    for (int j = 0; j < V * NS; ++j) {
+      double s = 0.0, fac = 1.0;
+      for (int m = 0; m <= N; ++m) {
+        if (m > 0) fac *= (M->xi[k] * dt) / m;
+        s += fac * dQ[(size_t)m * V * NS + j];
+      }
+      q[(size_t)k * V * NS + j] = s;
+    }
+  free(dQ);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Time step, eq. (CFL_condition): dt = C h / (d (2N+1) lambda_max)           */
+/* ------------------------------------------------------------------------ */
+
+double or_dt(const or_mesh* M, const double* Q) {
+  const int V = M->nvar, NS = ipow(M->n, M->dim), C = ncells(M);
+  double lam = 0.0;
+  for (int c = 0; c < C; ++c)
+    for (int i = 0; i < NS; ++i) {
+      double q[OR_MAXV];
+      for (int v = 0; v < V; ++v) q[v] = Q[((size_t)c * V + v) * NS + i];
+      for (int dir = 0; dir < M->dim; ++dir) {
+        double s = or_speed(M, c, q, dir);
+        if (s > lam) lam = s;
+      }
+    }
+  double h = M->h[0];
+  for (int a = 1; a < M->dim; ++a)
+    if (M->h[a] < h) h = M->h[a];
+  return M->cfl * h / ((double)M->dim * (2.0 * M->N + 1.0) * lam);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Rusanov flux, eq. (rusanov_flux), with one speed per face (max over nodes */
+/* and both sides).  qm/Fm: left (lower) cell's trace, qp/Fp: right cell's.  */
+/* Arrays are [v][j].                                                        */
+/* ------------------------------------------------------------------------ */
+
+void or_rusanov(const or_mesh* M, int cellL, int cellR, int dir, int nface, const double* qm,
+                const double* qp, const double* Fm, const double* Fp, double* G) {
+  const int V = M->nvar;
+  double s = 0.0;
+  for (int j = 0; j < nface; ++j) {
+    double a[OR_MAXV], b[OR_MAXV];
+    for (int v = 0; v < V; ++v) {
+      a[v] = qm[v * nface + j];
+      b[v] = qp[v * nface + j];
+    }
+    double sa = or_speed(M, cellL, a, dir), sb = or_speed(M, cellR, b, dir);
+    if (sa > s) s = sa;
+    if (sb > s) s = sb;
+  }
+  for (int v = 0; v < V; ++v)
+    for (int j = 0; j < nface; ++j) {
+      int o = v * nface + j;
+      G[o] = 0.5 * (Fm[o] + Fp[o]) + 0.5 * s * (qm[o] - qp[o]);
+    }
+}
+
+static int neighbour(const or_mesh* M, int c, int dir, int side) {
+  int cc[3] = {c % M->m[0], (c / M->m[0]) % M->m[1], c / (M->m[0] * M->m[1])};
+  cc[dir] = (cc[dir] + (side ? 1 : -1) + M->m[dir]) % M->m[dir]; /* periodic */
+  return cc[0] + M->m[0] * (cc[1] + M->m[1] * cc[2]);
+}
+
+/* index of the face node j of spatial node i for a face normal to dir:
+ * the remaining indices in increasing dimension order */
+static int face_index(const or_mesh* M, int i, int dir) {
+  int j = 0, s = 1, r = i;
+  for (int a = 0; a < M->dim; ++a) {
+    int ia = r % M->n;
+    r /= M->n;
+    if (a == dir) continue;
+    j += ia * s;
+    s *= M->n;
+  }
+  return j;
+}
+
+/* ------------------------------------------------------------------------ */
+/* One ADER-DG step, Sec. 2 and Algorithm 1:                                 */
+/*  pass 1 per cell: predictor, time averages, face traces (expansion),      */
+/*         Q += dt vol   (eq. weak_form_volume_surface, volume term)          */
+/*  pass 2 per cell: Rusanov on each face, Q -= dt surf (surface term)       */
+/* ------------------------------------------------------------------------ */
+
+double or_step(const or_mesh* M, double* Q, double dt) {
+  const int n = M->n, V = M->nvar, d = M->dim, NS = ipow(n, d), NF = ipow(n, d - 1),
+            C = ncells(M);
+  /* traces[c][dir][side][v][j] of Qbar and of Fbar_dir */
+  size_t tsz = (size_t)C * d * 2 * V * NF;
+  double* TQ = (double*)malloc(sizeof(double) * tsz);
+  double* TF = (double*)malloc(sizeof(double) * tsz);
+
+#pragma omp parallel
+  {
+    double* q = (double*)malloc(sizeof(double) * (size_t)n * V * NS);
+    double* Fbar = (double*)malloc(sizeof(double) * (size_t)d * V * NS);
+    double* Qbar = (double*)malloc(sizeof(double) * (size_t)V * NS);
+    double* Qc = (double*)malloc(sizeof(double) * (size_t)V * NS);
+#pragma omp for schedule(dynamic, 4)
+    for (int c = 0; c < C; ++c) {
+      double* Qcell = Q + (size_t)c * V * NS;
+      memcpy(Qc, Qcell, sizeof(double) * (size_t)V * NS);
+      if (M->use_ck)
+        or_ck_cell(M, c, Qc, dt, q);
+      else
+        or_predictor_cell(M, c, Qc, dt, M->picard_iters, q);
+      /* time averages over [t^n, t^n+dt] divided by dt: sum_k w_k (.)_k */
+      for (int j = 0; j < d * V * NS; ++j) Fbar[j] = 0.0;
+      for (int j = 0; j < V * NS; ++j) Qbar[j] = 0.0;
+      for (int k = 0; k < n; ++k)
+        for (int i = 0; i < NS; ++i) {
+          double qv[OR_MAXV], Fv[OR_MAXV];
+          for (int v = 0; v < V; ++v) qv[v] = q[(k * V + v) * NS + i];
+          for (int v = 0; v < V; ++v) Qbar[v * NS + i] += M->w[k] * qv[v];
+          for (int dir = 0; dir < d; ++dir) {
+            or_flux(M, c, qv, dir, Fv);
+            for (int v = 0; v < V; ++v) Fbar[(dir * V + v) * NS + i] += M->w[k] * Fv[v];
+          }
+        }
+      /* face traces (expansion): extrapolate along dir to xi = 0 and xi = 1 */
+      for (int dir = 0; dir < d; ++dir)
+        for (int side = 0; side < 2; ++side) {
+          const double* psi = side ? M->psi1 : M->psi0;
+          double* tq = TQ + (((size_t)c * d + dir) * 2 + side) * V * NF;
+          double* tf = TF + (((size_t)c * d + dir) * 2 + side) * V * NF;
+          for (int j = 0; j < V * NF; ++j) tq[j] = tf[j] = 0.0;
+          for (int v = 0; v < V; ++v)
+            for (int i = 0; i < NS; ++i) {
+              int a = node_dir_index(M, i, dir), j = face_index(M, i, dir);
+              tq[v * NF + j] += psi[a] * Qbar[v * NS + i];
+              tf[v * NF + j] += psi[a] * Fbar[(dir * V + v) * NS + i];
+            }
+        }
+      /* volume integral, mass-matrix inverted:
+       * vol_i = sum_dir (1/h_dir)(1/w_{i_dir}) sum_a w_a D[a][i_dir] Fbar_dir(i[dir<-a]) */
+      for (int v = 0; v < V; ++v)
+        for (int i = 0; i < NS; ++i) {
+          double vol = 0.0;
+          for (int dir = 0; dir < d; ++dir) {
+            int idir = node_dir_index(M, i, dir);
+            double s = 0.0;
+            for (int a = 0; a < n; ++a)
+              s += M->w[a] * M->D[a][idir] * Fbar[(dir * V + v) * NS + node_with(M, i, dir, a)];
+            vol += s / (M->h[dir] * M->w[idir]);
+          }
+          Qcell[v * NS + i] += dt * vol;
+        }
+    }
+    free(q);
+    free(Fbar);
+    free(Qbar);
+    free(Qc);
+  }
+
+#pragma omp parallel
+  {
+    double* G0 = (double*)malloc(sizeof(double) * (size_t)V * NF);
+    double* G1 = (double*)malloc(sizeof(double) * (size_t)V * NF);
+#pragma omp for schedule(static)
+    for (int c = 0; c < C; ++c) {
+      double* Qcell = Q + (size_t)c * V * NS;
+      for (int dir = 0; dir < d; ++dir) {
+        int cl = neighbour(M, c, dir, 0), cr = neighbour(M, c, dir, 1);
+        /* left face of c: (cl side 1 | c side 0);  right face: (c side 1 | cr side 0) */
+        const double* qm0 = TQ + (((size_t)cl * d + dir) * 2 + 1) * V * NF;
+        const double* Fm0 = TF + (((size_t)cl * d + dir) * 2 + 1) * V * NF;
+        const double* qp0 = TQ + (((size_t)c * d + dir) * 2 + 0) * V * NF;
+        const double* Fp0 = TF + (((size_t)c * d + dir) * 2 + 0) * V * NF;
+        const double* qm1 = TQ + (((size_t)c * d + dir) * 2 + 1) * V * NF;
+        const double* Fm1 = TF + (((size_t)c * d + dir) * 2 + 1) * V * NF;
+        const double* qp1 = TQ + (((size_t)cr * d + dir) * 2 + 0) * V * NF;
+        const double* Fp1 = TF + (((size_t)cr * d + dir) * 2 + 0) * V * NF;
+        or_rusanov(M, cl, c, dir, NF, qm0, qp0, Fm0, Fp0, G0);
+        or_rusanov(M, c, cr, dir, NF, qm1, qp1, Fm1, Fp1, G1);
+        /* surface integral: int phi_k G.n dS on the right (n = +e_dir) and
+         * left (n = -e_dir) faces, mass-matrix inverted */
+        for (int v = 0; v < V; ++v)
+          for (int i = 0; i < NS; ++i) {
+            int a = node_dir_index(M, i, dir), j = face_index(M, i, dir);
+            double surf = (M->psi1[a] * G1[v * NF + j] - M->psi0[a] * G0[v * NF + j]) /
+                          (M->h[dir] * M->w[a]);
+            Qcell[v * NS + i] -= dt * surf;
+          }
+      }
+    }
+    free(G0);
+    free(G1);
+  }
+  free(TQ);
+  free(TF);
+  return dt;
+}
+
+int or_run(const or_mesh* M, double* Q, int nsteps, double* t, double* dt_last) {
+  double tt = t ? *t : 0.0, dt = 0.0;
+  for (int s = 0; s < nsteps; ++s) {
+    dt = or_dt(M, Q);
+    or_step(M, Q, dt);
+    tt += dt;
+  }
+  if (t) *t = tt;
+  if (dt_last) *dt_last = dt;
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Heap-allocated mesh handles for the ctypes wrapper                        */
+/* ------------------------------------------------------------------------ */
+
+or_mesh* or_create(int dim, int N, const int* m, const double* lo, const double* hi, int pde,
+                   const double* params, int nparams, double cfl, int picard_iters) {
+  or_mesh* M = (or_mesh*)malloc(sizeof(or_mesh));
+  if (!M) return NULL;
+  if (or_setup(M, dim, N, m, lo, hi, pde, params, nparams, cfl, picard_iters) != 0) {
+    free(M);
+    return NULL;
+  }
+  return M;
+}
+
+void or_destroy(or_mesh* M) { free(M); }
+
+void or_set_ck(or_mesh* M, int use_ck) { M->use_ck = use_ck; }
+
+void or_set_picard_iters(or_mesh* M, int iters) { M->picard_iters = iters; }

@@ -1,0 +1,101 @@
+/*
+ * adg_oracle.h -- plain, slow, FP64 CPU implementation of the ADER-DG step
+ * (predictor by Picard iteration, Rusanov Riemann solve, volume and surface
+ * integrals, CFL time step, L2 error).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This library exists to check the CUDA path.  Only
+ * the tests, the smoke check and the CPU-baseline leg of the benchmark may
+ * load it.  It shares no code, header, table or constant with the CUDA path.
+ *
+ * Section / equation references are to Marot-Lassauzaie & Bader, "Mixed-Precision
+ * in High-Order Methods: the Impact of Floating-Point Precision on the ADER-DG
+ * Algorithm" (arXiv 2504.06889):
+ *   Sec. 2 eq. (piecewise_solution)        nodal tensor-product GL basis
+ *   Sec. 2.1 eq. (Picard)                  space-time predictor system
+ *   Sec. 2.2 eq. (weak_form_volume_surface) corrector
+ *   Sec. 2.2 eq. (CFL_condition)           time step
+ *   Sec. 2.2 eq. (rusanov_flux)            Riemann solver
+ *   Sec. 4 (acoustic, elastic, Euler, shallow water)  PDE fluxes
+ *   Sec. 4.5 eq. (L2gauss)                 error norm
+ *
+ * Data layout (same as the exported state of the library under test, but
+ * written independently): Q[cell][var][node], cell = cx + m0*(cy + m1*cz),
+ * node = i0 + n*(i1 + n*i2), n = N+1, i0 the x index (fastest).
+ */
+#ifndef ADG_ORACLE_H
+#define ADG_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OR_MAXN 10 /* n = N+1 <= 10 */
+#define OR_MAXV 9
+
+enum { OR_ACOUSTIC = 0, OR_ELASTIC = 1, OR_EULER = 2, OR_SWE = 3 };
+enum { OR_SC_PLANAR = 0, OR_SC_EULER_WAVE = 1, OR_SC_SWE_MODES = 2, OR_SC_GAUSS_PULSE = 3 };
+
+typedef struct {
+  int dim, N, n, nvar, pde;
+  int m[3];
+  double lo[3], h[3];
+  double pp[8];       /* PDE parameters as given by the caller */
+  double cfl;         /* C_CFL of eq. (CFL_condition) */
+  int picard_iters;   /* fixed number of Picard sweeps */
+  int use_ck;         /* 1: Cauchy-Kowalevskaya predictor instead of Picard (linear PDEs) */
+  const double* cell_c; /* optional per-cell wave speed for acoustics (rho fixed); NULL = none */
+  /* 1D tables on [0,1] */
+  double xi[OR_MAXN], w[OR_MAXN];
+  double D[OR_MAXN][OR_MAXN];   /* D[a][b] = psi_b'(xi_a) */
+  double psi0[OR_MAXN], psi1[OR_MAXN];
+  double K1[OR_MAXN][OR_MAXN], K1inv[OR_MAXN][OR_MAXN];
+} or_mesh;
+
+int or_nvar(int pde, int dim);
+int or_setup(or_mesh* M, int dim, int N, const int* m, const double* lo, const double* hi,
+             int pde, const double* params, int nparams, double cfl, int picard_iters);
+void or_set_cell_c(or_mesh* M, const double* cell_c);
+
+/* 1D tables (GL nodes/weights on [0,1], derivative matrix, boundary values) */
+void or_tables(int n, double* xi, double* w, double* D, double* psi0, double* psi1,
+               double* K1, double* K1inv);
+double or_lagrange(int n, const double* xi, int j, double x);
+
+/* pointwise physics */
+void or_flux(const or_mesh* M, int cell, const double* q, int dir, double* F);
+double or_speed(const or_mesh* M, int cell, const double* q, int dir);
+
+/* exact / initial data and error */
+void or_exact(const or_mesh* M, int scen, const double* sp, int nsp, const double* x, double t,
+              double* Q);
+void or_interpolate(const or_mesh* M, int scen, const double* sp, int nsp, double t, double* Q);
+void or_l2_error(const or_mesh* M, const double* Q, int scen, const double* sp, int nsp, double t,
+                 double* out);
+void or_l2_diff(const or_mesh* M, const double* Qa, const double* Qb, double* out);
+void or_totals(const or_mesh* M, const double* Q, double* tot);
+
+/* one cell's predictor: q[(k*V+v)*NS+i], plus time averages */
+void or_predictor_cell(const or_mesh* M, int cell, const double* Qc, double dt, int iters,
+                       double* q);
+void or_ck_cell(const or_mesh* M, int cell, const double* Qc, double dt, double* q);
+
+/* whole step */
+double or_dt(const or_mesh* M, const double* Q);
+double or_step(const or_mesh* M, double* Q, double dt);
+int or_run(const or_mesh* M, double* Q, int nsteps, double* t, double* dt_last);
+
+/* Rusanov flux on one face node set, exposed for unit tests */
+void or_rusanov(const or_mesh* M, int cellL, int cellR, int dir, int nface, const double* qm,
+                const double* qp, const double* Fm, const double* Fp, double* G);
+
+/* heap handles (used by the Python wrapper) */
+or_mesh* or_create(int dim, int N, const int* m, const double* lo, const double* hi, int pde,
+                   const double* params, int nparams, double cfl, int picard_iters);
+void or_destroy(or_mesh* M);
+void or_set_ck(or_mesh* M, int use_ck);
+void or_set_picard_iters(or_mesh* M, int iters);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
