@@ -1,0 +1,356 @@
+#!/usr/bin/env python3
+"""Throughput of the ADER-DG step on GB300: DOF-updates/s per precision mix.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload euler3d] [--mixes fp64,fp32]
+    python bench.py --impl reference ...     # the FP64 CPU oracle on the host cores
+
+A step is one ADER-DG time step (predictor + volume, Riemann + surface + FP64 corrector,
+CFL reduction) over the whole mesh.  The default workload is 3D Euler, N = 5, 64^3 periodic
+cells (283 M DOF), the smooth density wave; its state (2.26 GB) is larger than L2, so no
+flush is needed between steps.  Each mix runs W untimed and K timed steps from the same
+initial state; its accuracy is stated as the L2 error (eq. L2gauss) against the analytic
+solution and relative to the plain FP64 GPU path after the same steps.  The printed value
+is the headline mix (FP32 Picard/predictor, FP64 state and corrector) unless --headline.
+
+With torchrun (N > 1) every rank runs an independent replica of the workload (the cells of
+one replica fit one GPU); value = all ranks' DOF-updates / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2504_06889_gb300 import inputs as I  # noqa: E402
+
+METRIC = "DOF-updates/s per ADER-DG step by precision mix vs plain FP64 GPU at stated L2"
+UNIT = "DOF-updates/s"
+
+# flops of one pointwise flux evaluation (all directions) per PDE, counted from the formulas
+FLUX_FLOPS = {(I.ACOUSTIC, 2): 4, (I.ACOUSTIC, 3): 6, (I.ELASTIC, 2): 12, (I.ELASTIC, 3): 24,
+              (I.EULER, 2): 26, (I.EULER, 3): 36, (I.SWE, 2): 14}
+# nonzero (direction, variable) flux components
+NZ = {(I.ACOUSTIC, 2): 4, (I.ACOUSTIC, 3): 6, (I.ELASTIC, 2): 10, (I.ELASTIC, 3): 24,
+      (I.EULER, 2): 8, (I.EULER, 3): 15, (I.SWE, 2): 6}
+
+MIXES = {
+    "fp64": {"picard": "fp64", "predictor": "fp64", "riemann": "fp64", "corrector": "fp64"},
+    "fp32": {"picard": "fp32", "predictor": "fp32", "riemann": "fp64", "corrector": "fp64"},
+}
+DTYPE = {"fp64": "f64", "fp32": "f32+f64"}
+
+
+def predictor_flops_per_cell(pde, dim, N, iters=None):
+    """Algorithmic flops of the predictor kernel for one cell (sum-factorised, no padding):
+    I sweeps x n time slices x NS nodes x (flux + derivative contractions on the nonzero flux
+    components + time operator), then the final flux, time averages, volume integral and
+    face extrapolation."""
+    n = N + 1
+    NS, NF = n ** dim, n ** (dim - 1)
+    V = I.nvar(pde, dim)
+    fl, nz = FLUX_FLOPS[(pde, dim)], NZ[(pde, dim)]
+    it = n if iters is None else iters
+    sweep = n * NS * (fl + nz * 2 * n + V * 2 * n)
+    final = n * NS * (fl + 2 * V + 2 * nz)
+    vol = NS * nz * 2 * n
+    traces = 2 * dim * NF * 2 * V * 2 * n
+    return it * sweep + final + vol + traces
+
+
+def predictor_bytes_per_cell(pde, dim, N, trace_bytes):
+    """Algorithmic HBM bytes of the predictor for one cell: read and write the FP64 state,
+    write the face traces (Qbar and Fbar.n, both sides of every direction)."""
+    n = N + 1
+    V = I.nvar(pde, dim)
+    return 16 * n ** dim * V + 2 * dim * 2 * V * n ** (dim - 1) * trace_bytes
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+def alu_peak_tflops(kind, sm_mhz):
+    """FP32: 152 SMs x 128 FP32 lanes x 2 flop per FMA x SM clock.  FP64: GB300's nominal
+    1.25 TFLOP/s (FP64 runs at a small fraction of the FP32 rate on this part)."""
+    if kind == "fp32":
+        return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    return 1.25
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index=0):
+        self.proc = None
+        self.dev = device_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    import torch
+
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_oracle_sample(wl, sample_cells, steps=1):
+    """Time the FP64 oracle (as it stands) for `steps` steps on a sample mesh of the same
+    workload (same N, PDE, scenario, per-cell work) with all host cores."""
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    import oracle
+
+    oracle.build()
+    sw = wl.with_cells((sample_cells,) * wl.dim)
+    M = oracle.Mesh(sw.dim, sw.N, sw.cells, sw.pde, sw.params, cfl=sw.cfl)
+    Q = M.interpolate(sw.scenario, sw.sp)
+    t0 = time.perf_counter()
+    M.run(Q, steps)
+    el = time.perf_counter() - t0
+    return {"value": sw.dofs * steps / el, "unit": UNIT, "cores": int(os.environ["OMP_NUM_THREADS"]),
+            "kind": "oracle",
+            "sample": f"{sw.name}: {steps} step(s) on {sample_cells}^{wl.dim} cells of the same "
+                      f"workload ({sw.dofs} DOF), {el:.2f} s"}
+
+
+def run_reference(args, wl):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if ws > 1 and rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    import oracle
+
+    oracle.build()
+    sc = args.ref_cells
+    sw = wl.with_cells((sc,) * wl.dim)
+    M = oracle.Mesh(sw.dim, sw.N, sw.cells, sw.pde, sw.params, cfl=sw.cfl)
+    Q = M.interpolate(sw.scenario, sw.sp)
+    M.run(Q, args.warmup)
+    t0 = time.perf_counter()
+    M.run(Q, args.steps)
+    el = time.perf_counter() - t0
+    value = sw.dofs * args.steps / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": wl.name, "mix": "fp64 (CPU oracle)", "sample_cells": [sc] * wl.dim},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": int(os.environ["OMP_NUM_THREADS"]),
+                         "kind": "oracle",
+                         "sample": f"each step on {sc}^{wl.dim} cells of {wl.name} ({sw.dofs} DOF)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="euler3d", choices=sorted(I.WORKLOADS))
+    ap.add_argument("--cells", type=int, default=0, help="override cells per direction")
+    ap.add_argument("--mixes", default="fp64,fp32")
+    ap.add_argument("--headline", default="fp32")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--ref-cells", type=int, default=12)
+    ap.add_argument("--cpu-cells", type=int, default=16)
+    args = ap.parse_args()
+    wl = I.WORKLOADS[args.workload]()
+    if args.cells:
+        wl = wl.with_cells((args.cells,) * wl.dim)
+    if args.impl == "reference":
+        return run_reference(args, wl)
+
+    import torch
+
+    from paper_2504_06889_gb300 import adg
+
+    ws, rank, local = dist_setup()
+    adg.load()
+    peaks, peak_src = load_peaks()
+    mixes = [m for m in args.mixes.split(",") if m]
+    headline = args.headline if args.headline in mixes else mixes[-1]
+    results = {}
+    ref_state = None
+    launches = 0
+    clocks = None
+    for mix in mixes:
+        prec = MIXES[mix]
+        s = adg.Solver(wl.dim, wl.N, wl.cells, wl.pde, wl.params, cfl=wl.cfl, precision=prec)
+        s.set_initial(wl.scenario, wl.sp)
+        s.step(args.warmup)
+        torch.cuda.synchronize()
+        barrier(ws)
+        sampler = ClockSampler(local) if mix == headline else None
+        if sampler:
+            sampler.start()
+            time.sleep(0.3)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        t, ms_pred, ms_corr, ms_tot = s.step_timed(args.steps)
+        e1.record()
+        torch.cuda.synchronize()
+        barrier(ws)
+        if sampler:
+            clocks = sampler.stop()
+        ms = max_over_ranks(e0.elapsed_time(e1), ws)
+        if mix == headline:
+            launches = 2 * args.steps
+        r = {"dof_per_s": ws * wl.dofs * args.steps / (ms * 1e-3), "ms_per_step": ms / args.steps,
+             "ms_predictor": ms_pred / args.steps, "ms_corrector": ms_corr / args.steps, "t": t}
+        if wl.has_exact:
+            r["l2_vs_exact"] = s.error_vs_exact()[1]
+        if mix == "fp64":
+            ref_state = s.Q.clone()
+            ref_norm = s.l2_diff(torch.zeros_like(s.Q))[1]
+            r["l2_rel_vs_fp64_gpu"] = 0.0
+        elif ref_state is not None:
+            r["l2_rel_vs_fp64_gpu"] = s.l2_diff(ref_state)[1] / ref_norm
+        # roofline of the dominant kernel (the predictor)
+        cells = wl.ncells
+        fl = predictor_flops_per_cell(wl.pde, wl.dim, wl.N) * cells
+        kind = "fp32" if prec["picard"] == "fp32" else "fp64"
+        sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+        pk = alu_peak_tflops(kind, sm_mhz)
+        ach = fl / (ms_pred / args.steps * 1e-3) / 1e12
+        r["roofline"] = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+                         "frac": ach / pk, "traffic": None,
+                         "kernel": "k_predictor", "peak_source": f"{kind} ALU derived at {sm_mhz:.0f} MHz"}
+        tb = 8 if prec["corrector"] == "fp64" else 4
+        bts = predictor_bytes_per_cell(wl.pde, wl.dim, wl.N, tb) * cells
+        r["predictor_gbs"] = bts / (ms_pred / args.steps * 1e-3) / 1e9
+        results[mix] = r
+        if mix == headline and not args.no_e2e:
+            # end to end through the public API with pinned host buffers, every step
+            host = torch.empty(s.Q.shape, dtype=torch.float64, pin_memory=True)
+            host.copy_(s.Q)
+            ke = max(1, min(args.steps, 10))
+            torch.cuda.synchronize()
+            barrier(ws)
+            t0 = time.perf_counter()
+            for _ in range(ke):
+                s.set_state(host, t)
+                s.step(1)
+                s.lib.adg_get_state(s.ctx, adg.C.c_void_p(host.data_ptr()), 1)
+            torch.cuda.synchronize()
+            el = max_over_ranks(time.perf_counter() - t0, ws)
+            nb = host.numel() * 8
+            r["e2e"] = {"value": ws * wl.dofs * ke / el, "unit": UNIT, "h2d_bytes_per_step": nb,
+                        "d2h_bytes_per_step": nb, "steps": ke}
+        s.close()
+        del s
+        torch.cuda.empty_cache()
+
+    if rank != 0:
+        return
+    h = results[headline]
+    cpu = None if args.no_cpu else cpu_oracle_sample(wl, args.cpu_cells)
+    line = {
+        "metric": METRIC, "value": h["dof_per_s"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": h["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPE.get(headline, headline),
+        "data": "synthetic",
+        "config": {"workload": wl.name, "pde": I.PDE_NAMES[wl.pde], "dim": wl.dim, "N": wl.N,
+                   "cells": list(wl.cells), "dof": wl.dofs, "mix": headline, "cfl": wl.cfl,
+                   "parallelism": "replicas" if ws > 1 else "single",
+                   "l2_flush": "inputs larger than L2 (FP64 state %.2f GB)" % (wl.dofs * 8 / 1e9)},
+        "mixes": results,
+        "roofline": dict(h["roofline"], peak_source=h["roofline"]["peak_source"] + f" ({peak_src} peaks file)"),
+        "cpu_baseline": cpu,
+        "e2e": h.get("e2e"),
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

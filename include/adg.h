@@ -1,0 +1,180 @@
+/*
+ * adg.h -- C ABI of the GB300 (sm_103a) mixed-precision ADER-DG library.
+ *
+ * The library advances a hyperbolic PDE system  Q_t + div F(Q) = 0  on a uniform
+ * periodic Cartesian mesh with the one-step ADER-DG scheme of Marot-Lassauzaie &
+ * Bader, arXiv 2504.06889 (Sec. 2, Algorithm 1): per cell a space-time predictor
+ * (eq. Picard, solved by Picard iteration), face extrapolation and the volume
+ * integral; per face a Rusanov Riemann solve (eq. rusanov_flux); the surface
+ * integral and the update of eq. (weak_form_volume_surface); the time step of
+ * eq. (CFL_condition).  Precision is chosen per kernel, as in Sec. 3.1.
+ *
+ * Conventions
+ *  - Every call returns an adg_status.  On failure adg_last_error() describes it.
+ *  - "device" pointers are CUDA global-memory addresses on the context's device;
+ *    "host" pointers are ordinary (ideally pinned) host memory.  The caller owns
+ *    every buffer it passes; the library keeps pointers given to
+ *    adg_bind_buffers() and uses them until they are re-bound or the context is
+ *    destroyed.  The context owns only its tables and a few device scalars.
+ *  - State layout (every exported state): double Q[cells][V][(N+1)^d], cell index
+ *    cx + m0*(cy + m1*cz), node index i0 + n*(i1 + n*i2) with n = N+1 and i0 the
+ *    x index; the node i sits at x = lo + (c + xi_i) h with xi the Gauss-Legendre
+ *    points on [0,1].  Variable orders:
+ *        acoustic  (p, v_x, v_y[, v_z])
+ *        elastic   2D (s_xx, s_yy, s_xy, v_x, v_y)
+ *                  3D (s_xx, s_yy, s_zz, s_xy, s_yz, s_xz, v_x, v_y, v_z)
+ *        euler     (rho, rho v_x, rho v_y[, rho v_z], E)
+ *        swe       (h, h u, h v)   (flat bathymetry)
+ *  - All work is enqueued on the stream given by adg_set_stream() (default: the
+ *    legacy default stream).  Only adg_step(), adg_get_state(..., to_host=1),
+ *    adg_error_vs_exact() and adg_l2_diff() wait for the stream.
+ *  - Calls made before their prerequisites return ADG_ENOTINIT.
+ */
+#ifndef ADG_H
+#define ADG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define ADG_API __attribute__((visibility("default")))
+#else
+#define ADG_API
+#endif
+
+typedef struct adg_ctx adg_ctx; /* opaque, library-owned */
+
+enum adg_status {
+  ADG_OK = 0,
+  ADG_EINVAL = -1,       /* bad argument (null pointer, size out of range, bad enum) */
+  ADG_ENOTINIT = -2,     /* a prerequisite call is missing */
+  ADG_ECUDA = -3,        /* a CUDA runtime call failed; adg_last_error() has its text */
+  ADG_ENONFINITE = -4,   /* a step produced Inf/NaN; t stops at the last good step */
+  ADG_ETIMEOUT = -5,     /* reserved: a bounded device wait ran out */
+  ADG_EUNSUPPORTED = -6, /* valid but not built (e.g. no kernel for this (PDE, d, N)) */
+  ADG_ENOMEM = -7        /* workspace smaller than adg_workspace_bytes() */
+};
+
+/* PDE systems of Sec. 4 (eq. acoustic, lin_elastic, euler_eq, swe with b = const) */
+enum adg_pde { ADG_ACOUSTIC = 0, ADG_ELASTIC = 1, ADG_EULER = 2, ADG_SWE = 3 };
+
+/* The per-kernel precision knobs of Sec. 3.1 ("predictor", "Picard", "corrector",
+ * "storage"), with the Riemann solve split from the face integral. */
+enum adg_kernel {
+  ADG_K_PICARD = 0,    /* arithmetic of the Picard sweeps (flux + contractions) */
+  ADG_K_PREDICTOR = 1, /* final flux, time averages, face extrapolation, volume integral */
+  ADG_K_RIEMANN = 2,   /* Rusanov flux arithmetic */
+  ADG_K_CORRECTOR = 3, /* face-trace storage and surface-integral arithmetic */
+  ADG_K_STORAGE = 4    /* persistent state: FP64 only */
+};
+
+enum adg_prec { ADG_FP64 = 0, ADG_FP32 = 1, ADG_BF16 = 2, ADG_FP16 = 3, ADG_FP8E4M3 = 4 };
+
+enum adg_flags {
+  ADG_F_COMPENSATED_LAST = 1, /* tensor-core Picard: last sweep with split hi/lo products */
+  ADG_F_PER_CELL_SCALE = 2    /* tensor-core Picard: power-of-two scaling per cell */
+};
+
+/* Scenario closed forms for adg_set_initial() / adg_error_vs_exact(); the
+ * parameter encodings are:
+ *  ADG_SC_PLANAR      [Q0[V], nw, {amp, kx, ky, kz, omega, r[V]} x nw]
+ *                     Q = Q0 + sum amp sin(k.x - omega t) r   (Sec. 4.2.1 planar waves)
+ *  ADG_SC_EULER_WAVE  [rho0, A, kx, ky, kz, ux, uy, uz, p0]
+ *                     rho = rho0 + A sin(k.(x - u t)), velocity u, pressure p0
+ *  ADG_SC_SWE_MODES   [h0, a0, kx0, ky0, nm, {a, kx, ky, phi} x nm], at rest;
+ *                     closed form at t = 0 only
+ *  ADG_SC_GAUSS_PULSE [x0, y0, z0, sigma, amp]: p = amp exp(-|x-x0|^2/(2 sigma^2)),
+ *                     periodic distance, v = 0; closed form at t = 0 only */
+enum adg_scenario {
+  ADG_SC_PLANAR = 0,
+  ADG_SC_EULER_WAVE = 1,
+  ADG_SC_SWE_MODES = 2,
+  ADG_SC_GAUSS_PULSE = 3
+};
+
+/* Create / destroy a context bound to the current CUDA device. */
+ADG_API int adg_create(adg_ctx** out);
+ADG_API int adg_destroy(adg_ctx* c);
+
+/* cuda_stream: a cudaStream_t (e.g. torch.cuda.current_stream().cuda_stream); NULL = legacy. */
+ADG_API int adg_set_stream(adg_ctx* c, void* cuda_stream);
+
+/* Uniform periodic mesh of [lo,hi]^dim with cells[d] cells per direction and
+ * order N (dim in {2,3}).  Sec. 2: tree-structured Cartesian grid, here uniform. */
+ADG_API int adg_init_mesh(adg_ctx* c, int dim, int order_N, const int* cells, const double* lo,
+                  const double* hi);
+
+/* PDE and its parameters (host array):
+ *   acoustic: rho, K        elastic: rho, c_p, c_s        euler: gamma        swe: g */
+ADG_API int adg_set_pde(adg_ctx* c, int pde, const double* params, int nparams);
+
+/* Precision of one kernel (Sec. 3.1).  Built combinations:
+ *   PICARD     FP64, FP32 (SIMT); BF16, FP16 (tensor cores, FP32 accumulation)
+ *   PREDICTOR  FP64, FP32
+ *   RIEMANN    FP64, FP32, BF16
+ *   CORRECTOR  FP64, FP32, BF16
+ *   STORAGE    FP64
+ * Others return ADG_EUNSUPPORTED. */
+ADG_API int adg_set_kernel_precision(adg_ctx* c, int kernel, int prec, int flags);
+
+/* C_CFL of eq. (CFL_condition) (dt = cfl h / (d (2N+1) lambda_max)) and the
+ * number of Picard sweeps (<= 0: N+1). */
+ADG_API int adg_set_numerics(adg_ctx* c, double cfl, int picard_iters);
+
+/* Bytes the caller must provide as workspace for this mesh/PDE/precision. */
+ADG_API int adg_workspace_bytes(const adg_ctx* c, size_t* bytes);
+/* Number of doubles of the state (cells * V * (N+1)^d) and V. */
+ADG_API int adg_state_size(const adg_ctx* c, size_t* ndouble, int* nvar);
+
+/* Bind caller-owned device buffers: the FP64 state (adg_state_size doubles) and
+ * a workspace of at least adg_workspace_bytes(), 256-byte aligned. */
+ADG_API int adg_bind_buffers(adg_ctx* c, double* d_state, void* d_workspace, size_t workspace_bytes);
+
+/* Interpolate a scenario's closed form at the GL nodes at t = 0 (Sec. 4.5: the
+ * DG solution starts from Q_h^*) and set t = 0.  params: host array, kept by the
+ * context for adg_error_vs_exact(). */
+ADG_API int adg_set_initial(adg_ctx* c, int scenario, const double* params, int nparams);
+
+/* Copy a state in (from_host = 1: host pointer; 0: device pointer) and set time t. */
+ADG_API int adg_set_state(adg_ctx* c, const double* Q, double t, int from_host);
+/* Copy the state out (to_host = 1: host pointer, waits; 0: device pointer, async). */
+ADG_API int adg_get_state(adg_ctx* c, double* Q, int to_host);
+
+/* Advance nsteps steps (dt^n from Q^n, eq. CFL_condition).  On return *t_out is
+ * the time after the last good step and *dt_last_out the last dt (either may be
+ * NULL).  Waits for the stream.  Returns ADG_ENONFINITE if a step produced a
+ * non-finite value. */
+ADG_API int adg_step(adg_ctx* c, int nsteps, double* t_out, double* dt_last_out);
+
+/* Enqueue nsteps steps and return without waiting (no status check). */
+ADG_API int adg_step_async(adg_ctx* c, int nsteps);
+
+/* adg_step with CUDA events around every kernel launch on the context's stream:
+ * ms_kernels[0] = summed device time of the predictor kernels, ms_kernels[1] = of the
+ * corrector kernels, ms_kernels[2] = of the whole nsteps (first to last event). */
+ADG_API int adg_step_timed(adg_ctx* c, int nsteps, double* t_out, double* ms_kernels);
+
+/* Current time and the dt the next step will use (waits). */
+ADG_API int adg_get_time(adg_ctx* c, double* t, double* dt_next);
+
+/* eq. (L2gauss) of Sec. 4.5 in FP64 between the state and the scenario's closed
+ * form at the current time: l2_per_var[V] (may be NULL) and the total. */
+ADG_API int adg_error_vs_exact(adg_ctx* c, double* l2_per_var, double* l2_total);
+
+/* eq. (L2gauss) between the state and another device state of the same shape. */
+ADG_API int adg_l2_diff(adg_ctx* c, const double* d_Qref, double* l2_per_var, double* l2_total);
+
+/* Text for the last failure on this context (never NULL). */
+ADG_API const char* adg_last_error(const adg_ctx* c);
+
+/* Number of variables of a PDE in dim dimensions, or -1. */
+ADG_API int adg_nvar(int pde, int dim);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ADG_H */

@@ -77,6 +77,7 @@ def _load():
             lib.or_step.argtypes = [P, dp, C.c_double]
             lib.or_step.restype = C.c_double
             lib.or_run.argtypes = [P, dp, C.c_int, dp, dp]
+            lib.or_step_cells.argtypes = [P, dp, C.c_double, C.c_int, ip, dp]
             lib.or_rusanov.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int, dp, dp, dp, dp, dp]
             _lib = lib
     return _lib
@@ -225,6 +226,15 @@ class Mesh:
         dl = np.zeros(1)
         _load().or_run(self._h, _dp(Q), int(nsteps), _dp(tt), _dp(dl))
         return float(tt[0]), float(dl[0])
+
+    def step_cells(self, Q, dt, cells):
+        """Q^{n+1} of the listed cells only (each needs itself and its face neighbours)."""
+        Q = np.ascontiguousarray(Q, dtype=np.float64)
+        ids = np.ascontiguousarray(cells, dtype=np.int32)
+        out = np.zeros((len(ids), self.V, self.NS))
+        _load().or_step_cells(self._h, _dp(Q), dt, len(ids), ids.ctypes.data_as(C.POINTER(C.c_int)),
+                              _dp(out))
+        return out
 
     def rusanov(self, qm, qp, Fm, Fp, dir, cellL=0, cellR=0):
         qm, qp, Fm, Fp = (np.ascontiguousarray(a, dtype=np.float64) for a in (qm, qp, Fm, Fp))

@@ -619,113 +619,178 @@ static int face_index(const or_mesh* M, int i, int dir) {
 /*  pass 2 per cell: Rusanov on each face, Q -= dt surf (surface term)       */
 /* ------------------------------------------------------------------------ */
 
+/* Pass 1 for one cell: reads Qc (the cell's Q^n), writes Qout = Q^n + dt vol and the
+ * cell's traces tq/tf [dir][side][v][j] of Qbar and Fbar_dir. */
+static void predict_cell(const or_mesh* M, int c, const double* Qc, double dt, double* Qout,
+                         double* tq_cell, double* tf_cell) {
+  const int n = M->n, V = M->nvar, d = M->dim, NS = ipow(n, d), NF = ipow(n, d - 1);
+  double* q = (double*)malloc(sizeof(double) * (size_t)n * V * NS);
+  double* Fbar = (double*)malloc(sizeof(double) * (size_t)d * V * NS);
+  double* Qbar = (double*)malloc(sizeof(double) * (size_t)V * NS);
+  if (M->use_ck)
+    or_ck_cell(M, c, Qc, dt, q);
+  else
+    or_predictor_cell(M, c, Qc, dt, M->picard_iters, q);
+  /* time averages over [t^n, t^n+dt] divided by dt: sum_k w_k (.)_k */
+  for (int j = 0; j < d * V * NS; ++j) Fbar[j] = 0.0;
+  for (int j = 0; j < V * NS; ++j) Qbar[j] = 0.0;
+  for (int k = 0; k < n; ++k)
+    for (int i = 0; i < NS; ++i) {
+      double qv[OR_MAXV], Fv[OR_MAXV];
+      for (int v = 0; v < V; ++v) qv[v] = q[(k * V + v) * NS + i];
+      for (int v = 0; v < V; ++v) Qbar[v * NS + i] += M->w[k] * qv[v];
+      for (int dir = 0; dir < d; ++dir) {
+        or_flux(M, c, qv, dir, Fv);
+        for (int v = 0; v < V; ++v) Fbar[(dir * V + v) * NS + i] += M->w[k] * Fv[v];
+      }
+    }
+  /* face traces (expansion): extrapolate along dir to xi = 0 and xi = 1 */
+  for (int dir = 0; dir < d; ++dir)
+    for (int side = 0; side < 2; ++side) {
+      const double* psi = side ? M->psi1 : M->psi0;
+      double* tq = tq_cell + (dir * 2 + side) * V * NF;
+      double* tf = tf_cell + (dir * 2 + side) * V * NF;
+      for (int j = 0; j < V * NF; ++j) tq[j] = tf[j] = 0.0;
+      for (int v = 0; v < V; ++v)
+        for (int i = 0; i < NS; ++i) {
+          int a = node_dir_index(M, i, dir), j = face_index(M, i, dir);
+          tq[v * NF + j] += psi[a] * Qbar[v * NS + i];
+          tf[v * NF + j] += psi[a] * Fbar[(dir * V + v) * NS + i];
+        }
+    }
+  /* volume integral, mass-matrix inverted:
+   * vol_i = sum_dir (1/h_dir)(1/w_{i_dir}) sum_a w_a D[a][i_dir] Fbar_dir(i[dir<-a]) */
+  for (int v = 0; v < V; ++v)
+    for (int i = 0; i < NS; ++i) {
+      double vol = 0.0;
+      for (int dir = 0; dir < d; ++dir) {
+        int idir = node_dir_index(M, i, dir);
+        double s = 0.0;
+        for (int a = 0; a < n; ++a)
+          s += M->w[a] * M->D[a][idir] * Fbar[(dir * V + v) * NS + node_with(M, i, dir, a)];
+        vol += s / (M->h[dir] * M->w[idir]);
+      }
+      Qout[v * NS + i] = Qc[v * NS + i] + dt * vol;
+    }
+  free(q);
+  free(Fbar);
+  free(Qbar);
+}
+
+/* Pass 2 for one cell c: trace(cell, dir, side) returns that cell's [v][j] block.
+ * Qcell holds Q^n + dt vol on entry and Q^{n+1} on exit. */
+typedef const double* (*trace_fn)(const void* ctx, int cell, int dir, int side, int which);
+
+static void correct_cell(const or_mesh* M, int c, double dt, trace_fn tr, const void* ctx,
+                         double* Qcell) {
+  const int V = M->nvar, d = M->dim, NS = ipow(M->n, d), NF = ipow(M->n, d - 1);
+  double* G0 = (double*)malloc(sizeof(double) * (size_t)V * NF);
+  double* G1 = (double*)malloc(sizeof(double) * (size_t)V * NF);
+  for (int dir = 0; dir < d; ++dir) {
+    int cl = neighbour(M, c, dir, 0), cr = neighbour(M, c, dir, 1);
+    /* left face of c: (cl side 1 | c side 0);  right face: (c side 1 | cr side 0) */
+    or_rusanov(M, cl, c, dir, NF, tr(ctx, cl, dir, 1, 0), tr(ctx, c, dir, 0, 0),
+               tr(ctx, cl, dir, 1, 1), tr(ctx, c, dir, 0, 1), G0);
+    or_rusanov(M, c, cr, dir, NF, tr(ctx, c, dir, 1, 0), tr(ctx, cr, dir, 0, 0),
+               tr(ctx, c, dir, 1, 1), tr(ctx, cr, dir, 0, 1), G1);
+    /* surface integral: int phi_k G.n dS on the right (n = +e_dir) and
+     * left (n = -e_dir) faces, mass-matrix inverted */
+    for (int v = 0; v < V; ++v)
+      for (int i = 0; i < NS; ++i) {
+        int a = node_dir_index(M, i, dir), j = face_index(M, i, dir);
+        double surf = (M->psi1[a] * G1[v * NF + j] - M->psi0[a] * G0[v * NF + j]) /
+                      (M->h[dir] * M->w[a]);
+        Qcell[v * NS + i] -= dt * surf;
+      }
+  }
+  free(G0);
+  free(G1);
+}
+
+typedef struct {
+  const double* TQ;
+  const double* TF;
+  int d, V, NF;
+} all_traces;
+
+static const double* all_trace(const void* ctx, int cell, int dir, int side, int which) {
+  const all_traces* A = (const all_traces*)ctx;
+  const double* base = which ? A->TF : A->TQ;
+  return base + (((size_t)cell * A->d + dir) * 2 + side) * A->V * A->NF;
+}
+
 double or_step(const or_mesh* M, double* Q, double dt) {
   const int n = M->n, V = M->nvar, d = M->dim, NS = ipow(n, d), NF = ipow(n, d - 1),
             C = ncells(M);
-  /* traces[c][dir][side][v][j] of Qbar and of Fbar_dir */
   size_t tsz = (size_t)C * d * 2 * V * NF;
   double* TQ = (double*)malloc(sizeof(double) * tsz);
   double* TF = (double*)malloc(sizeof(double) * tsz);
-
 #pragma omp parallel
   {
-    double* q = (double*)malloc(sizeof(double) * (size_t)n * V * NS);
-    double* Fbar = (double*)malloc(sizeof(double) * (size_t)d * V * NS);
-    double* Qbar = (double*)malloc(sizeof(double) * (size_t)V * NS);
     double* Qc = (double*)malloc(sizeof(double) * (size_t)V * NS);
 #pragma omp for schedule(dynamic, 4)
     for (int c = 0; c < C; ++c) {
       double* Qcell = Q + (size_t)c * V * NS;
       memcpy(Qc, Qcell, sizeof(double) * (size_t)V * NS);
-      if (M->use_ck)
-        or_ck_cell(M, c, Qc, dt, q);
-      else
-        or_predictor_cell(M, c, Qc, dt, M->picard_iters, q);
-      /* time averages over [t^n, t^n+dt] divided by dt: sum_k w_k (.)_k */
-      for (int j = 0; j < d * V * NS; ++j) Fbar[j] = 0.0;
-      for (int j = 0; j < V * NS; ++j) Qbar[j] = 0.0;
-      for (int k = 0; k < n; ++k)
-        for (int i = 0; i < NS; ++i) {
-          double qv[OR_MAXV], Fv[OR_MAXV];
-          for (int v = 0; v < V; ++v) qv[v] = q[(k * V + v) * NS + i];
-          for (int v = 0; v < V; ++v) Qbar[v * NS + i] += M->w[k] * qv[v];
-          for (int dir = 0; dir < d; ++dir) {
-            or_flux(M, c, qv, dir, Fv);
-            for (int v = 0; v < V; ++v) Fbar[(dir * V + v) * NS + i] += M->w[k] * Fv[v];
-          }
-        }
-      /* face traces (expansion): extrapolate along dir to xi = 0 and xi = 1 */
-      for (int dir = 0; dir < d; ++dir)
-        for (int side = 0; side < 2; ++side) {
-          const double* psi = side ? M->psi1 : M->psi0;
-          double* tq = TQ + (((size_t)c * d + dir) * 2 + side) * V * NF;
-          double* tf = TF + (((size_t)c * d + dir) * 2 + side) * V * NF;
-          for (int j = 0; j < V * NF; ++j) tq[j] = tf[j] = 0.0;
-          for (int v = 0; v < V; ++v)
-            for (int i = 0; i < NS; ++i) {
-              int a = node_dir_index(M, i, dir), j = face_index(M, i, dir);
-              tq[v * NF + j] += psi[a] * Qbar[v * NS + i];
-              tf[v * NF + j] += psi[a] * Fbar[(dir * V + v) * NS + i];
-            }
-        }
-      /* volume integral, mass-matrix inverted:
-       * vol_i = sum_dir (1/h_dir)(1/w_{i_dir}) sum_a w_a D[a][i_dir] Fbar_dir(i[dir<-a]) */
-      for (int v = 0; v < V; ++v)
-        for (int i = 0; i < NS; ++i) {
-          double vol = 0.0;
-          for (int dir = 0; dir < d; ++dir) {
-            int idir = node_dir_index(M, i, dir);
-            double s = 0.0;
-            for (int a = 0; a < n; ++a)
-              s += M->w[a] * M->D[a][idir] * Fbar[(dir * V + v) * NS + node_with(M, i, dir, a)];
-            vol += s / (M->h[dir] * M->w[idir]);
-          }
-          Qcell[v * NS + i] += dt * vol;
-        }
+      predict_cell(M, c, Qc, dt, Qcell, TQ + (size_t)c * d * 2 * V * NF,
+                   TF + (size_t)c * d * 2 * V * NF);
     }
-    free(q);
-    free(Fbar);
-    free(Qbar);
     free(Qc);
   }
-
-#pragma omp parallel
-  {
-    double* G0 = (double*)malloc(sizeof(double) * (size_t)V * NF);
-    double* G1 = (double*)malloc(sizeof(double) * (size_t)V * NF);
-#pragma omp for schedule(static)
-    for (int c = 0; c < C; ++c) {
-      double* Qcell = Q + (size_t)c * V * NS;
-      for (int dir = 0; dir < d; ++dir) {
-        int cl = neighbour(M, c, dir, 0), cr = neighbour(M, c, dir, 1);
-        /* left face of c: (cl side 1 | c side 0);  right face: (c side 1 | cr side 0) */
-        const double* qm0 = TQ + (((size_t)cl * d + dir) * 2 + 1) * V * NF;
-        const double* Fm0 = TF + (((size_t)cl * d + dir) * 2 + 1) * V * NF;
-        const double* qp0 = TQ + (((size_t)c * d + dir) * 2 + 0) * V * NF;
-        const double* Fp0 = TF + (((size_t)c * d + dir) * 2 + 0) * V * NF;
-        const double* qm1 = TQ + (((size_t)c * d + dir) * 2 + 1) * V * NF;
-        const double* Fm1 = TF + (((size_t)c * d + dir) * 2 + 1) * V * NF;
-        const double* qp1 = TQ + (((size_t)cr * d + dir) * 2 + 0) * V * NF;
-        const double* Fp1 = TF + (((size_t)cr * d + dir) * 2 + 0) * V * NF;
-        or_rusanov(M, cl, c, dir, NF, qm0, qp0, Fm0, Fp0, G0);
-        or_rusanov(M, c, cr, dir, NF, qm1, qp1, Fm1, Fp1, G1);
-        /* surface integral: int phi_k G.n dS on the right (n = +e_dir) and
-         * left (n = -e_dir) faces, mass-matrix inverted */
-        for (int v = 0; v < V; ++v)
-          for (int i = 0; i < NS; ++i) {
-            int a = node_dir_index(M, i, dir), j = face_index(M, i, dir);
-            double surf = (M->psi1[a] * G1[v * NF + j] - M->psi0[a] * G0[v * NF + j]) /
-                          (M->h[dir] * M->w[a]);
-            Qcell[v * NS + i] -= dt * surf;
-          }
-      }
-    }
-    free(G0);
-    free(G1);
-  }
+  all_traces A = {TQ, TF, d, V, NF};
+#pragma omp parallel for schedule(static)
+  for (int c = 0; c < C; ++c) correct_cell(M, c, dt, all_trace, &A, Q + (size_t)c * V * NS);
   free(TQ);
   free(TF);
+  (void)n;
   return dt;
+}
+
+/* The same step evaluated only at the listed cells: out[s] = Q^{n+1} of cells[s].  Each listed
+ * cell needs the predictors of itself and its 2d face neighbours. */
+typedef struct {
+  int d, V, NF, nloc;
+  const int* ids;
+  const double* TQ;
+  const double* TF;
+} local_traces;
+
+static const double* local_trace(const void* ctx, int cell, int dir, int side, int which) {
+  const local_traces* L = (const local_traces*)ctx;
+  int s = 0;
+  while (s < L->nloc && L->ids[s] != cell) ++s;
+  const double* base = which ? L->TF : L->TQ;
+  return base + (((size_t)s * L->d + dir) * 2 + side) * L->V * L->NF;
+}
+
+void or_step_cells(const or_mesh* M, const double* Q, double dt, int nsample, const int* cells,
+                   double* out) {
+  const int V = M->nvar, d = M->dim, NS = ipow(M->n, d), NF = ipow(M->n, d - 1);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int s = 0; s < nsample; ++s) {
+    int ids[7];
+    int nloc = 0;
+    ids[nloc++] = cells[s];
+    for (int dir = 0; dir < d; ++dir)
+      for (int side = 0; side < 2; ++side) {
+        int nb = neighbour(M, cells[s], dir, side), seen = 0;
+        for (int t = 0; t < nloc; ++t) seen |= ids[t] == nb;
+        if (!seen) ids[nloc++] = nb;
+      }
+    double* TQ = (double*)malloc(sizeof(double) * (size_t)nloc * d * 2 * V * NF);
+    double* TF = (double*)malloc(sizeof(double) * (size_t)nloc * d * 2 * V * NF);
+    double* Qv = (double*)malloc(sizeof(double) * (size_t)V * NS);
+    for (int t = 0; t < nloc; ++t) {
+      predict_cell(M, ids[t], Q + (size_t)ids[t] * V * NS, dt, Qv, TQ + (size_t)t * d * 2 * V * NF,
+                   TF + (size_t)t * d * 2 * V * NF);
+      if (t == 0) memcpy(out + (size_t)s * V * NS, Qv, sizeof(double) * (size_t)V * NS);
+    }
+    local_traces L = {d, V, NF, nloc, ids, TQ, TF};
+    correct_cell(M, cells[s], dt, local_trace, &L, out + (size_t)s * V * NS);
+    free(TQ);
+    free(TF);
+    free(Qv);
+  }
 }
 
 int or_run(const or_mesh* M, double* Q, int nsteps, double* t, double* dt_last) {

@@ -83,6 +83,9 @@ void or_ck_cell(const or_mesh* M, int cell, const double* Qc, double dt, double*
 double or_dt(const or_mesh* M, const double* Q);
 double or_step(const or_mesh* M, double* Q, double dt);
 int or_run(const or_mesh* M, double* Q, int nsteps, double* t, double* dt_last);
+/* the step at listed cells only: out[s][V][NS] = Q^{n+1} of cells[s] (needs full Q^n) */
+void or_step_cells(const or_mesh* M, const double* Q, double dt, int nsample, const int* cells,
+                   double* out);
 
 /* Rusanov flux on one face node set, exposed for unit tests */
 void or_rusanov(const or_mesh* M, int cellL, int cellR, int dir, int nface, const double* qm,

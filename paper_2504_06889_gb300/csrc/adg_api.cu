@@ -1,0 +1,651 @@
+// Host implementation of the C ABI declared in include/adg.h.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/adg.h"
+#include "adg_internal.h"
+
+namespace adg {
+
+// ---- kernel registry ---------------------------------------------------------------------------
+static std::vector<Entry>& registry() {
+  static std::vector<Entry> r;
+  return r;
+}
+void register_entry(const Entry& e) { registry().push_back(e); }
+
+void register_acoustic();
+void register_euler();
+void register_elastic();
+void register_swe();
+
+static void ensure_registry() {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    register_acoustic();
+    register_euler();
+    register_elastic();
+    register_swe();
+  });
+}
+
+const Entry* find_entry(int pde, int dim, int N) {
+  ensure_registry();
+  for (const Entry& e : registry())
+    if (e.pde == pde && e.dim == dim && e.N == N) return &e;
+  return nullptr;
+}
+
+// ---- 1D tables on [0,1]: Gauss-Legendre points by Newton on the shifted Legendre polynomial,
+// barycentric Lagrange weights for derivative and boundary values (Sec. 2). -------------------
+static void legendre_shifted(int n, long double x, long double* P, long double* dP) {
+  // P_n(2x-1) and d/dx via the three-term recurrence in t = 2x - 1
+  const long double t = 2.0L * x - 1.0L;
+  long double pm = 0.0L, p = 1.0L, dpm = 0.0L, dp = 0.0L;
+  for (int k = 0; k < n; ++k) {
+    const long double pn = ((2 * k + 1) * t * p - k * pm) / (k + 1);
+    const long double dpn = ((2 * k + 1) * (p + t * dp) - k * dpm) / (k + 1);
+    pm = p;
+    p = pn;
+    dpm = dp;
+    dp = dpn;
+  }
+  *P = p;
+  *dP = 2.0L * dp;  // chain rule dt/dx = 2
+}
+
+static bool build_tables(int n, Tables* T) {
+  if (n < 1 || n > kMaxN1) return false;
+  std::memset(T, 0, sizeof(*T));
+  T->n = n;
+  long double x[kMaxN1], w[kMaxN1], b[kMaxN1];
+  const long double pi = 3.14159265358979323846264338327950288L;
+  for (int j = 0; j < n; ++j) {
+    long double xj = 0.5L * (1.0L - cosl(pi * (j + 0.75L) / (n + 0.5L)));  // ascending guess
+    for (int it = 0; it < 200; ++it) {
+      long double P, dP;
+      legendre_shifted(n, xj, &P, &dP);
+      const long double step = P / dP;
+      xj -= step;
+      if (fabsl(step) < 1e-20L) break;
+    }
+    long double P, dP;
+    legendre_shifted(n, xj, &P, &dP);
+    x[j] = xj;
+    w[j] = 1.0L / (xj * (1.0L - xj) * dP * dP);  // 2/((1-t^2) P'(t)^2) / 2 with t = 2x-1
+  }
+  for (int j = 0; j < n; ++j) {
+    long double p = 1.0L;
+    for (int m = 0; m < n; ++m)
+      if (m != j) p *= (x[j] - x[m]);
+    b[j] = 1.0L / p;
+  }
+  long double D[kMaxN1][kMaxN1];
+  for (int i = 0; i < n; ++i) {
+    long double diag = 0.0L;
+    for (int j = 0; j < n; ++j) {
+      if (j == i) continue;
+      D[i][j] = (b[j] / b[i]) / (x[i] - x[j]);
+      diag -= D[i][j];
+    }
+    D[i][i] = diag;
+  }
+  auto boundary = [&](long double s, long double* out) {
+    long double den = 0.0L;
+    for (int m = 0; m < n; ++m) den += b[m] / (s - x[m]);
+    for (int j = 0; j < n; ++j) out[j] = (b[j] / (s - x[j])) / den;
+  };
+  long double p0[kMaxN1], p1[kMaxN1];
+  boundary(0.0L, p0);
+  boundary(1.0L, p1);
+  // K1[k][l] = psi_k(1) psi_l(1) - w_l psi_k'(xi_l); P = K1^{-1} diag(w) by Gaussian elimination
+  long double A[kMaxN1][2 * kMaxN1];
+  for (int k = 0; k < n; ++k)
+    for (int l = 0; l < n; ++l) {
+      A[k][l] = p1[k] * p1[l] - w[l] * D[l][k];
+      A[k][n + l] = (k == l) ? w[l] : 0.0L;
+    }
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (fabsl(A[r][c]) > fabsl(A[piv][c])) piv = r;
+    if (fabsl(A[piv][c]) < 1e-30L) return false;
+    if (piv != c)
+      for (int k = 0; k < 2 * n; ++k) std::swap(A[c][k], A[piv][k]);
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      const long double f = A[r][c] / A[c][c];
+      for (int k = 0; k < 2 * n; ++k) A[r][k] -= f * A[c][k];
+    }
+  }
+  for (int k = 0; k < n; ++k) {
+    T->xi[k] = (double)x[k];
+    T->w[k] = (double)w[k];
+    T->psi0[k] = (double)p0[k];
+    T->psi1[k] = (double)p1[k];
+    for (int l = 0; l < n; ++l) {
+      T->D[k][l] = (double)D[k][l];
+      T->P[k][l] = (double)(A[k][n + l] / A[k][k]);
+      T->Vm[k][l] = (double)(w[l] * D[l][k] / w[k]);
+    }
+  }
+  return true;
+}
+
+}  // namespace adg
+
+using namespace adg;
+
+struct adg_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool have_mesh = false, have_pde = false, have_bufs = false, have_state = false;
+  int dim = 0, N = 0, n = 0, NS = 0, NF = 0, V = 0;
+  int m[3] = {1, 1, 1};
+  double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1}, h[3] = {1, 1, 1};
+  int ncells = 0;
+  int pde = -1;
+  double params[8] = {0};
+  PdeParams pp{};
+  int prec[5] = {P64, P64, P64, P64, P64};
+  int flags = 0;
+  double cfl = 0.9;
+  int picard_iters = 0;
+  double* Q = nullptr;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  DevScalars* sc = nullptr;
+  double* d_sp = nullptr;  // scenario parameters
+  int d_sp_cap = 0;
+  double* d_l2 = nullptr;  // [kMaxV + 1]
+  double* d_cell_c = nullptr;
+  int scenario = -1;
+  std::vector<double> sp;
+  Tables tab{};
+  const Entry* entry = nullptr;
+  std::string err;
+};
+
+static int fail(adg_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+static int cuda_fail(adg_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, ADG_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define ADG_CUDA(c, call)                                  \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, #call); \
+  } while (0)
+
+static size_t trace_elem_bytes(int p) { return p == P64 ? 8 : p == P32 ? 4 : 2; }
+
+static size_t traces_bytes(const adg_ctx* c) {
+  return (size_t)c->ncells * c->dim * 2 * 2 * c->V * c->NF * trace_elem_bytes(c->prec[ADG_K_CORRECTOR]);
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static size_t l2_partial_bytes(const adg_ctx* c) { return (size_t)152 * 4 * c->V * sizeof(double); }
+
+static void fill_step_args(const adg_ctx* c, StepArgs* a) {
+  std::memset(a, 0, sizeof(*a));
+  a->Q = c->Q;
+  a->traces = c->ws;
+  a->sc = c->sc;
+  for (int d = 0; d < 3; ++d) {
+    a->m[d] = c->m[d];
+    a->invh[d] = 1.0 / c->h[d];
+  }
+  a->ncells = c->ncells;
+  double hmin = c->h[0];
+  for (int d = 1; d < c->dim; ++d) hmin = std::min(hmin, c->h[d]);
+  a->hmin = hmin;
+  a->cfl = c->cfl;
+  a->picard_iters = c->picard_iters > 0 ? c->picard_iters : c->N + 1;
+  a->tab = c->tab;
+  a->pp = c->pp;
+}
+
+extern "C" {
+
+int adg_nvar(int pde, int dim) {
+  if (dim < 2 || dim > 3) return -1;
+  switch (pde) {
+    case ADG_ACOUSTIC: return 1 + dim;
+    case ADG_ELASTIC: return dim == 3 ? 9 : 5;
+    case ADG_EULER: return 2 + dim;
+    case ADG_SWE: return dim == 2 ? 3 : -1;
+  }
+  return -1;
+}
+
+int adg_create(adg_ctx** out) {
+  if (!out) return ADG_EINVAL;
+  *out = nullptr;
+  adg_ctx* c = new adg_ctx();
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e == cudaSuccess) e = cudaMalloc(&c->sc, sizeof(DevScalars));
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_l2, sizeof(double) * (kMaxV + 1));
+  if (e == cudaSuccess) e = cudaMemset(c->sc, 0, sizeof(DevScalars));
+  if (e != cudaSuccess) {
+    if (c->sc) cudaFree(c->sc);
+    if (c->d_l2) cudaFree(c->d_l2);
+    delete c;
+    return ADG_ECUDA;
+  }
+  *out = c;
+  return ADG_OK;
+}
+
+int adg_destroy(adg_ctx* c) {
+  if (!c) return ADG_EINVAL;
+  if (c->sc) cudaFree(c->sc);
+  if (c->d_l2) cudaFree(c->d_l2);
+  if (c->d_sp) cudaFree(c->d_sp);
+  if (c->d_cell_c) cudaFree(c->d_cell_c);
+  delete c;
+  return ADG_OK;
+}
+
+const char* adg_last_error(const adg_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int adg_set_stream(adg_ctx* c, void* s) {
+  if (!c) return ADG_EINVAL;
+  c->stream = (cudaStream_t)s;
+  return ADG_OK;
+}
+
+static void refresh_entry(adg_ctx* c) {
+  c->entry = (c->have_mesh && c->have_pde) ? find_entry(c->pde, c->dim, c->N) : nullptr;
+}
+
+int adg_init_mesh(adg_ctx* c, int dim, int order_N, const int* cells, const double* lo,
+                  const double* hi) {
+  if (!c) return ADG_EINVAL;
+  if (dim < 2 || dim > 3) return fail(c, ADG_EINVAL, "dim must be 2 or 3");
+  if (order_N < 0 || order_N + 1 > kMaxN1) return fail(c, ADG_EINVAL, "order N must be in [0, 7]");
+  if (!cells || !lo || !hi) return fail(c, ADG_EINVAL, "null cells/lo/hi");
+  long long nc = 1;
+  for (int d = 0; d < dim; ++d) {
+    if (cells[d] < 1) return fail(c, ADG_EINVAL, "cells must be >= 1");
+    if (!(hi[d] > lo[d])) return fail(c, ADG_EINVAL, "hi must exceed lo");
+    nc *= cells[d];
+  }
+  if (nc > (1LL << 30)) return fail(c, ADG_EINVAL, "too many cells");
+  c->dim = dim;
+  c->N = order_N;
+  c->n = order_N + 1;
+  c->NS = 1;
+  for (int d = 0; d < dim; ++d) c->NS *= c->n;
+  c->NF = c->NS / c->n;
+  for (int d = 0; d < 3; ++d) {
+    c->m[d] = d < dim ? cells[d] : 1;
+    c->lo[d] = d < dim ? lo[d] : 0.0;
+    c->hi[d] = d < dim ? hi[d] : 1.0;
+    c->h[d] = (c->hi[d] - c->lo[d]) / c->m[d];
+  }
+  c->ncells = (int)nc;
+  if (!build_tables(c->n, &c->tab)) return fail(c, ADG_EINVAL, "table construction failed");
+  c->have_mesh = true;
+  c->have_bufs = false;
+  c->have_state = false;
+  if (c->have_pde) c->V = adg_nvar(c->pde, dim);
+  refresh_entry(c);
+  return ADG_OK;
+}
+
+int adg_set_pde(adg_ctx* c, int pde, const double* params, int nparams) {
+  if (!c) return ADG_EINVAL;
+  if (!c->have_mesh) return fail(c, ADG_ENOTINIT, "adg_init_mesh first");
+  const int V = adg_nvar(pde, c->dim);
+  if (V < 0) return fail(c, ADG_EINVAL, "unknown PDE for this dimension");
+  const int need = pde == ADG_ACOUSTIC ? 2 : pde == ADG_ELASTIC ? 3 : 1;
+  if (!params || nparams < need) return fail(c, ADG_EINVAL, "missing PDE parameters");
+  PdeParams p{};
+  p.pde = pde;
+  if (pde == ADG_ACOUSTIC) {
+    p.rho = params[0];
+    p.K = params[1];
+    if (!(p.rho > 0 && p.K > 0)) return fail(c, ADG_EINVAL, "acoustic: rho, K > 0");
+  } else if (pde == ADG_ELASTIC) {
+    p.rho = params[0];
+    p.cp = params[1];
+    p.cs = params[2];
+    p.mu = p.rho * p.cs * p.cs;
+    p.lam = p.rho * p.cp * p.cp - 2.0 * p.mu;
+    if (!(p.rho > 0 && p.cp > 0 && p.cs > 0)) return fail(c, ADG_EINVAL, "elastic: rho, cp, cs > 0");
+  } else if (pde == ADG_EULER) {
+    p.gamma = params[0];
+    if (!(p.gamma > 1)) return fail(c, ADG_EINVAL, "euler: gamma > 1");
+  } else {
+    p.g = params[0];
+    if (!(p.g > 0)) return fail(c, ADG_EINVAL, "swe: g > 0");
+  }
+  p.cell_c = c->d_cell_c;
+  c->pp = p;
+  c->pde = pde;
+  c->V = V;
+  for (int j = 0; j < nparams && j < 8; ++j) c->params[j] = params[j];
+  c->have_pde = true;
+  c->have_bufs = false;
+  c->have_state = false;
+  refresh_entry(c);
+  if (!c->entry)
+    return fail(c, ADG_EUNSUPPORTED, "no kernels built for this (PDE, dim, N)");
+  return ADG_OK;
+}
+
+int adg_set_kernel_precision(adg_ctx* c, int kernel, int prec, int flags) {
+  if (!c) return ADG_EINVAL;
+  if (kernel < 0 || kernel > ADG_K_STORAGE) return fail(c, ADG_EINVAL, "unknown kernel");
+  if (prec < 0 || prec > ADG_FP8E4M3) return fail(c, ADG_EINVAL, "unknown precision");
+  if (kernel == ADG_K_STORAGE && prec != ADG_FP64)
+    return fail(c, ADG_EUNSUPPORTED, "storage precision other than FP64 is not built");
+  if (prec == ADG_FP16 || prec == ADG_FP8E4M3)
+    return fail(c, ADG_EUNSUPPORTED, "precision not built for this kernel");
+  if ((kernel == ADG_K_PICARD || kernel == ADG_K_PREDICTOR) && prec == ADG_BF16)
+    return fail(c, ADG_EUNSUPPORTED, "bf16 predictor not built");
+  if (kernel == ADG_K_CORRECTOR && prec != c->prec[ADG_K_CORRECTOR]) c->have_bufs = false;
+  c->prec[kernel] = prec;
+  c->flags = flags;
+  return ADG_OK;
+}
+
+int adg_set_numerics(adg_ctx* c, double cfl, int picard_iters) {
+  if (!c) return ADG_EINVAL;
+  if (!(cfl > 0.0)) return fail(c, ADG_EINVAL, "cfl must be > 0");
+  if (picard_iters > 1000) return fail(c, ADG_EINVAL, "picard_iters too large");
+  c->cfl = cfl;
+  c->picard_iters = picard_iters;
+  return ADG_OK;
+}
+
+int adg_state_size(const adg_ctx* c, size_t* ndouble, int* nvar) {
+  if (!c) return ADG_EINVAL;
+  if (!c->have_mesh || !c->have_pde) return ADG_ENOTINIT;
+  if (ndouble) *ndouble = (size_t)c->ncells * c->V * c->NS;
+  if (nvar) *nvar = c->V;
+  return ADG_OK;
+}
+
+int adg_workspace_bytes(const adg_ctx* c, size_t* bytes) {
+  if (!c || !bytes) return ADG_EINVAL;
+  if (!c->have_mesh || !c->have_pde) return ADG_ENOTINIT;
+  *bytes = align256(traces_bytes(c)) + align256(l2_partial_bytes(c));
+  return ADG_OK;
+}
+
+int adg_bind_buffers(adg_ctx* c, double* d_state, void* d_ws, size_t ws_bytes) {
+  if (!c) return ADG_EINVAL;
+  if (!c->have_mesh || !c->have_pde) return fail(c, ADG_ENOTINIT, "mesh and PDE first");
+  if (!d_state || !d_ws) return fail(c, ADG_EINVAL, "null buffer");
+  if (((uintptr_t)d_state & 15) || ((uintptr_t)d_ws & 255))
+    return fail(c, ADG_EINVAL, "state must be 16-byte and workspace 256-byte aligned");
+  size_t need = 0;
+  adg_workspace_bytes(c, &need);
+  if (ws_bytes < need) return fail(c, ADG_ENOMEM, "workspace smaller than adg_workspace_bytes");
+  c->Q = d_state;
+  c->ws = d_ws;
+  c->ws_bytes = ws_bytes;
+  c->have_bufs = true;
+  return ADG_OK;
+}
+
+static int reset_scalars_and_lambda(adg_ctx* c, double t) {
+  DevScalars s{};
+  s.t = t;
+  ADG_CUDA(c, cudaMemcpyAsync(c->sc, &s, sizeof(s), cudaMemcpyHostToDevice, c->stream));
+  StepArgs a;
+  fill_step_args(c, &a);
+  ADG_CUDA(c, c->entry->lambda(a, c->stream));
+  c->have_state = true;
+  return ADG_OK;
+}
+
+int adg_set_initial(adg_ctx* c, int scenario, const double* params, int nparams) {
+  if (!c) return ADG_EINVAL;
+  if (!c->have_bufs || !c->entry) return fail(c, ADG_ENOTINIT, "bind buffers first");
+  if (scenario < ADG_SC_PLANAR || scenario > ADG_SC_GAUSS_PULSE) return fail(c, ADG_EINVAL, "unknown scenario");
+  if (!params || nparams < 1) return fail(c, ADG_EINVAL, "missing scenario parameters");
+  // validate the encodings' lengths
+  int need = 0;
+  if (scenario == ADG_SC_PLANAR) {
+    if (nparams < c->V + 1) return fail(c, ADG_EINVAL, "planar: too few parameters");
+    need = c->V + 1 + (int)params[c->V] * (5 + c->V);
+  } else if (scenario == ADG_SC_EULER_WAVE) {
+    if (c->pde != ADG_EULER) return fail(c, ADG_EINVAL, "euler wave needs the Euler PDE");
+    need = 9;
+  } else if (scenario == ADG_SC_SWE_MODES) {
+    if (c->pde != ADG_SWE) return fail(c, ADG_EINVAL, "swe modes need the SWE PDE");
+    if (nparams < 5) return fail(c, ADG_EINVAL, "swe modes: too few parameters");
+    need = 5 + 4 * (int)params[4];
+  } else {
+    if (c->pde != ADG_ACOUSTIC) return fail(c, ADG_EINVAL, "gauss pulse needs acoustics");
+    need = 5;
+  }
+  if (nparams < need || need < 0) return fail(c, ADG_EINVAL, "scenario: parameter count mismatch");
+  if (c->d_sp_cap < nparams) {
+    if (c->d_sp) cudaFree(c->d_sp);
+    c->d_sp = nullptr;
+    ADG_CUDA(c, cudaMalloc(&c->d_sp, sizeof(double) * nparams));
+    c->d_sp_cap = nparams;
+  }
+  c->sp.assign(params, params + nparams);
+  ADG_CUDA(c, cudaMemcpyAsync(c->d_sp, c->sp.data(), sizeof(double) * nparams, cudaMemcpyHostToDevice,
+                              c->stream));
+  c->scenario = scenario;
+  InitArgs ia;
+  std::memset(&ia, 0, sizeof(ia));
+  ia.Q = c->Q;
+  ia.sp = c->d_sp;
+  ia.scenario = scenario;
+  ia.nsp = nparams;
+  for (int d = 0; d < 3; ++d) {
+    ia.m[d] = c->m[d];
+    ia.lo[d] = c->lo[d];
+    ia.h[d] = c->h[d];
+  }
+  ia.ncells = c->ncells;
+  ia.t = 0.0;
+  ia.tab = c->tab;
+  ia.pp = c->pp;
+  ADG_CUDA(c, c->entry->init(ia, c->stream));
+  // the host copy of the parameters must stay valid until the copy ran
+  ADG_CUDA(c, cudaStreamSynchronize(c->stream));
+  return reset_scalars_and_lambda(c, 0.0);
+}
+
+int adg_set_state(adg_ctx* c, const double* Qin, double t, int from_host) {
+  if (!c) return ADG_EINVAL;
+  if (!c->have_bufs || !c->entry) return fail(c, ADG_ENOTINIT, "bind buffers first");
+  if (!Qin) return fail(c, ADG_EINVAL, "null state");
+  const size_t bytes = sizeof(double) * (size_t)c->ncells * c->V * c->NS;
+  if (Qin != c->Q)
+    ADG_CUDA(c, cudaMemcpyAsync(c->Q, Qin, bytes, from_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                                c->stream));
+  return reset_scalars_and_lambda(c, t);
+}
+
+int adg_get_state(adg_ctx* c, double* Qout, int to_host) {
+  if (!c) return ADG_EINVAL;
+  if (!c->have_state) return fail(c, ADG_ENOTINIT, "no state yet");
+  if (!Qout) return fail(c, ADG_EINVAL, "null output");
+  const size_t bytes = sizeof(double) * (size_t)c->ncells * c->V * c->NS;
+  if (Qout != c->Q)
+    ADG_CUDA(c, cudaMemcpyAsync(Qout, c->Q, bytes, to_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                                c->stream));
+  if (to_host) ADG_CUDA(c, cudaStreamSynchronize(c->stream));
+  return ADG_OK;
+}
+
+static int select_kernels(adg_ctx* c, StepFn* pred, StepFn* corr) {
+  const int pic = c->prec[ADG_K_PICARD], prd = c->prec[ADG_K_PREDICTOR];
+  const int rie = c->prec[ADG_K_RIEMANN], cor = c->prec[ADG_K_CORRECTOR];
+  if (pic != prd) return fail(c, ADG_EUNSUPPORTED, "SIMT predictor needs PICARD == PREDICTOR precision");
+  if (pic > P32 || rie > PBF16 || cor > PBF16) return fail(c, ADG_EUNSUPPORTED, "precision mix not built");
+  *pred = c->entry->predictor[pic][cor];
+  *corr = c->entry->corrector[rie][cor];
+  if (!*pred || !*corr) return fail(c, ADG_EUNSUPPORTED, "precision mix not built for this (PDE, d, N)");
+  return ADG_OK;
+}
+
+int adg_step_async(adg_ctx* c, int nsteps) {
+  if (!c) return ADG_EINVAL;
+  if (!c->have_state) return fail(c, ADG_ENOTINIT, "set an initial state first");
+  if (nsteps < 0) return fail(c, ADG_EINVAL, "nsteps < 0");
+  size_t need = 0;
+  adg_workspace_bytes(c, &need);
+  if (c->ws_bytes < need) return fail(c, ADG_ENOMEM, "workspace too small for this precision");
+  StepFn pred = nullptr, corr = nullptr;
+  int st = select_kernels(c, &pred, &corr);
+  if (st != ADG_OK) return st;
+  StepArgs a;
+  fill_step_args(c, &a);
+  for (int s = 0; s < nsteps; ++s) {
+    ADG_CUDA(c, pred(a, c->stream));
+    ADG_CUDA(c, corr(a, c->stream));
+  }
+  return ADG_OK;
+}
+
+int adg_step(adg_ctx* c, int nsteps, double* t_out, double* dt_last_out) {
+  int st = adg_step_async(c, nsteps);
+  if (st != ADG_OK) return st;
+  DevScalars s;
+  ADG_CUDA(c, cudaMemcpyAsync(&s, c->sc, sizeof(s), cudaMemcpyDeviceToHost, c->stream));
+  ADG_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (t_out) *t_out = s.t;
+  if (dt_last_out) *dt_last_out = s.dt_last;
+  if (s.bad) return fail(c, ADG_ENONFINITE, "non-finite value in the state; t is the last good time");
+  return ADG_OK;
+}
+
+int adg_step_timed(adg_ctx* c, int nsteps, double* t_out, double* ms_kernels) {
+  if (!c) return ADG_EINVAL;
+  if (!c->have_state) return fail(c, ADG_ENOTINIT, "set an initial state first");
+  if (nsteps < 1) return fail(c, ADG_EINVAL, "nsteps < 1");
+  StepFn pred = nullptr, corr = nullptr;
+  int st = select_kernels(c, &pred, &corr);
+  if (st != ADG_OK) return st;
+  StepArgs a;
+  fill_step_args(c, &a);
+  std::vector<cudaEvent_t> ev((size_t)2 * nsteps + 1, nullptr);
+  for (auto& e : ev) {
+    cudaError_t ce = cudaEventCreate(&e);
+    if (ce != cudaSuccess) {
+      for (auto& x : ev)
+        if (x) cudaEventDestroy(x);
+      return cuda_fail(c, ce, "cudaEventCreate");
+    }
+  }
+  int rc = ADG_OK;
+  cudaError_t ce = cudaEventRecord(ev[0], c->stream);
+  for (int s = 0; s < nsteps && ce == cudaSuccess; ++s) {
+    ce = pred(a, c->stream);
+    if (ce == cudaSuccess) ce = cudaEventRecord(ev[2 * s + 1], c->stream);
+    if (ce == cudaSuccess) ce = corr(a, c->stream);
+    if (ce == cudaSuccess) ce = cudaEventRecord(ev[2 * s + 2], c->stream);
+  }
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
+  double sp = 0.0, sc = 0.0;
+  for (int s = 0; s < nsteps && ce == cudaSuccess; ++s) {
+    float a1 = 0.f, a2 = 0.f;
+    ce = cudaEventElapsedTime(&a1, ev[2 * s], ev[2 * s + 1]);
+    if (ce == cudaSuccess) ce = cudaEventElapsedTime(&a2, ev[2 * s + 1], ev[2 * s + 2]);
+    sp += a1;
+    sc += a2;
+  }
+  float tot = 0.f;
+  if (ce == cudaSuccess) ce = cudaEventElapsedTime(&tot, ev[0], ev[2 * nsteps]);
+  for (auto& e : ev) cudaEventDestroy(e);
+  if (ce != cudaSuccess) return cuda_fail(c, ce, "adg_step_timed");
+  if (ms_kernels) {
+    ms_kernels[0] = sp;
+    ms_kernels[1] = sc;
+    ms_kernels[2] = tot;
+  }
+  DevScalars sv;
+  ADG_CUDA(c, cudaMemcpyAsync(&sv, c->sc, sizeof(sv), cudaMemcpyDeviceToHost, c->stream));
+  ADG_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (t_out) *t_out = sv.t;
+  if (sv.bad) rc = fail(c, ADG_ENONFINITE, "non-finite value in the state; t is the last good time");
+  return rc;
+}
+
+int adg_get_time(adg_ctx* c, double* t, double* dt_next) {
+  if (!c) return ADG_EINVAL;
+  if (!c->have_state) return fail(c, ADG_ENOTINIT, "no state yet");
+  DevScalars s;
+  ADG_CUDA(c, cudaMemcpyAsync(&s, c->sc, sizeof(s), cudaMemcpyDeviceToHost, c->stream));
+  ADG_CUDA(c, cudaStreamSynchronize(c->stream));
+  double lam;
+  std::memcpy(&lam, &s.lam_cur, sizeof(lam));
+  double hmin = c->h[0];
+  for (int d = 1; d < c->dim; ++d) hmin = std::min(hmin, c->h[d]);
+  if (t) *t = s.t;
+  if (dt_next) *dt_next = c->cfl * hmin / ((double)c->dim * (2.0 * c->N + 1.0) * lam);
+  if (s.bad) return fail(c, ADG_ENONFINITE, "state has non-finite values");
+  return ADG_OK;
+}
+
+static int run_l2(adg_ctx* c, const double* Qref, double* per, double* tot) {
+  if (!c->have_state) return fail(c, ADG_ENOTINIT, "no state yet");
+  L2Args a;
+  std::memset(&a, 0, sizeof(a));
+  a.Q = c->Q;
+  a.Qref = Qref;
+  a.sp = c->d_sp;
+  a.scenario = c->scenario;
+  a.nsp = (int)c->sp.size();
+  for (int d = 0; d < 3; ++d) {
+    a.m[d] = c->m[d];
+    a.lo[d] = c->lo[d];
+    a.h[d] = c->h[d];
+  }
+  a.ncells = c->ncells;
+  DevScalars s;
+  ADG_CUDA(c, cudaMemcpyAsync(&s, c->sc, sizeof(s), cudaMemcpyDeviceToHost, c->stream));
+  ADG_CUDA(c, cudaStreamSynchronize(c->stream));
+  a.t = s.t;
+  a.partial = (double*)((char*)c->ws + align256(traces_bytes(c)));
+  a.out = c->d_l2;
+  a.tab = c->tab;
+  a.pp = c->pp;
+  int nb = 0;
+  ADG_CUDA(c, c->entry->l2(a, &nb, c->stream));
+  double out[kMaxV + 1];
+  ADG_CUDA(c, cudaMemcpyAsync(out, c->d_l2, sizeof(double) * (c->V + 1), cudaMemcpyDeviceToHost, c->stream));
+  ADG_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (per)
+    for (int v = 0; v < c->V; ++v) per[v] = out[v];
+  if (tot) *tot = out[c->V];
+  return ADG_OK;
+}
+
+int adg_error_vs_exact(adg_ctx* c, double* per, double* tot) {
+  if (!c) return ADG_EINVAL;
+  if (c->scenario < 0) return fail(c, ADG_ENOTINIT, "no scenario set");
+  if ((c->scenario == ADG_SC_SWE_MODES || c->scenario == ADG_SC_GAUSS_PULSE)) {
+    DevScalars s;
+    ADG_CUDA(c, cudaMemcpyAsync(&s, c->sc, sizeof(s), cudaMemcpyDeviceToHost, c->stream));
+    ADG_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (s.t != 0.0) return fail(c, ADG_EUNSUPPORTED, "scenario has no closed form for t > 0");
+  }
+  return run_l2(c, nullptr, per, tot);
+}
+
+int adg_l2_diff(adg_ctx* c, const double* d_Qref, double* per, double* tot) {
+  if (!c) return ADG_EINVAL;
+  if (!d_Qref) return fail(c, ADG_EINVAL, "null reference state");
+  return run_l2(c, d_Qref, per, tot);
+}
+
+}  // extern "C"

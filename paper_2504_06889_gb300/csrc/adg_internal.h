@@ -1,0 +1,108 @@
+// Internal types shared by the host API and the kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace adg {
+
+constexpr int kMaxN1 = 8;  // n = N+1 <= 8
+constexpr int kMaxV = 9;
+
+enum Prec { P64 = 0, P32 = 1, PBF16 = 2, PF16 = 3, PF8 = 4 };
+
+// 1D operators on the reference interval [0,1] (Sec. 2), in FP64.
+struct Tables {
+  int n;
+  double xi[kMaxN1], w[kMaxN1], psi0[kMaxN1], psi1[kMaxN1];
+  double D[kMaxN1][kMaxN1];   // D[a][b] = psi_b'(xi_a)
+  double P[kMaxN1][kMaxN1];   // P = K1^{-1} diag(w): Picard update q = Q - dt P R
+  double Vm[kMaxN1][kMaxN1];  // Vm[i][m] = w_m D[m][i] / w_i: mass-inverted volume operator
+};
+
+// PDE parameters (acoustic rho,K; elastic rho,cp,cs; euler gamma; swe g)
+struct PdeParams {
+  int pde;
+  double rho, K, cp, cs, lam, mu, gamma, g;
+  const double* cell_c;  // optional per-cell acoustic wave speed (device), K = rho c^2
+};
+
+// Device-resident step scalars (owned by the context).
+struct DevScalars {
+  unsigned long long lam_cur;   // bits of lambda_max(Q^n)   (>= 0, so integer order = value order)
+  unsigned long long lam_next;  // bits of lambda_max(Q^{n+1}) being reduced
+  double t;                     // time after the last good step
+  double dt_last;               // dt of the last good step
+  unsigned int counter;         // blocks of the corrector that have finished
+  unsigned int nonfinite;       // set by a corrector block that saw Inf/NaN this step
+  unsigned int bad;             // latched by the last corrector block: stop advancing
+  unsigned int steps;           // good steps taken since the state was set
+};
+
+struct StepArgs {
+  double* Q;          // state [cells][V][NS]
+  void* traces;       // [cells][D][2 sides][2 (Qbar, Fbar.n)][V][NF] in the corrector precision
+  DevScalars* sc;
+  int m[3];
+  int ncells;
+  double invh[3];
+  double hmin;
+  double cfl;
+  int picard_iters;
+  int pad;
+  Tables tab;
+  PdeParams pp;
+};
+
+struct InitArgs {
+  double* Q;
+  const double* sp;  // scenario parameters (device)
+  int scenario;
+  int nsp;
+  int m[3];
+  int ncells;
+  double lo[3], h[3];
+  double t;
+  Tables tab;
+  PdeParams pp;
+};
+
+struct L2Args {
+  const double* Q;
+  const double* Qref;  // null: compare with the scenario's closed form
+  const double* sp;
+  int scenario;
+  int nsp;
+  int m[3];
+  int ncells;
+  double lo[3], h[3];
+  double t;
+  double* partial;  // [blocks][V]
+  double* out;      // [V+1]
+  Tables tab;
+  PdeParams pp;
+};
+
+using StepFn = cudaError_t (*)(const StepArgs&, cudaStream_t);
+using InitFn = cudaError_t (*)(const InitArgs&, cudaStream_t);
+using L2Fn = cudaError_t (*)(const L2Args&, int* nblocks, cudaStream_t);
+using LamFn = cudaError_t (*)(const StepArgs&, cudaStream_t);
+
+// Kernels built for one (PDE, d, N).  Indices: [picard/predictor prec][trace prec]
+// and [riemann prec][corrector prec] over {P64, P32, PBF16}; null = not built.
+struct Entry {
+  int pde, dim, N;
+  int V, NS, NF;
+  StepFn predictor[3][3];
+  StepFn corrector[3][3];
+  LamFn lambda;
+  InitFn init;
+  L2Fn l2;
+  int l2_blocks_per_cell_group;  // cells per block of the L2 kernel
+};
+
+void register_entry(const Entry& e);
+const Entry* find_entry(int pde, int dim, int N);
+
+}  // namespace adg

@@ -1,0 +1,692 @@
+// SIMT kernels of the ADER-DG step (arXiv 2504.06889, Sec. 2 and Algorithm 1), templated on
+// the PDE, the dimension d, the order N and the per-kernel precisions.
+//
+//  k_predictor   one thread per spatial node of a cell; the thread keeps its node's space-time
+//                column q[k][v] (all time nodes) in registers.  Per Picard sweep and time slice k
+//                the pointwise fluxes go to shared memory in a pencil layout (the n values along
+//                each direction contiguous), each thread contracts its three pencils with the 1D
+//                derivative matrix, and applies the time operator P = K1^-1 diag(w) to its own
+//                column in registers (eq. Picard: q = Q - dt P R).  The final sweep's fluxes are
+//                time-averaged; the volume integral updates Q in FP64 and the face traces of
+//                Qbar and Fbar.n are written in the corrector precision.
+//  k_corrector   per cell: Rusanov fluxes on its 2d faces from its own and its neighbours'
+//                traces (one speed per face, eq. rusanov_flux), the surface integral, the FP64
+//                update of eq. (weak_form_volume_surface), lambda_max(Q^{n+1}) for the next
+//                dt (eq. CFL_condition) and the end-of-step bookkeeping by the last block.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "adg_internal.h"
+#include "adg_physics.cuh"
+
+namespace adg {
+
+template <int PDE_, int D_, int N_> struct Cfg {
+  static constexpr int PDE = PDE_, D = D_, N = N_, n = N_ + 1;
+  static constexpr int NS = ipow_c(n, D), NF = ipow_c(n, D - 1), V = nvar_c(PDE_, D_);
+  static constexpr int CPB = NS >= 96 ? 1 : (128 / NS);  // cells per block
+  static constexpr int THREADS = CPB * NS;
+};
+
+// node index of face node j with coordinate a along dir (inverse of the face index)
+template <int D, int n> __device__ __forceinline__ int node_of_face(int dir, int j, int a) {
+  if (D == 2) return dir == 0 ? a + n * j : j + n * a;
+  if (dir == 0) return a + n * j;
+  if (dir == 1) return (j % n) + n * (a + n * (j / n));
+  return j + n * n * a;
+}
+
+__device__ __forceinline__ double dt_from(const StepArgs& a, int D, int N) {
+  const double lam = __longlong_as_double((long long)a.sc->lam_cur);
+  return a.cfl * a.hmin / ((double)D * (2.0 * N + 1.0) * lam);
+}
+
+__device__ __forceinline__ int neighbour(const StepArgs& a, int c, int dir, int side) {
+  int cc[3] = {c % a.m[0], (c / a.m[0]) % a.m[1], c / (a.m[0] * a.m[1])};
+  cc[dir] += side ? 1 : -1;
+  if (cc[dir] < 0) cc[dir] += a.m[dir];
+  if (cc[dir] >= a.m[dir]) cc[dir] -= a.m[dir];
+  return cc[0] + a.m[0] * (cc[1] + a.m[1] * cc[2]);
+}
+
+template <class C, class T, class TP> struct PredSmem {
+  static constexpr size_t sweep = sizeof(T) * C::CPB * C::D * C::V * C::NS;
+  static constexpr size_t fin = sizeof(TP) * C::CPB * (C::D + 1) * C::V * C::NS;
+  static constexpr size_t big = ((sweep > fin ? sweep : fin) + 15) / 16 * 16;
+  static constexpr size_t tables = sizeof(T) * 2 * C::n * C::n + sizeof(TP) * (C::n * C::n + 3 * C::n);
+  static constexpr size_t total = big + tables;
+};
+
+// ------------------------------------------------------------------------------------------------
+// predictor + volume integral + face traces
+// ------------------------------------------------------------------------------------------------
+template <class C, class T, class TP, class TS>
+__global__ void __launch_bounds__(C::THREADS) k_predictor(const __grid_constant__ StepArgs a) {
+  using Ph = Phys<C::PDE, C::D>;
+  constexpr int n = C::n, V = C::V, D = C::D, NS = C::NS, NF = C::NF, CPB = C::CPB;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (a.sc->bad) return;
+  const double dt = dt_from(a, D, C::N);
+
+  // tables: dtP (T), D (T), Vm (TP), w, psi0, psi1 (TP)
+  T* sD = reinterpret_cast<T*>(smem_raw + PredSmem<C, T, TP>::big);
+  T* sdtP = sD + n * n;
+  TP* sVm = reinterpret_cast<TP*>(sdtP + n * n);
+  TP* sw = sVm + n * n;
+  TP* sp0 = sw + n;
+  TP* sp1 = sp0 + n;
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    const int r = t / n, cidx = t % n;
+    sD[t] = (T)a.tab.D[r][cidx];
+    sdtP[t] = (T)(dt * a.tab.P[r][cidx]);
+    sVm[t] = (TP)a.tab.Vm[r][cidx];
+  }
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    sw[t] = (TP)a.tab.w[t];
+    sp0[t] = (TP)a.tab.psi0[t];
+    sp1[t] = (TP)a.tab.psi1[t];
+  }
+
+  const int lc = threadIdx.x / NS, i = threadIdx.x % NS;
+  const int cell = blockIdx.x * CPB + lc;
+  const bool valid = cell < a.ncells;
+  const int cl = valid ? cell : 0;
+
+  int idx[3] = {i % n, (i / n) % n, i / (n * n)};
+  int pb[3];  // start of this node's pencil along dir in the pencil layout
+  pb[0] = (i / n) * n;
+  if (D == 2) {
+    pb[1] = idx[0] * n;
+  } else {
+    pb[1] = (idx[0] + n * idx[2]) * n;
+    pb[2] = (idx[0] + n * idx[1]) * n;
+  }
+  const T invh[3] = {(T)a.invh[0], (T)a.invh[1], (T)a.invh[2]};
+  const PP<T> pp = make_pp<T>(a.pp, cl);
+
+  T Qh[V];
+  const double* Qc = a.Q + (size_t)cl * V * NS;
+#pragma unroll
+  for (int v = 0; v < V; ++v) Qh[v] = (T)Qc[v * NS + i];
+
+  T* sF = reinterpret_cast<T*>(smem_raw) + (size_t)lc * D * V * NS;  // [dir][v][pencil layout]
+
+  T q[n][V];
+#pragma unroll
+  for (int k = 0; k < n; ++k)
+#pragma unroll
+    for (int v = 0; v < V; ++v) q[k][v] = Qh[v];
+
+  __syncthreads();
+  for (int r = 0; r < a.picard_iters; ++r) {
+    T qn[n][V];
+#pragma unroll
+    for (int k = 0; k < n; ++k)
+#pragma unroll
+      for (int v = 0; v < V; ++v) qn[k][v] = Qh[v];
+#pragma unroll
+    for (int k = 0; k < n; ++k) {
+      T F[D][V];
+      Ph::flux(pp, q[k], F);
+#pragma unroll
+      for (int dir = 0; dir < D; ++dir)
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+          if (Ph::nz(dir, v)) sF[(dir * V + v) * NS + pb[dir] + idx[dir]] = F[dir][v];
+      __syncthreads();
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        T rv = T(0);
+#pragma unroll
+        for (int dir = 0; dir < D; ++dir) {
+          if (!Ph::nz(dir, v)) continue;
+          const T* Fp = sF + (dir * V + v) * NS + pb[dir];
+          const T* Dr = sD + idx[dir] * n;
+          T s = T(0);
+#pragma unroll
+          for (int m = 0; m < n; ++m) s += Dr[m] * Fp[m];
+          rv += s * invh[dir];
+        }
+        // q_new[kk] = Q - dt sum_l P[kk][l] R_l  (column l = k)
+#pragma unroll
+        for (int kk = 0; kk < n; ++kk) qn[kk][v] -= sdtP[kk * n + k] * rv;
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int k = 0; k < n; ++k)
+#pragma unroll
+      for (int v = 0; v < V; ++v) q[k][v] = qn[k][v];
+  }
+
+  // ---- final flux, time averages (Qbar = sum_k w_k q_k, Fbar = sum_k w_k F(q_k)) ---------------
+  const PP<TP> ppP = make_pp<TP>(a.pp, cl);
+  TP Fb[D][V], Qb[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    Qb[v] = TP(0);
+#pragma unroll
+    for (int dir = 0; dir < D; ++dir) Fb[dir][v] = TP(0);
+  }
+#pragma unroll
+  for (int k = 0; k < n; ++k) {
+    TP qk[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) qk[v] = (TP)q[k][v];
+    TP F[D][V];
+    Ph::flux(ppP, qk, F);
+    const TP wk = sw[k];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      Qb[v] += wk * qk[v];
+#pragma unroll
+      for (int dir = 0; dir < D; ++dir) Fb[dir][v] += wk * F[dir][v];
+    }
+  }
+  // shared: Fbar [dir][v][pencil layout], Qbar [v][node]
+  TP* sFb = reinterpret_cast<TP*>(smem_raw) + (size_t)lc * (D + 1) * V * NS;
+  TP* sQb = sFb + D * V * NS;
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    sQb[v * NS + i] = Qb[v];
+#pragma unroll
+    for (int dir = 0; dir < D; ++dir)
+      if (Ph::nz(dir, v)) sFb[(dir * V + v) * NS + pb[dir] + idx[dir]] = Fb[dir][v];
+  }
+  __syncthreads();
+
+  // ---- volume integral: Q_i += dt sum_dir (1/h_dir) sum_m Vm[i_dir][m] Fbar(i[dir<-m]) --------
+  if (valid) {
+    double* Qw = a.Q + (size_t)cell * V * NS;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      TP vol = TP(0);
+#pragma unroll
+      for (int dir = 0; dir < D; ++dir) {
+        if (!Ph::nz(dir, v)) continue;
+        const TP* Fp = sFb + (dir * V + v) * NS + pb[dir];
+        const TP* Vr = sVm + idx[dir] * n;
+        TP s = TP(0);
+#pragma unroll
+        for (int m = 0; m < n; ++m) s += Vr[m] * Fp[m];
+        vol += s * (TP)a.invh[dir];
+      }
+      Qw[v * NS + i] += dt * (double)vol;
+    }
+  }
+
+  // ---- face traces: trace(dir, side)_j = sum_a psi_a(side) X(node(dir, j, a)) ------------------
+  if (valid) {
+    TS* tr = reinterpret_cast<TS*>(a.traces) + (size_t)cell * D * 2 * 2 * V * NF;
+    constexpr int items = D * 2 * 2 * V * NF;
+    for (int it = i; it < items; it += NS) {
+      const int j = it % NF;
+      const int v = (it / NF) % V;
+      const int qf = (it / (NF * V)) % 2;
+      const int side = (it / (NF * V * 2)) % 2;
+      const int dir = it / (NF * V * 4);
+      const TP* psi = side ? sp1 : sp0;
+      TP s = TP(0);
+      if (qf == 0) {
+#pragma unroll
+        for (int m = 0; m < n; ++m) s += psi[m] * sQb[v * NS + node_of_face<D, n>(dir, j, m)];
+      } else {
+        bool nzv = false;
+#pragma unroll
+        for (int dd = 0; dd < D; ++dd)
+          if (dd == dir) nzv = Ph::nz(dd, v);
+        if (nzv) {
+          const TP* Fp = sFb + (dir * V + v) * NS + j * n;
+#pragma unroll
+          for (int m = 0; m < n; ++m) s += psi[m] * Fp[m];
+        }
+      }
+      tr[it] = (TS)s;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Riemann + surface integral + FP64 corrector + lambda_max for the next dt
+// ------------------------------------------------------------------------------------------------
+template <class C, class TR, class TC> struct CorrSmem {
+  // traces of both sides for 2d faces: [2d][2 (minus, plus)][2 (Q, F)][V][NF] in TR,
+  // G: [2d][V][NF] in TC, speeds [2d][NF] in TR
+  static constexpr size_t tr = sizeof(TR) * C::CPB * 2 * C::D * 4 * C::V * C::NF;
+  static constexpr size_t g = sizeof(TC) * C::CPB * 2 * C::D * C::V * C::NF;
+  static constexpr size_t sp = sizeof(TR) * C::CPB * 2 * C::D * C::NF;
+  static constexpr size_t total = tr + g + sp + 64;
+};
+
+template <class C, class TR, class TC, class TS>
+__global__ void __launch_bounds__(C::THREADS) k_corrector(const __grid_constant__ StepArgs a) {
+  using Ph = Phys<C::PDE, C::D>;
+  constexpr int n = C::n, V = C::V, D = C::D, NS = C::NS, NF = C::NF, CPB = C::CPB;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ unsigned long long s_lam;
+  __shared__ unsigned int s_bad, s_last;
+  if (a.sc->bad) return;
+  const double dt = dt_from(a, D, C::N);
+  if (threadIdx.x == 0) {
+    s_lam = 0ull;
+    s_bad = 0u;
+  }
+
+  const int lc = threadIdx.x / NS, i = threadIdx.x % NS;
+  const int cell = blockIdx.x * CPB + lc;
+  const bool valid = cell < a.ncells;
+  const int cl = valid ? cell : 0;
+
+  TR* sT = reinterpret_cast<TR*>(smem_raw) + (size_t)lc * 2 * D * 4 * V * NF;
+  TC* sG = reinterpret_cast<TC*>(smem_raw + CorrSmem<C, TR, TC>::tr) + (size_t)lc * 2 * D * V * NF;
+  TR* sS = reinterpret_cast<TR*>(smem_raw + CorrSmem<C, TR, TC>::tr + CorrSmem<C, TR, TC>::g) +
+           (size_t)lc * 2 * D * NF;
+
+  const TS* trc = reinterpret_cast<const TS*>(a.traces);
+  constexpr size_t cellsz = (size_t)D * 2 * 2 * V * NF;
+
+  // load both sides of the 2d faces: face f = 2 dir + side; minus = left cell's side-1 trace,
+  // plus = right cell's side-0 trace
+  for (int it = i; it < 2 * D * 2 * 2 * V * NF; it += NS) {
+    const int j = it % NF;
+    const int v = (it / NF) % V;
+    const int qf = (it / (NF * V)) % 2;
+    const int pm = (it / (NF * V * 2)) % 2;  // 0 minus, 1 plus
+    const int f = it / (NF * V * 4);
+    const int dir = f / 2, side = f % 2;
+    // right face (side 1): minus = own side 1, plus = right neighbour side 0
+    // left face  (side 0): minus = left neighbour side 1, plus = own side 0
+    const bool own = (side == 1) ? (pm == 0) : (pm == 1);
+    const int src = own ? cl : neighbour(a, cl, dir, side);
+    const int sside = pm == 0 ? 1 : 0;
+    const TS val = trc[(size_t)src * cellsz + (((dir * 2 + sside) * 2 + qf) * V + v) * NF + j];
+    sT[it] = tcast<TR>(todouble(val));
+  }
+  __syncthreads();
+  const PP<TR> ppL = make_pp<TR>(a.pp, cl);
+  // speed at every face node on both sides (the neighbour's material for its side)
+  for (int it = i; it < 2 * D * NF; it += NS) {
+    const int j = it % NF, f = it / NF, dir = f / 2, side = f % 2;
+    TR qm[V], qp[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      qm[v] = sT[(((f * 2 + 0) * 2 + 0) * V + v) * NF + j];
+      qp[v] = sT[(((f * 2 + 1) * 2 + 0) * V + v) * NF + j];
+    }
+    const int nb = neighbour(a, cl, dir, side);
+    const PP<TR> ppN = make_pp<TR>(a.pp, nb);
+    const TR sm = side ? Ph::speed(ppL, qm, dir) : Ph::speed(ppN, qm, dir);
+    const TR sp = side ? Ph::speed(ppN, qp, dir) : Ph::speed(ppL, qp, dir);
+    sS[it] = tmax(sm, sp);
+  }
+  __syncthreads();
+  // Rusanov: G = (Fm + Fp)/2 + s/2 (qm - qp), s = max over the face's nodes
+  for (int it = i; it < 2 * D * V * NF; it += NS) {
+    const int j = it % NF, v = (it / NF) % V, f = it / (NF * V);
+    TR s = sS[f * NF];
+    for (int jj = 1; jj < NF; ++jj) s = tmax(s, sS[f * NF + jj]);
+    const TR qm = sT[(((f * 2 + 0) * 2 + 0) * V + v) * NF + j];
+    const TR qp = sT[(((f * 2 + 1) * 2 + 0) * V + v) * NF + j];
+    const TR Fm = sT[(((f * 2 + 0) * 2 + 1) * V + v) * NF + j];
+    const TR Fp = sT[(((f * 2 + 1) * 2 + 1) * V + v) * NF + j];
+    const TR half = tcast<TR>(0.5);
+    const TR G = half * (Fm + Fp) + half * s * (qm - qp);
+    sG[it] = tcast<TC>(todouble(G));
+  }
+  __syncthreads();
+
+  // surface integral and update: Q_i -= dt sum_dir (1/h)(psi1[i_dir] G+ - psi0[i_dir] G-)/w[i_dir]
+  double lam = 0.0;
+  bool bad = false;
+  if (valid) {
+    const int idx[3] = {i % n, (i / n) % n, i / (n * n)};
+    int jf[3];
+    if (D == 2) {
+      jf[0] = idx[1];
+      jf[1] = idx[0];
+    } else {
+      jf[0] = idx[1] + n * idx[2];
+      jf[1] = idx[0] + n * idx[2];
+      jf[2] = idx[0] + n * idx[1];
+    }
+    double* Qw = a.Q + (size_t)cell * V * NS;
+    double qnew[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      TC surf = tcast<TC>(0.0);
+#pragma unroll
+      for (int dir = 0; dir < D; ++dir) {
+        const int id = idx[dir];
+        const TC gp = sG[((2 * dir + 1) * V + v) * NF + jf[dir]];
+        const TC gm = sG[((2 * dir + 0) * V + v) * NF + jf[dir]];
+        const TC c1 = tcast<TC>(a.tab.psi1[id] * a.invh[dir] / a.tab.w[id]);
+        const TC c0 = tcast<TC>(a.tab.psi0[id] * a.invh[dir] / a.tab.w[id]);
+        surf += c1 * gp - c0 * gm;
+      }
+      const double qv = Qw[v * NS + i] - dt * todouble(surf);
+      Qw[v * NS + i] = qv;
+      qnew[v] = qv;
+      bad |= !isfinite(qv);
+    }
+    const PP<double> pd = make_pp<double>(a.pp, cell);
+#pragma unroll
+    for (int dir = 0; dir < D; ++dir) lam = fmax(lam, Ph::speed(pd, qnew, dir));
+    bad |= !isfinite(lam);
+  }
+  // block max of lambda (non-negative doubles order like their bit patterns)
+  __syncthreads();
+  if (valid && !bad) atomicMax(&s_lam, (unsigned long long)__double_as_longlong(lam));
+  if (bad) atomicOr(&s_bad, 1u);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    atomicMax(&a.sc->lam_next, s_lam);
+    if (s_bad) atomicOr(&a.sc->nonfinite, 1u);
+    __threadfence();
+    const unsigned prev = atomicAdd(&a.sc->counter, 1u);
+    s_last = (prev == gridDim.x - 1) ? 1u : 0u;
+  }
+  __syncthreads();
+  if (s_last && threadIdx.x == 0) {
+    __threadfence();
+    volatile DevScalars* sc = a.sc;
+    if (sc->nonfinite) {
+      sc->bad = 1u;
+    } else {
+      sc->t = sc->t + dt;
+      sc->dt_last = dt;
+      sc->lam_cur = sc->lam_next;
+      sc->steps = sc->steps + 1u;
+    }
+    sc->lam_next = 0ull;
+    sc->counter = 0u;
+    __threadfence();
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// lambda_max(Q) for the first dt after the state was set
+// ------------------------------------------------------------------------------------------------
+template <class C>
+__global__ void k_lambda(const __grid_constant__ StepArgs a) {
+  using Ph = Phys<C::PDE, C::D>;
+  constexpr int V = C::V, NS = C::NS, D = C::D;
+  __shared__ unsigned long long s_lam;
+  __shared__ unsigned int s_bad;
+  if (threadIdx.x == 0) {
+    s_lam = 0ull;
+    s_bad = 0u;
+  }
+  __syncthreads();
+  double lam = 0.0;
+  bool bad = false;
+  const size_t total = (size_t)a.ncells * NS;
+  for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < total;
+       g += (size_t)gridDim.x * blockDim.x) {
+    const int cell = (int)(g / NS), i = (int)(g % NS);
+    double q[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      q[v] = a.Q[((size_t)cell * V + v) * NS + i];
+      bad |= !isfinite(q[v]);
+    }
+    const PP<double> pd = make_pp<double>(a.pp, cell);
+#pragma unroll
+    for (int dir = 0; dir < D; ++dir) lam = fmax(lam, Ph::speed(pd, q, dir));
+  }
+  bad |= !isfinite(lam);
+  if (!bad) atomicMax(&s_lam, (unsigned long long)__double_as_longlong(lam));
+  else atomicOr(&s_bad, 1u);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    atomicMax(&a.sc->lam_cur, s_lam);
+    if (s_bad) atomicOr(&a.sc->bad, 1u);
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// scenario closed forms (shared by the initial interpolation and the L2 error)
+// ------------------------------------------------------------------------------------------------
+template <int PDE, int D, int V>
+__device__ void exact_solution(int scen, const double* sp, const PdeParams& pp, const double* x,
+                               const double* L, double t, double* Q) {
+#pragma unroll
+  for (int v = 0; v < V; ++v) Q[v] = 0.0;
+  if (scen == 0) {  // planar waves
+#pragma unroll
+    for (int v = 0; v < V; ++v) Q[v] = sp[v];
+    const int nw = (int)sp[V];
+    const double* p = sp + V + 1;
+    for (int w = 0; w < nw; ++w, p += 5 + V) {
+      double ph = -p[4] * t;
+#pragma unroll
+      for (int d = 0; d < D; ++d) ph += p[1 + d] * x[d];
+      const double s = p[0] * sin(ph);
+#pragma unroll
+      for (int v = 0; v < V; ++v) Q[v] += s * p[5 + v];
+    }
+  } else if (scen == 1) {  // Euler density wave
+    double ph = 0.0, u2 = 0.0;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      ph += sp[2 + d] * (x[d] - sp[5 + d] * t);
+      u2 += sp[5 + d] * sp[5 + d];
+    }
+    const double rho = sp[0] + sp[1] * sin(ph);
+    Q[0] = rho;
+#pragma unroll
+    for (int d = 0; d < D; ++d) Q[1 + d] = rho * sp[5 + d];
+    Q[1 + D] = sp[8] / (pp.gamma - 1.0) + 0.5 * rho * u2;
+  } else if (scen == 2) {  // shallow water at rest with modes
+    double h = sp[0] + sp[1] * sin(sp[2] * x[0]) * sin(sp[3] * x[1]);
+    const int nm = (int)sp[4];
+    for (int j = 0; j < nm; ++j) h += sp[5 + 4 * j] * sin(sp[6 + 4 * j] * x[0] + sp[7 + 4 * j] * x[1] + sp[8 + 4 * j]);
+    Q[0] = h;
+  } else if (scen == 3) {  // Gaussian pressure pulse, periodic distance
+    double r2 = 0.0;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      double dx = x[d] - sp[d];
+      dx -= L[d] * floor(dx / L[d] + 0.5);
+      r2 += dx * dx;
+    }
+    Q[0] = sp[4] * exp(-r2 / (2.0 * sp[3] * sp[3]));
+  }
+}
+
+template <class C>
+__global__ void k_init(const __grid_constant__ InitArgs a) {
+  constexpr int V = C::V, NS = C::NS, D = C::D, n = C::n;
+  const size_t total = (size_t)a.ncells * NS;
+  for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < total;
+       g += (size_t)gridDim.x * blockDim.x) {
+    const int cell = (int)(g / NS), i = (int)(g % NS);
+    const int cc[3] = {cell % a.m[0], (cell / a.m[0]) % a.m[1], cell / (a.m[0] * a.m[1])};
+    const int ii[3] = {i % n, (i / n) % n, i / (n * n)};
+    double x[3], L[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      x[d] = d < D ? a.lo[d] + (cc[d] + a.tab.xi[ii[d]]) * a.h[d] : 0.0;
+      L[d] = a.h[d] * a.m[d];
+    }
+    double Q[V];
+    exact_solution<C::PDE, D, V>(a.scenario, a.sp, a.pp, x, L, a.t, Q);
+#pragma unroll
+    for (int v = 0; v < V; ++v) a.Q[((size_t)cell * V + v) * NS + i] = Q[v];
+  }
+}
+
+// eq. (L2gauss): per-block partial sums of V_c w_i (Q* - Q_h)^2 per variable, then one block sums
+// the partials in block order (deterministic).
+constexpr int kL2Threads = 256;
+
+template <class C>
+__global__ void __launch_bounds__(kL2Threads) k_l2_partial(const __grid_constant__ L2Args a) {
+  constexpr int V = C::V, NS = C::NS, D = C::D, n = C::n;
+  __shared__ double s_acc[kL2Threads / 32][V];
+  double acc[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) acc[v] = 0.0;
+  double Vc = 1.0;
+#pragma unroll
+  for (int d = 0; d < D; ++d) Vc *= a.h[d];
+  const size_t total = (size_t)a.ncells * NS;
+  for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < total;
+       g += (size_t)gridDim.x * blockDim.x) {
+    const int cell = (int)(g / NS), i = (int)(g % NS);
+    const int ii[3] = {i % n, (i / n) % n, i / (n * n)};
+    double W = Vc;
+#pragma unroll
+    for (int d = 0; d < D; ++d) W *= a.tab.w[ii[d]];
+    double Qe[V];
+    if (a.Qref) {
+#pragma unroll
+      for (int v = 0; v < V; ++v) Qe[v] = a.Qref[((size_t)cell * V + v) * NS + i];
+    } else {
+      const int cc[3] = {cell % a.m[0], (cell / a.m[0]) % a.m[1], cell / (a.m[0] * a.m[1])};
+      double x[3], L[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        x[d] = d < D ? a.lo[d] + (cc[d] + a.tab.xi[ii[d]]) * a.h[d] : 0.0;
+        L[d] = a.h[d] * a.m[d];
+      }
+      exact_solution<C::PDE, D, V>(a.scenario, a.sp, a.pp, x, L, a.t, Qe);
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const double e = Qe[v] - a.Q[((size_t)cell * V + v) * NS + i];
+      acc[v] += W * e * e;
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < V; ++v)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc[v] += __shfl_down_sync(0xffffffffu, acc[v], o);
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+  if (lane == 0)
+#pragma unroll
+    for (int v = 0; v < V; ++v) s_acc[warp][v] = acc[v];
+  __syncthreads();
+  if (threadIdx.x < V) {
+    double s = 0.0;
+    for (int w = 0; w < kL2Threads / 32; ++w) s += s_acc[w][threadIdx.x];
+    a.partial[(size_t)blockIdx.x * V + threadIdx.x] = s;
+  }
+}
+
+template <int V>
+__global__ void k_l2_final(const double* partial, int nblocks, double* out) {
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int v = 0; v < V; ++v) {
+      double s = 0.0;
+      for (int b = 0; b < nblocks; ++b) s += partial[(size_t)b * V + v];
+      out[v] = sqrt(s);
+      tot += s;
+    }
+    out[V] = sqrt(tot);
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// launchers
+// ------------------------------------------------------------------------------------------------
+template <class C, class T, class TP, class TS>
+cudaError_t launch_predictor(const StepArgs& a, cudaStream_t s) {
+  const size_t smem = PredSmem<C, T, TP>::total;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_predictor<C, T, TP, TS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int blocks = (a.ncells + C::CPB - 1) / C::CPB;
+  k_predictor<C, T, TP, TS><<<blocks, C::THREADS, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <class C, class TR, class TC, class TS>
+cudaError_t launch_corrector(const StepArgs& a, cudaStream_t s) {
+  const size_t smem = CorrSmem<C, TR, TC>::total;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_corrector<C, TR, TC, TS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int blocks = (a.ncells + C::CPB - 1) / C::CPB;
+  k_corrector<C, TR, TC, TS><<<blocks, C::THREADS, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <class C>
+cudaError_t launch_lambda(const StepArgs& a, cudaStream_t s) {
+  const size_t total = (size_t)a.ncells * C::NS;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  k_lambda<C><<<blocks, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <class C>
+cudaError_t launch_init(const InitArgs& a, cudaStream_t s) {
+  const size_t total = (size_t)a.ncells * C::NS;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_init<C><<<blocks, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+constexpr int kL2Blocks = 152 * 4;
+
+template <class C>
+cudaError_t launch_l2(const L2Args& a, int* nblocks, cudaStream_t s) {
+  const size_t total = (size_t)a.ncells * C::NS;
+  int blocks = (int)((total + kL2Threads - 1) / kL2Threads);
+  if (blocks > kL2Blocks) blocks = kL2Blocks;
+  if (nblocks) *nblocks = blocks;
+  k_l2_partial<C><<<blocks, kL2Threads, 0, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_l2_final<C::V><<<1, 32, 0, s>>>(a.partial, blocks, a.out);
+  return cudaGetLastError();
+}
+
+// Fill an Entry with the SIMT kernels for one (PDE, d, N).  with_bf16: also build bf16 traces
+// and bf16 Riemann/corrector arithmetic (used for the per-kernel precision sweep).
+template <int PDE, int D, int N, bool with_bf16>
+Entry make_entry() {
+  using C = Cfg<PDE, D, N>;
+  Entry e{};
+  e.pde = PDE;
+  e.dim = D;
+  e.N = N;
+  e.V = C::V;
+  e.NS = C::NS;
+  e.NF = C::NF;
+  e.predictor[P64][P64] = launch_predictor<C, double, double, double>;
+  e.predictor[P64][P32] = launch_predictor<C, double, double, float>;
+  e.predictor[P32][P64] = launch_predictor<C, float, float, double>;
+  e.predictor[P32][P32] = launch_predictor<C, float, float, float>;
+  e.corrector[P64][P64] = launch_corrector<C, double, double, double>;
+  e.corrector[P32][P32] = launch_corrector<C, float, float, float>;
+  e.corrector[P64][P32] = launch_corrector<C, double, float, float>;
+  e.corrector[P32][P64] = launch_corrector<C, float, double, double>;
+  if constexpr (with_bf16) {
+    e.predictor[P64][PBF16] = launch_predictor<C, double, double, __nv_bfloat16>;
+    e.predictor[P32][PBF16] = launch_predictor<C, float, float, __nv_bfloat16>;
+    e.corrector[PBF16][PBF16] = launch_corrector<C, __nv_bfloat16, __nv_bfloat16, __nv_bfloat16>;
+    e.corrector[P64][PBF16] = launch_corrector<C, double, __nv_bfloat16, __nv_bfloat16>;
+    e.corrector[P32][PBF16] = launch_corrector<C, float, __nv_bfloat16, __nv_bfloat16>;
+    e.corrector[PBF16][P64] = launch_corrector<C, __nv_bfloat16, double, double>;
+    e.corrector[PBF16][P32] = launch_corrector<C, __nv_bfloat16, float, float>;
+  }
+  e.lambda = launch_lambda<C>;
+  e.init = launch_init<C>;
+  e.l2 = launch_l2<C>;
+  return e;
+}
+
+}  // namespace adg

@@ -1,0 +1,205 @@
+// Pointwise physics of Sec. 4 of arXiv 2504.06889 for the CUDA kernels:
+// fluxes F_dir(q) for all directions at once, and the spectral radius of dF_dir/dq.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "adg_internal.h"
+
+namespace adg {
+
+constexpr int ipow_c(int b, int e) { return e == 0 ? 1 : b * ipow_c(b, e - 1); }
+constexpr int nvar_c(int pde, int d) {
+  return pde == 0 ? 1 + d : pde == 1 ? (d == 3 ? 9 : 5) : pde == 2 ? 2 + d : 3;
+}
+
+// Arithmetic helpers that also work for bf16 (computed with bf16 rounding per op).
+template <class T> __device__ __forceinline__ T tcast(double x) { return (T)x; }
+template <> __device__ __forceinline__ __nv_bfloat16 tcast<__nv_bfloat16>(double x) {
+  return __double2bfloat16(x);
+}
+template <class T> __device__ __forceinline__ double todouble(T x) { return (double)x; }
+template <> __device__ __forceinline__ double todouble<__nv_bfloat16>(__nv_bfloat16 x) {
+  return (double)__bfloat162float(x);
+}
+template <class T> __device__ __forceinline__ T tsqrt(T x) { return sqrt(x); }
+template <> __device__ __forceinline__ float tsqrt<float>(float x) { return sqrtf(x); }
+template <> __device__ __forceinline__ __nv_bfloat16 tsqrt<__nv_bfloat16>(__nv_bfloat16 x) {
+  return __float2bfloat16(sqrtf(__bfloat162float(x)));
+}
+template <class T> __device__ __forceinline__ T tabs(T x) { return x < T(0) ? -x : x; }
+template <> __device__ __forceinline__ __nv_bfloat16 tabs<__nv_bfloat16>(__nv_bfloat16 x) {
+  return __habs(x);
+}
+template <class T> __device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
+template <> __device__ __forceinline__ __nv_bfloat16 tmax<__nv_bfloat16>(__nv_bfloat16 a,
+                                                                         __nv_bfloat16 b) {
+  return __hmax(a, b);
+}
+
+// PDE parameters converted to the arithmetic type T.
+template <class T> struct PP {
+  T rho, irho, K, lam, mu, lam2mu, gm1, gamma, g, halfg, c;
+};
+
+template <class T> __device__ __forceinline__ PP<T> make_pp(const PdeParams& p, int cell) {
+  PP<T> r;
+  double K = p.K, c = p.pde == 0 ? sqrt(p.K / p.rho) : p.cp;
+  if (p.pde == 0 && p.cell_c) {
+    c = p.cell_c[cell];
+    K = p.rho * c * c;
+  }
+  r.rho = tcast<T>(p.rho);
+  r.irho = tcast<T>(1.0 / p.rho);
+  r.K = tcast<T>(K);
+  r.lam = tcast<T>(p.lam);
+  r.mu = tcast<T>(p.mu);
+  r.lam2mu = tcast<T>(p.lam + 2.0 * p.mu);
+  r.gm1 = tcast<T>(p.gamma - 1.0);
+  r.gamma = tcast<T>(p.gamma);
+  r.g = tcast<T>(p.g);
+  r.halfg = tcast<T>(0.5 * p.g);
+  r.c = tcast<T>(c < 0 ? -c : c);
+  return r;
+}
+
+template <int PDE, int D> struct Phys;
+
+// ---- linear acoustics, eq. (acoustic): F_dir = (K v_dir, p/rho e_dir) ----------------------
+template <int D> struct Phys<0, D> {
+  static constexpr int V = 1 + D;
+  static constexpr bool linear = true;
+  __host__ __device__ static constexpr bool nz(int dir, int v) { return v == 0 || v == 1 + dir; }
+  template <class T> __device__ static __forceinline__ void flux(const PP<T>& p, const T* q, T (*F)[V]) {
+#pragma unroll
+    for (int dir = 0; dir < D; ++dir) {
+#pragma unroll
+      for (int v = 0; v < V; ++v) F[dir][v] = T(0);
+      F[dir][0] = p.K * q[1 + dir];
+      F[dir][1 + dir] = q[0] * p.irho;
+    }
+  }
+  template <class T> __device__ static __forceinline__ T speed(const PP<T>& p, const T*, int) { return p.c; }
+};
+
+// ---- linear elasticity, velocity-stress form, eq. (lin_elastic) ------------------------------
+template <> struct Phys<1, 3> {
+  static constexpr int V = 9;  // sxx syy szz sxy syz sxz vx vy vz
+  static constexpr bool linear = true;
+  __host__ __device__ static constexpr bool nz(int dir, int v) {
+    return !((dir == 0 && v == 4) || (dir == 1 && v == 5) || (dir == 2 && v == 3));
+  }
+  template <class T> __device__ static __forceinline__ void flux(const PP<T>& p, const T* q, T (*F)[V]) {
+    const T vx = q[6], vy = q[7], vz = q[8];
+    // direction x
+    F[0][0] = -p.lam2mu * vx;
+    F[0][1] = -p.lam * vx;
+    F[0][2] = -p.lam * vx;
+    F[0][3] = -p.mu * vy;
+    F[0][4] = T(0);
+    F[0][5] = -p.mu * vz;
+    F[0][6] = -q[0] * p.irho;
+    F[0][7] = -q[3] * p.irho;
+    F[0][8] = -q[5] * p.irho;
+    // direction y
+    F[1][0] = -p.lam * vy;
+    F[1][1] = -p.lam2mu * vy;
+    F[1][2] = -p.lam * vy;
+    F[1][3] = -p.mu * vx;
+    F[1][4] = -p.mu * vz;
+    F[1][5] = T(0);
+    F[1][6] = -q[3] * p.irho;
+    F[1][7] = -q[1] * p.irho;
+    F[1][8] = -q[4] * p.irho;
+    // direction z
+    F[2][0] = -p.lam * vz;
+    F[2][1] = -p.lam * vz;
+    F[2][2] = -p.lam2mu * vz;
+    F[2][3] = T(0);
+    F[2][4] = -p.mu * vy;
+    F[2][5] = -p.mu * vx;
+    F[2][6] = -q[5] * p.irho;
+    F[2][7] = -q[4] * p.irho;
+    F[2][8] = -q[2] * p.irho;
+  }
+  template <class T> __device__ static __forceinline__ T speed(const PP<T>& p, const T*, int) { return p.c; }
+};
+
+template <> struct Phys<1, 2> {
+  static constexpr int V = 5;  // sxx syy sxy vx vy
+  static constexpr bool linear = true;
+  __host__ __device__ static constexpr bool nz(int, int) { return true; }
+  template <class T> __device__ static __forceinline__ void flux(const PP<T>& p, const T* q, T (*F)[V]) {
+    const T vx = q[3], vy = q[4];
+    F[0][0] = -p.lam2mu * vx;
+    F[0][1] = -p.lam * vx;
+    F[0][2] = -p.mu * vy;
+    F[0][3] = -q[0] * p.irho;
+    F[0][4] = -q[2] * p.irho;
+    F[1][0] = -p.lam * vy;
+    F[1][1] = -p.lam2mu * vy;
+    F[1][2] = -p.mu * vx;
+    F[1][3] = -q[2] * p.irho;
+    F[1][4] = -q[1] * p.irho;
+  }
+  template <class T> __device__ static __forceinline__ T speed(const PP<T>& p, const T*, int) { return p.c; }
+};
+
+// ---- compressible Euler, eq. (euler_eq), ideal gas ---------------------------------------------
+template <int D> struct Phys<2, D> {
+  static constexpr int V = 2 + D;
+  static constexpr bool linear = false;
+  __host__ __device__ static constexpr bool nz(int, int) { return true; }
+  template <class T> __device__ static __forceinline__ T pressure(const PP<T>& p, const T* q, T* u) {
+    const T ir = T(1) / q[0];
+    T ke = T(0);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      u[a] = q[1 + a] * ir;
+      ke += q[1 + a] * u[a];
+    }
+    return p.gm1 * (q[1 + D] - T(0.5) * ke);
+  }
+  template <class T> __device__ static __forceinline__ void flux(const PP<T>& p, const T* q, T (*F)[V]) {
+    T u[D];
+    const T pr = pressure(p, q, u);
+    const T Ep = q[1 + D] + pr;
+#pragma unroll
+    for (int dir = 0; dir < D; ++dir) {
+      F[dir][0] = q[1 + dir];
+#pragma unroll
+      for (int a = 0; a < D; ++a) F[dir][1 + a] = q[1 + a] * u[dir];
+      F[dir][1 + dir] += pr;
+      F[dir][1 + D] = u[dir] * Ep;
+    }
+  }
+  template <class T> __device__ static __forceinline__ T speed(const PP<T>& p, const T* q, int dir) {
+    T u[D];
+    const T pr = pressure(p, q, u);
+    return tabs(u[dir]) + tsqrt(p.gamma * pr / q[0]);
+  }
+};
+
+// ---- shallow water, flat bathymetry (Sec. 4.4): F_dir = (h v_dir, h v v_dir + g h^2/2 e_dir) --
+template <> struct Phys<3, 2> {
+  static constexpr int V = 3;
+  static constexpr bool linear = false;
+  __host__ __device__ static constexpr bool nz(int, int) { return true; }
+  template <class T> __device__ static __forceinline__ void flux(const PP<T>& p, const T* q, T (*F)[V]) {
+    const T ih = T(1) / q[0];
+    const T u = q[1] * ih, v = q[2] * ih;
+    const T ph = p.halfg * q[0] * q[0];
+    F[0][0] = q[1];
+    F[0][1] = q[1] * u + ph;
+    F[0][2] = q[2] * u;
+    F[1][0] = q[2];
+    F[1][1] = q[1] * v;
+    F[1][2] = q[2] * v + ph;
+  }
+  template <class T> __device__ static __forceinline__ T speed(const PP<T>& p, const T* q, int dir) {
+    return tabs(q[1 + dir] / q[0]) + tsqrt(p.g * q[0]);
+  }
+};
+
+}  // namespace adg

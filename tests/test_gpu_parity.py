@@ -1,0 +1,281 @@
+"""GPU parity of the CUDA path against the FP64 oracle, through the C ABI.
+
+Tolerances:
+  * FP64 everywhere: elementwise |Q_gpu - Q_oracle| <= 1e-12 max|Q| (rounding-order
+    differences only; the only reductions are a max and fixed-order sums).
+  * FP32 Picard/predictor (and FP32 Riemann/corrector): relative eq.-(L2gauss) distance
+    <= 1e-5 (the FP32 tolerance of the benchmark spec, relative per eq. L2gauss).
+  * bf16 Riemann/corrector: relative distance <= steps * 2^-8 (one bf16 rounding unit of
+    the face data per step bounds the update error; gross mistakes give O(1)).
+"""
+import numpy as np
+import pytest
+
+from paper_2504_06889_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def adg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2504_06889_gb300 import adg as A
+    from paper_2504_06889_gb300 import build
+
+    build.build()
+    A.load()
+    return A
+
+
+def elastic2d(cells, N=3):
+    w = [I.elastic_p_wave((2 * np.pi, 0.0), 1.0, 2.0, 1.0),
+         I.elastic_s_wave((0.0, 2 * np.pi), (1.0, 0.0), 1.0, 2.0, 1.0)]
+    return I.Workload("el2", 2, N, cells, I.ELASTIC, (1.0, 2.0, 1.0), I.SC_PLANAR, I.planar(5, w), 3)
+
+
+def euler2d(cells, N=3):
+    return I.Workload("eu2", 2, N, cells, I.EULER, (1.4,), I.SC_EULER_WAVE,
+                      I.euler_wave(k=(2 * np.pi, 4 * np.pi), u=(1.0, -0.5)), 3)
+
+
+def acoustic3d(cells, N=2):
+    w = I.acoustic_wave((2 * np.pi, -2 * np.pi, 4 * np.pi), 1.0, 2.0)
+    return I.Workload("ac3", 3, N, cells, I.ACOUSTIC, (1.0, 2.0), I.SC_PLANAR, I.planar(4, [w]), 3)
+
+
+SMALL = [
+    I.acoustic2d_planar(N=3).with_cells((5, 3), 4),   # 15 cells, 8 per block: ragged tail
+    I.acoustic2d_planar(N=2).with_cells((4, 4), 4),
+    I.euler3d_wave(N=5).with_cells((3, 2, 2), 3),
+    I.euler3d_wave(N=2).with_cells((3, 3, 3), 3),
+    euler2d((4, 3)),
+    I.elastic3d_planar(N=6).with_cells((2, 2, 2), 2),
+    I.elastic3d_planar(N=2).with_cells((3, 2, 2), 3),
+    elastic2d((4, 3)),
+    I.swe2d_modes(N=4).with_cells((7, 3), 3),          # 21 cells, 5 per block: ragged tail
+    I.swe2d_modes(N=2).with_cells((5, 5), 3),
+    I.acoustic3d_pulse(N=4).with_cells((3, 3, 2), 3),
+    acoustic3d((3, 3, 3)),
+]
+IDS = [f"{w.name.split('_')[0]}_N{w.N}_{'x'.join(map(str, w.cells))}" for w in SMALL]
+
+
+def oracle_run(oracle_mod, wl, steps):
+    M = oracle_mod.Mesh(wl.dim, wl.N, wl.cells, wl.pde, wl.params, cfl=wl.cfl)
+    Q = M.interpolate(wl.scenario, wl.sp)
+    t, dt = M.run(Q, steps)
+    return M, Q, t
+
+
+def gpu_run(adg, wl, steps, precision=None):
+    s = adg.Solver(wl.dim, wl.N, wl.cells, wl.pde, wl.params, cfl=wl.cfl, precision=precision)
+    s.set_initial(wl.scenario, wl.sp)
+    t, dt = s.step(steps)
+    Q = s.state()
+    return s, Q, t
+
+
+def rel_l2(M, Qa, Qb):
+    return M.l2_diff(Qa, Qb)[1] / M.l2_diff(Qb, M.zeros())[1]
+
+
+@pytest.mark.parametrize("wl", SMALL, ids=IDS)
+def test_initial_interpolation_matches_oracle(adg, oracle_mod, wl):
+    M = oracle_mod.Mesh(wl.dim, wl.N, wl.cells, wl.pde, wl.params, cfl=wl.cfl)
+    Qo = M.interpolate(wl.scenario, wl.sp)
+    s = adg.Solver(wl.dim, wl.N, wl.cells, wl.pde, wl.params, cfl=wl.cfl)
+    s.set_initial(wl.scenario, wl.sp)
+    Qg = s.state()
+    np.testing.assert_allclose(Qg, Qo, rtol=0, atol=4e-15 * np.abs(Qo).max())
+    t, dt = s.time()
+    assert t == 0.0
+    assert abs(dt - M.dt(Qo)) <= 1e-15 * dt
+
+
+@pytest.mark.parametrize("wl", SMALL, ids=IDS)
+def test_fp64_step_matches_oracle(adg, oracle_mod, wl):
+    M, Qo, to = oracle_run(oracle_mod, wl, wl.steps)
+    s, Qg, tg = gpu_run(adg, wl, wl.steps)
+    assert abs(tg - to) <= 1e-14 * to
+    np.testing.assert_allclose(Qg, Qo, rtol=0, atol=1e-12 * np.abs(Qo).max())
+    # error functional against the closed form, evaluated on the device
+    if wl.has_exact:
+        per_g, tot_g = s.error_vs_exact()
+        per_o, tot_o = M.l2_error(Qo, wl.scenario, wl.sp, to)
+        assert abs(tot_g - tot_o) <= 1e-9 * tot_o + 1e-15
+    # conservation of the totals
+    Q0 = M.interpolate(wl.scenario, wl.sp)
+    np.testing.assert_allclose(M.totals(Qg), M.totals(Q0), rtol=0, atol=1e-13 * np.abs(Q0).max())
+
+
+@pytest.mark.parametrize("wl", SMALL, ids=IDS)
+def test_fp32_predictor_within_1e5(adg, oracle_mod, wl):
+    M, Qo, to = oracle_run(oracle_mod, wl, wl.steps)
+    _, Qg, tg = gpu_run(adg, wl, wl.steps, precision={"picard": "fp32", "predictor": "fp32"})
+    assert abs(tg - to) <= 1e-6 * to
+    assert rel_l2(M, Qg, Qo) <= 1e-5
+
+
+@pytest.mark.parametrize("rie,cor", [("fp64", "fp32"), ("fp32", "fp32"), ("fp32", "fp64")])
+@pytest.mark.parametrize("wl", SMALL[:4] + SMALL[8:9], ids=IDS[:4] + IDS[8:9])
+def test_fp32_riemann_corrector_within_1e5(adg, oracle_mod, wl, rie, cor):
+    M, Qo, to = oracle_run(oracle_mod, wl, wl.steps)
+    _, Qg, _ = gpu_run(adg, wl, wl.steps, precision={"riemann": rie, "corrector": cor})
+    assert rel_l2(M, Qg, Qo) <= 1e-5
+
+
+@pytest.mark.parametrize("pic,rie,cor", [
+    ("fp64", "bf16", "bf16"), ("fp64", "fp64", "bf16"), ("fp64", "bf16", "fp64"),
+    ("fp32", "bf16", "bf16"), ("fp32", "fp32", "bf16"), ("fp32", "bf16", "fp32"),
+])
+def test_swe_bf16_riemann_corrector_bounded(adg, oracle_mod, pic, rie, cor):
+    wl = SMALL[8]
+    M, Qo, to = oracle_run(oracle_mod, wl, wl.steps)
+    _, Qg, _ = gpu_run(adg, wl, wl.steps,
+                       precision={"picard": pic, "predictor": pic, "riemann": rie, "corrector": cor})
+    err = rel_l2(M, Qg, Qo)
+    assert err <= wl.steps * 2.0 ** -8
+    assert np.all(np.isfinite(Qg))
+
+
+def test_single_cell_periodic_mesh(adg, oracle_mod):
+    """m = 1 along a direction: the cell is its own neighbour."""
+    wl = I.euler3d_wave(N=2).with_cells((1, 2, 1), 3)
+    M, Qo, to = oracle_run(oracle_mod, wl, 3)
+    _, Qg, _ = gpu_run(adg, wl, 3)
+    np.testing.assert_allclose(Qg, Qo, rtol=0, atol=1e-12 * np.abs(Qo).max())
+
+
+def test_anisotropic_box(adg, oracle_mod):
+    wl = I.acoustic2d_planar(N=3)
+    lo, hi = [0.0, -1.0], [1.0, 2.0]
+    w = I.acoustic_wave((2 * np.pi, 2 * np.pi / 3), 1.0, 1.0)
+    sp = I.planar(3, [w])
+    M = oracle_mod.Mesh(2, 3, (4, 5), I.ACOUSTIC, (1.0, 1.0), lo=lo, hi=hi, cfl=wl.cfl)
+    Qo = M.interpolate(I.SC_PLANAR, sp)
+    to, _ = M.run(Qo, 4)
+    s = adg.Solver(2, 3, (4, 5), I.ACOUSTIC, (1.0, 1.0), lo=lo, hi=hi, cfl=wl.cfl)
+    s.set_initial(I.SC_PLANAR, sp)
+    tg, _ = s.step(4)
+    np.testing.assert_allclose(s.state(), Qo, rtol=0, atol=1e-12 * np.abs(Qo).max())
+    assert abs(tg - to) <= 1e-14 * to
+
+
+def test_set_state_roundtrip_and_l2_diff(adg, oracle_mod):
+    wl = I.euler3d_wave(N=5).with_cells((2, 2, 2))
+    M = oracle_mod.Mesh(wl.dim, wl.N, wl.cells, wl.pde, wl.params, cfl=wl.cfl)
+    Qo = M.interpolate(wl.scenario, wl.sp)
+    s = adg.Solver(wl.dim, wl.N, wl.cells, wl.pde, wl.params, cfl=wl.cfl)
+    s.set_initial(wl.scenario, wl.sp)
+    Qp = Qo + 1e-3 * np.random.default_rng(0).normal(size=Qo.shape)
+    s.set_state(Qp, t=0.25)
+    np.testing.assert_array_equal(s.state(), Qp)
+    t, _ = s.time()
+    assert t == 0.25
+    ref = torch.from_numpy(Qo).cuda()
+    per, tot = s.l2_diff(ref)
+    per_o, tot_o = M.l2_diff(Qp, Qo)
+    np.testing.assert_allclose(per, per_o, rtol=1e-12)
+    assert abs(tot - tot_o) <= 1e-12 * tot_o
+
+
+# ---- error paths (host-side faults only) ---------------------------------------------------------
+
+def test_errors_before_prerequisites(adg):
+    import ctypes as C
+
+    lib = adg.load()
+    h = C.c_void_p()
+    assert lib.adg_create(C.byref(h)) == adg.OK
+    t = C.c_double()
+    assert lib.adg_step(h, 1, C.byref(t), None) == adg.ENOTINIT
+    p = (C.c_double * 2)(1.0, 1.0)
+    assert lib.adg_set_pde(h, adg.ACOUSTIC, p, 2) == adg.ENOTINIT
+    cells = (C.c_int * 2)(4, 4)
+    lo = (C.c_double * 2)(0.0, 0.0)
+    hi = (C.c_double * 2)(1.0, 1.0)
+    assert lib.adg_init_mesh(h, 4, 3, cells, lo, hi) == adg.EINVAL
+    assert lib.adg_init_mesh(h, 2, 3, cells, lo, lo) == adg.EINVAL
+    assert lib.adg_init_mesh(h, 2, 3, cells, lo, hi) == adg.OK
+    assert lib.adg_set_pde(h, adg.SWE, p, 0) == adg.EINVAL
+    assert lib.adg_set_kernel_precision(h, adg.K_STORAGE, adg.FP32, 0) == adg.EUNSUPPORTED
+    assert lib.adg_set_pde(h, adg.ACOUSTIC, p, 2) == adg.OK
+    ws = C.c_size_t()
+    assert lib.adg_workspace_bytes(h, C.byref(ws)) == adg.OK
+    Q = torch.zeros(16 * 3 * 16, dtype=torch.float64, device="cuda")
+    W = torch.empty(ws.value + 512, dtype=torch.uint8, device="cuda")
+    base = W.data_ptr() + (-W.data_ptr()) % 256
+    assert lib.adg_bind_buffers(h, C.c_void_p(Q.data_ptr()), C.c_void_p(base), ws.value - 1) == adg.ENOMEM
+    assert lib.adg_bind_buffers(h, C.c_void_p(Q.data_ptr()), C.c_void_p(base + 8), ws.value) == adg.EINVAL
+    assert lib.adg_bind_buffers(h, C.c_void_p(Q.data_ptr()), C.c_void_p(base), ws.value) == adg.OK
+    assert lib.adg_step(h, 1, C.byref(t), None) == adg.ENOTINIT  # no state yet
+    assert lib.adg_last_error(h)
+    assert lib.adg_destroy(h) == adg.OK
+
+
+def test_unbuilt_order_is_unsupported(adg):
+    with pytest.raises(adg.AdgError) as e:
+        adg.Solver(2, 7, (4, 4), adg.EULER, (1.4,))
+    assert e.value.code == adg.EUNSUPPORTED
+
+
+def test_nonfinite_state_is_reported_and_time_stops(adg, oracle_mod):
+    wl = I.euler3d_wave(N=2).with_cells((3, 3, 3))
+    s = adg.Solver(wl.dim, wl.N, wl.cells, wl.pde, wl.params, cfl=wl.cfl)
+    s.set_initial(wl.scenario, wl.sp)
+    t1, _ = s.step(2)
+    Q = s.state()
+    Q[5, 0, 3] = np.nan  # injected on the host
+    s.set_state(Q, t=t1)
+    with pytest.raises(adg.AdgError) as e:
+        s.step(3)
+    assert e.value.code == adg.ENONFINITE
+    # a negative density is not caught by the CFL check but a NaN produced later is:
+    s.set_initial(wl.scenario, wl.sp)
+    Q = s.state()
+    Q[7, 4, :] = np.inf
+    s.set_state(Q, t=0.0)
+    with pytest.raises(adg.AdgError):
+        s.step(1)
+    # recovery: a good state steps again
+    s.set_initial(wl.scenario, wl.sp)
+    t, _ = s.step(2)
+    assert abs(t - t1) <= 1e-14 * t1
+
+
+# ---- full size, in the benchmark's launch configuration: sampled cells ----------------------------
+
+FULL = [
+    (I.euler3d_wave(), [("fp64", 1e-12), ("fp32", 1e-5)]),
+    (I.elastic3d_planar(), [("fp32", 1e-5)]),
+    (I.swe2d_modes(), [("fp64", 1e-12), ("fp32", 1e-5)]),
+    (I.acoustic3d_pulse(), [("fp64", 1e-12)]),
+]
+
+
+@pytest.mark.parametrize("wl,precs", FULL, ids=[w.name for w, _ in FULL])
+def test_full_size_sampled_cells_match_oracle(adg, oracle_mod, wl, precs):
+    M = oracle_mod.Mesh(wl.dim, wl.N, wl.cells, wl.pde, wl.params, cfl=wl.cfl)
+    Q0 = M.interpolate(wl.scenario, wl.sp)
+    dt = M.dt(Q0)
+    rng = np.random.default_rng(11)
+    ids = np.unique(np.concatenate([[0, M.ncells - 1], rng.integers(0, M.ncells, size=14)]))
+    ref = M.step_cells(Q0, dt, ids)
+    for prec, tol in precs:
+        s = adg.Solver(wl.dim, wl.N, wl.cells, wl.pde, wl.params, cfl=wl.cfl,
+                       precision={"picard": prec, "predictor": prec})
+        s.set_state(Q0, 0.0)
+        t, dtg = s.step(1)
+        assert abs(dtg - dt) <= 1e-15 * dt
+        Qg = s.Q[torch.from_numpy(ids).cuda()].cpu().numpy()
+        for j in range(len(ids)):
+            err = np.sqrt(np.sum((Qg[j] - ref[j]) ** 2)) / np.sqrt(np.sum(ref[j] ** 2))
+            if prec == "fp64":
+                assert np.abs(Qg[j] - ref[j]).max() <= tol * np.abs(ref[j]).max(), (ids[j], err)
+            else:
+                assert err <= tol, (ids[j], err)
+        s.close()
+        del s
+        torch.cuda.empty_cache()

@@ -241,3 +241,18 @@ def test_acoustic_energy_does_not_grow(oracle_mod):
         e.append(energy(Q))
     assert all(e[j + 1] <= e[j] * (1 + 1e-14) for j in range(len(e) - 1)), e
     assert e[-1] < e[0]
+
+
+@pytest.mark.parametrize("cells", [(3, 4), (1, 2), (2, 2, 3)])
+def test_sampled_step_equals_full_step(oracle_mod, cells):
+    dim = len(cells)
+    wl = I.acoustic2d_planar(m=4, N=3) if dim == 2 else I.euler3d_wave(m=2, N=2)
+    wl = wl.with_cells(cells)
+    M = mesh_for(oracle_mod, wl)
+    Q = M.interpolate(wl.scenario, wl.sp)
+    dt = M.dt(Q)
+    Q1 = Q.copy()
+    M.step(Q1, dt)
+    ids = np.arange(M.ncells)[::-1].copy()
+    out = M.step_cells(Q, dt, ids)
+    np.testing.assert_array_equal(out, Q1[ids])
