@@ -174,6 +174,36 @@ ADG_API const char* adg_last_error(const adg_ctx* c);
 /* Number of variables of a PDE in dim dimensions, or -1. */
 ADG_API int adg_nvar(int pde, int dim);
 
+/* ---- stepping without device allocation ------------------------------------------------------
+ * The paper has no counterpart: this entry point serves callers that cannot allocate device
+ * memory, for example host applications that own the whole device memory pool, code with a
+ * fixed memory budget that must not allocate after start-up, or code that must avoid the
+ * device-wide synchronisation that cudaMalloc and cudaFree can cause.
+ *
+ * adg_step_noalloc advances the caller's FP64 state d_Q (device pointer, layout as above,
+ * updated in place) by nsteps steps of the all-FP64 scheme, without a context and without any
+ * allocation: it calls no cudaMalloc or cudaFree.  Its scratch (step scalars and face traces)
+ * is one file-scope device array of ADG_NOALLOC_SCRATCH_BYTES that every GPU loading the
+ * library keeps until the process exits.  *t_inout is the time of d_Q on entry and after the
+ * last good step on return; *dt_last_out (may be NULL) the last dt.  cuda_stream: the stream to
+ * run on (NULL = legacy default stream); the call waits for it before returning.
+ *
+ * Limits and behaviour:
+ *  - the FP64 face traces, cells * dim * 4 * V * (N+1)^(dim-1) * 8 bytes, must fit in
+ *    ADG_NOALLOC_SCRATCH_BYTES - 256; larger meshes return ADG_ENOMEM before any work;
+ *  - the first call on a device, with that device current, looks up the array's device address
+ *    (cudaGetSymbolAddress) and keeps it; make that first call before any stream capture;
+ *  - all calls share the array and it keeps the last call's contents; each call clears the
+ *    scalars it needs before using them.  Calls that overlap on the GPU (other streams or
+ *    threads) race on the array: serialise them;
+ *  - returns ADG_EINVAL for bad arguments, ADG_EUNSUPPORTED when no kernels are built for
+ *    (pde, dim, N), ADG_ENONFINITE when a step produced Inf/NaN, ADG_ECUDA on a CUDA error. */
+#define ADG_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+ADG_API int adg_step_noalloc(int pde, int dim, int order_N, const int* cells, const double* lo,
+                             const double* hi, const double* pde_params, int nparams, double cfl,
+                             int picard_iters, double* d_Q, int nsteps, double* t_inout,
+                             double* dt_last_out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -55,6 +55,8 @@ _SIGS = {
     "adg_l2_diff": [_P, _P, _dp, _dp],
     "adg_last_error": [_P],
     "adg_nvar": [C.c_int, C.c_int],
+    "adg_step_noalloc": [C.c_int, C.c_int, C.c_int, _ip, _dp, _dp, _dp, C.c_int, C.c_double, C.c_int,
+                         _P, C.c_int, _dp, _dp, _P],
 }
 
 

@@ -58,7 +58,7 @@ static void legendre_shifted(int n, long double x, long double* P, long double* 
   *dP = 2.0L * dp;  // chain rule dt/dx = 2
 }
 
-static bool build_tables(int n, Tables* T) {
+bool build_tables(int n, Tables* T) {
   if (n < 1 || n > kMaxN1) return false;
   std::memset(T, 0, sizeof(*T));
   T->n = n;

@@ -103,6 +103,7 @@ struct Entry {
 };
 
 void register_entry(const Entry& e);
+bool build_tables(int n, Tables* T);
 const Entry* find_entry(int pde, int dim, int N);
 
 }  // namespace adg
