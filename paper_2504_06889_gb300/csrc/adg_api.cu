@@ -131,9 +131,34 @@ bool build_tables(int n, Tables* T) {
       T->D[k][l] = (double)D[k][l];
       T->P[k][l] = (double)(A[k][n + l] / A[k][k]);
       T->Vm[k][l] = (double)(w[l] * D[l][k] / w[k]);
+      T->fD[k][l] = (float)T->D[k][l];
+      T->fP[k][l] = (float)T->P[k][l];
+      T->fVm[k][l] = (float)T->Vm[k][l];
     }
+    T->fw[k] = (float)T->w[k];
+    T->fpsi0[k] = (float)T->psi0[k];
+    T->fpsi1[k] = (float)T->psi1[k];
   }
   return true;
+}
+
+void finalize_pde_params(PdeParams* p) {
+  p->irho = p->rho > 0 ? 1.0 / p->rho : 0.0;
+  p->lam2mu = p->lam + 2.0 * p->mu;
+  p->gm1 = p->gamma - 1.0;
+  p->halfg = 0.5 * p->g;
+  p->c = p->pde == 0 ? std::sqrt(p->K / p->rho) : std::fabs(p->cp);
+  p->f_rho = (float)p->rho;
+  p->f_irho = (float)p->irho;
+  p->f_K = (float)p->K;
+  p->f_lam = (float)p->lam;
+  p->f_mu = (float)p->mu;
+  p->f_lam2mu = (float)p->lam2mu;
+  p->f_gm1 = (float)p->gm1;
+  p->f_gamma = (float)p->gamma;
+  p->f_g = (float)p->g;
+  p->f_halfg = (float)p->halfg;
+  p->f_c = (float)p->c;
 }
 
 }  // namespace adg
@@ -330,6 +355,7 @@ int adg_set_pde(adg_ctx* c, int pde, const double* params, int nparams) {
     if (!(p.g > 0)) return fail(c, ADG_EINVAL, "swe: g > 0");
   }
   p.cell_c = c->d_cell_c;
+  finalize_pde_params(&p);
   c->pp = p;
   c->pde = pde;
   c->V = V;

@@ -19,6 +19,9 @@ struct Tables {
   double D[kMaxN1][kMaxN1];   // D[a][b] = psi_b'(xi_a)
   double P[kMaxN1][kMaxN1];   // P = K1^{-1} diag(w): Picard update q = Q - dt P R
   double Vm[kMaxN1][kMaxN1];  // Vm[i][m] = w_m D[m][i] / w_i: mass-inverted volume operator
+  // FP32 copies for the FP32 kernels (rounded from the FP64 values)
+  float fD[kMaxN1][kMaxN1], fP[kMaxN1][kMaxN1], fVm[kMaxN1][kMaxN1];
+  float fw[kMaxN1], fpsi0[kMaxN1], fpsi1[kMaxN1];
 };
 
 // PDE parameters (acoustic rho,K; elastic rho,cp,cs; euler gamma; swe g)
@@ -26,7 +29,11 @@ struct PdeParams {
   int pde;
   double rho, K, cp, cs, lam, mu, gamma, g;
   const double* cell_c;  // optional per-cell acoustic wave speed (device), K = rho c^2
+  // derived on the host by finalize_pde_params (FP64 and FP32 copies)
+  double irho, lam2mu, gm1, halfg, c;
+  float f_rho, f_irho, f_K, f_lam, f_mu, f_lam2mu, f_gm1, f_gamma, f_g, f_halfg, f_c;
 };
+void finalize_pde_params(PdeParams* p);
 
 // Device-resident step scalars (owned by the context).
 struct DevScalars {

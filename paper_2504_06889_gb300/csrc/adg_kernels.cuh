@@ -42,6 +42,32 @@ __device__ __forceinline__ double dt_from(const StepArgs& a, int D, int N) {
   return a.cfl * a.hmin / ((double)D * (2.0 * N + 1.0) * lam);
 }
 
+// dt of this step, computed by one thread and shared through shared memory (the FP64 division
+// is expensive on this part; every block computes the same value)
+__device__ __forceinline__ double block_dt(const StepArgs& a, int D, int N, double* s_dt) {
+  if (threadIdx.x == 0) *s_dt = dt_from(a, D, N);
+  __syncthreads();
+  return *s_dt;
+}
+
+// table entries in the kernel's arithmetic type (FP32 kernels read the FP32 copies)
+template <class T> struct Tab {
+  __device__ static __forceinline__ T D(const Tables& t, int r, int c) { return (T)t.D[r][c]; }
+  __device__ static __forceinline__ T P(const Tables& t, int r, int c) { return (T)t.P[r][c]; }
+  __device__ static __forceinline__ T Vm(const Tables& t, int r, int c) { return (T)t.Vm[r][c]; }
+  __device__ static __forceinline__ T w(const Tables& t, int r) { return (T)t.w[r]; }
+  __device__ static __forceinline__ T psi0(const Tables& t, int r) { return (T)t.psi0[r]; }
+  __device__ static __forceinline__ T psi1(const Tables& t, int r) { return (T)t.psi1[r]; }
+};
+template <> struct Tab<float> {
+  __device__ static __forceinline__ float D(const Tables& t, int r, int c) { return t.fD[r][c]; }
+  __device__ static __forceinline__ float P(const Tables& t, int r, int c) { return t.fP[r][c]; }
+  __device__ static __forceinline__ float Vm(const Tables& t, int r, int c) { return t.fVm[r][c]; }
+  __device__ static __forceinline__ float w(const Tables& t, int r) { return t.fw[r]; }
+  __device__ static __forceinline__ float psi0(const Tables& t, int r) { return t.fpsi0[r]; }
+  __device__ static __forceinline__ float psi1(const Tables& t, int r) { return t.fpsi1[r]; }
+};
+
 __device__ __forceinline__ int neighbour(const StepArgs& a, int c, int dir, int side) {
   int cc[3] = {c % a.m[0], (c / a.m[0]) % a.m[1], c / (a.m[0] * a.m[1])};
   cc[dir] += side ? 1 : -1;
@@ -50,11 +76,55 @@ __device__ __forceinline__ int neighbour(const StepArgs& a, int c, int dir, int 
   return cc[0] + a.m[0] * (cc[1] + a.m[1] * cc[2]);
 }
 
+// Pencil layout of a flux slice in shared memory: for each direction the n values along that
+// direction are contiguous, padded to an even stride so that they can be read with 8- or 16-byte
+// vector loads.
+template <class C> struct Pencil {
+  static constexpr int S = (C::n % 2 == 0) ? C::n : C::n + 1;  // stride of one pencil
+  static constexpr int PER_DIR = C::NF * S;                    // one variable, one direction
+};
+
+template <class T, int S> struct VecLoad;
+template <int S> struct VecLoad<float, S> {
+  static constexpr int W = (S % 4 == 0) ? 4 : 2;
+  __device__ static __forceinline__ void load(const float* p, float* out) {
+    if constexpr (W == 4) {
+#pragma unroll
+      for (int j = 0; j < S; j += 4) {
+        const float4 v = *reinterpret_cast<const float4*>(p + j);
+        out[j] = v.x;
+        out[j + 1] = v.y;
+        out[j + 2] = v.z;
+        out[j + 3] = v.w;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < S; j += 2) {
+        const float2 v = *reinterpret_cast<const float2*>(p + j);
+        out[j] = v.x;
+        out[j + 1] = v.y;
+      }
+    }
+  }
+};
+template <int S> struct VecLoad<double, S> {
+  __device__ static __forceinline__ void load(const double* p, double* out) {
+#pragma unroll
+    for (int j = 0; j < S; j += 2) {
+      const double2 v = *reinterpret_cast<const double2*>(p + j);
+      out[j] = v.x;
+      out[j + 1] = v.y;
+    }
+  }
+};
+
 template <class C, class T, class TP> struct PredSmem {
-  static constexpr size_t sweep = sizeof(T) * C::CPB * C::D * C::V * C::NS;
-  static constexpr size_t fin = sizeof(TP) * C::CPB * (C::D + 1) * C::V * C::NS;
+  // two flux-slice buffers (double buffering) during the sweeps
+  static constexpr size_t sweep = sizeof(T) * 2 * C::CPB * C::D * C::V * Pencil<C>::PER_DIR;
+  // final stage: Fbar in pencil layout + Qbar
+  static constexpr size_t fin = sizeof(TP) * C::CPB * (C::D * C::V * Pencil<C>::PER_DIR + C::V * C::NS);
   static constexpr size_t big = ((sweep > fin ? sweep : fin) + 15) / 16 * 16;
-  static constexpr size_t tables = sizeof(T) * 2 * C::n * C::n + sizeof(TP) * (C::n * C::n + 3 * C::n);
+  static constexpr size_t tables = sizeof(T) * C::n * C::n + sizeof(TP) * (C::n * C::n + 3 * C::n);
   static constexpr size_t total = big + tables;
 };
 
@@ -65,27 +135,28 @@ template <class C, class T, class TP, class TS>
 __global__ void __launch_bounds__(C::THREADS) k_predictor(const __grid_constant__ StepArgs a) {
   using Ph = Phys<C::PDE, C::D>;
   constexpr int n = C::n, V = C::V, D = C::D, NS = C::NS, NF = C::NF, CPB = C::CPB;
+  constexpr int S = Pencil<C>::S, PD = Pencil<C>::PER_DIR;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double s_dt;
   if (a.sc->bad) return;
-  const double dt = dt_from(a, D, C::N);
+  const double dt = block_dt(a, D, C::N, &s_dt);
 
-  // tables: dtP (T), D (T), Vm (TP), w, psi0, psi1 (TP)
-  T* sD = reinterpret_cast<T*>(smem_raw + PredSmem<C, T, TP>::big);
-  T* sdtP = sD + n * n;
+  // tables: dt P (T), then Vm, w, psi0, psi1 (TP)
+  T* sdtP = reinterpret_cast<T*>(smem_raw + PredSmem<C, T, TP>::big);
   TP* sVm = reinterpret_cast<TP*>(sdtP + n * n);
   TP* sw = sVm + n * n;
   TP* sp0 = sw + n;
   TP* sp1 = sp0 + n;
+  const T dtT = (T)dt;
   for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
     const int r = t / n, cidx = t % n;
-    sD[t] = (T)a.tab.D[r][cidx];
-    sdtP[t] = (T)(dt * a.tab.P[r][cidx]);
-    sVm[t] = (TP)a.tab.Vm[r][cidx];
+    sdtP[t] = dtT * Tab<T>::P(a.tab, r, cidx);
+    sVm[t] = Tab<TP>::Vm(a.tab, r, cidx);
   }
   for (int t = threadIdx.x; t < n; t += blockDim.x) {
-    sw[t] = (TP)a.tab.w[t];
-    sp0[t] = (TP)a.tab.psi0[t];
-    sp1[t] = (TP)a.tab.psi1[t];
+    sw[t] = Tab<TP>::w(a.tab, t);
+    sp0[t] = Tab<TP>::psi0(a.tab, t);
+    sp1[t] = Tab<TP>::psi1(a.tab, t);
   }
 
   const int lc = threadIdx.x / NS, i = threadIdx.x % NS;
@@ -93,16 +164,24 @@ __global__ void __launch_bounds__(C::THREADS) k_predictor(const __grid_constant_
   const bool valid = cell < a.ncells;
   const int cl = valid ? cell : 0;
 
-  int idx[3] = {i % n, (i / n) % n, i / (n * n)};
-  int pb[3];  // start of this node's pencil along dir in the pencil layout
-  pb[0] = (i / n) * n;
+  const int idx[3] = {i % n, (i / n) % n, i / (n * n)};
+  int pb[3];  // start of this node's pencil along dir (pencil index times the stride)
+  pb[0] = (i / n) * S;
   if (D == 2) {
-    pb[1] = idx[0] * n;
+    pb[1] = idx[0] * S;
+    pb[2] = 0;
   } else {
-    pb[1] = (idx[0] + n * idx[2]) * n;
-    pb[2] = (idx[0] + n * idx[1]) * n;
+    pb[1] = (idx[0] + n * idx[2]) * S;
+    pb[2] = (idx[0] + n * idx[1]) * S;
   }
-  const T invh[3] = {(T)a.invh[0], (T)a.invh[1], (T)a.invh[2]};
+  // this node's rows of the derivative matrix, scaled by 1/h_dir
+  T Dr[D][S];
+#pragma unroll
+  for (int dir = 0; dir < D; ++dir) {
+    const T ih = (T)a.invh[dir];
+#pragma unroll
+    for (int m = 0; m < S; ++m) Dr[dir][m] = m < n ? Tab<T>::D(a.tab, idx[dir], m) * ih : T(0);
+  }
   const PP<T> pp = make_pp<T>(a.pp, cl);
 
   T Qh[V];
@@ -110,7 +189,11 @@ __global__ void __launch_bounds__(C::THREADS) k_predictor(const __grid_constant_
 #pragma unroll
   for (int v = 0; v < V; ++v) Qh[v] = (T)Qc[v * NS + i];
 
-  T* sF = reinterpret_cast<T*>(smem_raw) + (size_t)lc * D * V * NS;  // [dir][v][pencil layout]
+  T* sFbuf = reinterpret_cast<T*>(smem_raw);
+  constexpr size_t bufsz = (size_t)CPB * D * V * PD;
+  // zero the pencil pads once (they are read as part of the vector loads and multiplied by 0)
+  if (S != n)
+    for (size_t t = threadIdx.x; t < 2 * bufsz; t += blockDim.x) sFbuf[t] = T(0);
 
   T q[n][V];
 #pragma unroll
@@ -119,6 +202,7 @@ __global__ void __launch_bounds__(C::THREADS) k_predictor(const __grid_constant_
     for (int v = 0; v < V; ++v) q[k][v] = Qh[v];
 
   __syncthreads();
+  int buf = 0;
   for (int r = 0; r < a.picard_iters; ++r) {
     T qn[n][V];
 #pragma unroll
@@ -127,13 +211,16 @@ __global__ void __launch_bounds__(C::THREADS) k_predictor(const __grid_constant_
       for (int v = 0; v < V; ++v) qn[k][v] = Qh[v];
 #pragma unroll
     for (int k = 0; k < n; ++k) {
-      T F[D][V];
-      Ph::flux(pp, q[k], F);
+      T* sF = sFbuf + buf * bufsz + (size_t)lc * D * V * PD;
+      {
+        T F[D][V];
+        Ph::flux(pp, q[k], F);
 #pragma unroll
-      for (int dir = 0; dir < D; ++dir)
+        for (int dir = 0; dir < D; ++dir)
 #pragma unroll
-        for (int v = 0; v < V; ++v)
-          if (Ph::nz(dir, v)) sF[(dir * V + v) * NS + pb[dir] + idx[dir]] = F[dir][v];
+          for (int v = 0; v < V; ++v)
+            if (Ph::nz(dir, v)) sF[(dir * V + v) * PD + pb[dir] + idx[dir]] = F[dir][v];
+      }
       __syncthreads();
 #pragma unroll
       for (int v = 0; v < V; ++v) {
@@ -141,24 +228,23 @@ __global__ void __launch_bounds__(C::THREADS) k_predictor(const __grid_constant_
 #pragma unroll
         for (int dir = 0; dir < D; ++dir) {
           if (!Ph::nz(dir, v)) continue;
-          const T* Fp = sF + (dir * V + v) * NS + pb[dir];
-          const T* Dr = sD + idx[dir] * n;
-          T s = T(0);
+          T f[S];
+          VecLoad<T, S>::load(sF + (dir * V + v) * PD + pb[dir], f);
 #pragma unroll
-          for (int m = 0; m < n; ++m) s += Dr[m] * Fp[m];
-          rv += s * invh[dir];
+          for (int m = 0; m < n; ++m) rv += Dr[dir][m] * f[m];
         }
         // q_new[kk] = Q - dt sum_l P[kk][l] R_l  (column l = k)
 #pragma unroll
         for (int kk = 0; kk < n; ++kk) qn[kk][v] -= sdtP[kk * n + k] * rv;
       }
-      __syncthreads();
+      buf ^= 1;  // the next slice writes the other buffer: one barrier per slice
     }
 #pragma unroll
     for (int k = 0; k < n; ++k)
 #pragma unroll
       for (int v = 0; v < V; ++v) q[k][v] = qn[k][v];
   }
+  __syncthreads();
 
   // ---- final flux, time averages (Qbar = sum_k w_k q_k, Fbar = sum_k w_k F(q_k)) ---------------
   const PP<TP> ppP = make_pp<TP>(a.pp, cl);
@@ -185,14 +271,14 @@ __global__ void __launch_bounds__(C::THREADS) k_predictor(const __grid_constant_
     }
   }
   // shared: Fbar [dir][v][pencil layout], Qbar [v][node]
-  TP* sFb = reinterpret_cast<TP*>(smem_raw) + (size_t)lc * (D + 1) * V * NS;
-  TP* sQb = sFb + D * V * NS;
+  TP* sFb = reinterpret_cast<TP*>(smem_raw) + (size_t)lc * (D * V * PD + V * NS);
+  TP* sQb = sFb + D * V * PD;
 #pragma unroll
   for (int v = 0; v < V; ++v) {
     sQb[v * NS + i] = Qb[v];
 #pragma unroll
     for (int dir = 0; dir < D; ++dir)
-      if (Ph::nz(dir, v)) sFb[(dir * V + v) * NS + pb[dir] + idx[dir]] = Fb[dir][v];
+      if (Ph::nz(dir, v)) sFb[(dir * V + v) * PD + pb[dir] + idx[dir]] = Fb[dir][v];
   }
   __syncthreads();
 
@@ -205,7 +291,7 @@ __global__ void __launch_bounds__(C::THREADS) k_predictor(const __grid_constant_
 #pragma unroll
       for (int dir = 0; dir < D; ++dir) {
         if (!Ph::nz(dir, v)) continue;
-        const TP* Fp = sFb + (dir * V + v) * NS + pb[dir];
+        const TP* Fp = sFb + (dir * V + v) * PD + pb[dir];
         const TP* Vr = sVm + idx[dir] * n;
         TP s = TP(0);
 #pragma unroll
@@ -237,7 +323,7 @@ __global__ void __launch_bounds__(C::THREADS) k_predictor(const __grid_constant_
         for (int dd = 0; dd < D; ++dd)
           if (dd == dir) nzv = Ph::nz(dd, v);
         if (nzv) {
-          const TP* Fp = sFb + (dir * V + v) * NS + j * n;
+          const TP* Fp = sFb + (dir * V + v) * PD + j * S;
 #pragma unroll
           for (int m = 0; m < n; ++m) s += psi[m] * Fp[m];
         }
@@ -255,8 +341,9 @@ template <class C, class TR, class TC> struct CorrSmem {
   // G: [2d][V][NF] in TC, speeds [2d][NF] in TR
   static constexpr size_t tr = sizeof(TR) * C::CPB * 2 * C::D * 4 * C::V * C::NF;
   static constexpr size_t g = sizeof(TC) * C::CPB * 2 * C::D * C::V * C::NF;
-  static constexpr size_t sp = sizeof(TR) * C::CPB * 2 * C::D * C::NF;
-  static constexpr size_t total = tr + g + sp + 64;
+  static constexpr size_t sp = sizeof(TR) * C::CPB * 2 * C::D * (C::NF + 1);
+  static constexpr size_t coef = sizeof(TC) * 2 * C::D * C::n;
+  static constexpr size_t total = tr + g + sp + coef + 64;
 };
 
 template <class C, class TR, class TC, class TS>
@@ -265,13 +352,15 @@ __global__ void __launch_bounds__(C::THREADS) k_corrector(const __grid_constant_
   constexpr int n = C::n, V = C::V, D = C::D, NS = C::NS, NF = C::NF, CPB = C::CPB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ unsigned long long s_lam;
-  __shared__ unsigned int s_bad, s_last;
+  __shared__ unsigned int s_bad, s_last, s_l32;
+  __shared__ double s_dt;
   if (a.sc->bad) return;
-  const double dt = dt_from(a, D, C::N);
   if (threadIdx.x == 0) {
     s_lam = 0ull;
     s_bad = 0u;
+    s_l32 = 0u;
   }
+  const double dt = block_dt(a, D, C::N, &s_dt);
 
   const int lc = threadIdx.x / NS, i = threadIdx.x % NS;
   const int cell = blockIdx.x * CPB + lc;
@@ -280,8 +369,16 @@ __global__ void __launch_bounds__(C::THREADS) k_corrector(const __grid_constant_
 
   TR* sT = reinterpret_cast<TR*>(smem_raw) + (size_t)lc * 2 * D * 4 * V * NF;
   TC* sG = reinterpret_cast<TC*>(smem_raw + CorrSmem<C, TR, TC>::tr) + (size_t)lc * 2 * D * V * NF;
-  TR* sS = reinterpret_cast<TR*>(smem_raw + CorrSmem<C, TR, TC>::tr + CorrSmem<C, TR, TC>::g) +
-           (size_t)lc * 2 * D * NF;
+  TR* sSall = reinterpret_cast<TR*>(smem_raw + CorrSmem<C, TR, TC>::tr + CorrSmem<C, TR, TC>::g);
+  TR* sS = sSall + (size_t)lc * 2 * D * NF;
+  TR* sSmax = sSall + (size_t)CPB * 2 * D * NF + (size_t)lc * 2 * D;  // per-face Rusanov speed
+  // surface coefficients psi_s(xi_i) / (h_dir w_i): [side][dir][i]
+  TC* sCoef = reinterpret_cast<TC*>(smem_raw + CorrSmem<C, TR, TC>::tr + CorrSmem<C, TR, TC>::g +
+                                    CorrSmem<C, TR, TC>::sp);
+  for (int t = threadIdx.x; t < 2 * D * n; t += blockDim.x) {
+    const int id = t % n, dir = (t / n) % D, side = t / (n * D);
+    sCoef[t] = tcast<TC>((side ? a.tab.psi1[id] : a.tab.psi0[id]) * a.invh[dir] / a.tab.w[id]);
+  }
 
   const TS* trc = reinterpret_cast<const TS*>(a.traces);
   constexpr size_t cellsz = (size_t)D * 2 * 2 * V * NF;
@@ -321,11 +418,16 @@ __global__ void __launch_bounds__(C::THREADS) k_corrector(const __grid_constant_
     sS[it] = tmax(sm, sp);
   }
   __syncthreads();
+  for (int f = i; f < 2 * D; f += NS) {
+    TR s = sS[f * NF];
+    for (int jj = 1; jj < NF; ++jj) s = tmax(s, sS[f * NF + jj]);
+    sSmax[f] = s;
+  }
+  __syncthreads();
   // Rusanov: G = (Fm + Fp)/2 + s/2 (qm - qp), s = max over the face's nodes
   for (int it = i; it < 2 * D * V * NF; it += NS) {
     const int j = it % NF, v = (it / NF) % V, f = it / (NF * V);
-    TR s = sS[f * NF];
-    for (int jj = 1; jj < NF; ++jj) s = tmax(s, sS[f * NF + jj]);
+    const TR s = sSmax[f];
     const TR qm = sT[(((f * 2 + 0) * 2 + 0) * V + v) * NF + j];
     const TR qp = sT[(((f * 2 + 1) * 2 + 0) * V + v) * NF + j];
     const TR Fm = sT[(((f * 2 + 0) * 2 + 1) * V + v) * NF + j];
@@ -338,7 +440,9 @@ __global__ void __launch_bounds__(C::THREADS) k_corrector(const __grid_constant_
 
   // surface integral and update: Q_i -= dt sum_dir (1/h)(psi1[i_dir] G+ - psi0[i_dir] G-)/w[i_dir]
   double lam = 0.0;
-  bool bad = false;
+  float lam32 = 0.0f;
+  bool bad = false, risky = false;
+  double qnew_keep[V];
   if (valid) {
     const int idx[3] = {i % n, (i / n) % n, i / (n * n)};
     int jf[3];
@@ -360,22 +464,34 @@ __global__ void __launch_bounds__(C::THREADS) k_corrector(const __grid_constant_
         const int id = idx[dir];
         const TC gp = sG[((2 * dir + 1) * V + v) * NF + jf[dir]];
         const TC gm = sG[((2 * dir + 0) * V + v) * NF + jf[dir]];
-        const TC c1 = tcast<TC>(a.tab.psi1[id] * a.invh[dir] / a.tab.w[id]);
-        const TC c0 = tcast<TC>(a.tab.psi0[id] * a.invh[dir] / a.tab.w[id]);
-        surf += c1 * gp - c0 * gm;
+        surf += sCoef[(D + dir) * n + id] * gp - sCoef[dir * n + id] * gm;
       }
       const double qv = Qw[v * NS + i] - dt * todouble(surf);
       Qw[v * NS + i] = qv;
       qnew[v] = qv;
+      qnew_keep[v] = qv;
       bad |= !isfinite(qv);
     }
-    const PP<double> pd = make_pp<double>(a.pp, cell);
+    // FP32 estimate of this node's spectral radius; the exact FP64 value is computed below
+    // only for nodes that can hold the block maximum
+    float qf[V];
 #pragma unroll
-    for (int dir = 0; dir < D; ++dir) lam = fmax(lam, Ph::speed(pd, qnew, dir));
+    for (int v = 0; v < V; ++v) qf[v] = (float)qnew[v];
+    const float l32 = Ph::maxspeed(make_pp<float>(a.pp, cell), qf);
+    risky = !(l32 < 3.0e38f) || Ph::speed_is_ill_conditioned(qf);
+    if (!risky) atomicMax(&s_l32, __float_as_uint(l32));
+    lam32 = l32;
+  }
+  __syncthreads();
+  // exact FP64 lambda on the candidates: every node whose estimate is within 1e-4 (relative) of
+  // the block's largest estimate, or whose estimate is unreliable.  The FP32 relative error is
+  // far below 1e-4 for well-conditioned states, so the FP64 maximum is among the candidates.
+  if (valid && !bad && (risky || lam32 >= __uint_as_float(s_l32) * (1.0f - 1.0e-4f))) {
+    const PP<double> pd = make_pp<double>(a.pp, cell);
+    lam = Ph::maxspeed(pd, qnew_keep);
     bad |= !isfinite(lam);
   }
   // block max of lambda (non-negative doubles order like their bit patterns)
-  __syncthreads();
   if (valid && !bad) atomicMax(&s_lam, (unsigned long long)__double_as_longlong(lam));
   if (bad) atomicOr(&s_bad, 1u);
   __syncthreads();
@@ -431,8 +547,7 @@ __global__ void k_lambda(const __grid_constant__ StepArgs a) {
       bad |= !isfinite(q[v]);
     }
     const PP<double> pd = make_pp<double>(a.pp, cell);
-#pragma unroll
-    for (int dir = 0; dir < D; ++dir) lam = fmax(lam, Ph::speed(pd, q, dir));
+    lam = fmax(lam, Ph::maxspeed(pd, q));
   }
   bad |= !isfinite(lam);
   if (!bad) atomicMax(&s_lam, (unsigned long long)__double_as_longlong(lam));

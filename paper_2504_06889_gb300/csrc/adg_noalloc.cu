@@ -81,6 +81,7 @@ int pde_params_from(int pde, int dim, const double* p, int np, PdeParams* out) {
     out->g = p[0];
     if (!(out->g > 0)) return ADG_EINVAL;
   }
+  finalize_pde_params(out);
   return ADG_OK;
 }
 

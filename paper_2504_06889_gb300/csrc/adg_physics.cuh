@@ -43,24 +43,47 @@ template <class T> struct PP {
   T rho, irho, K, lam, mu, lam2mu, gm1, gamma, g, halfg, c;
 };
 
+// Per-cell parameters in the arithmetic type T (derived constants come precomputed from the
+// host; only a per-cell acoustic wave speed is read per cell).
 template <class T> __device__ __forceinline__ PP<T> make_pp(const PdeParams& p, int cell) {
   PP<T> r;
-  double K = p.K, c = p.pde == 0 ? sqrt(p.K / p.rho) : p.cp;
-  if (p.pde == 0 && p.cell_c) {
-    c = p.cell_c[cell];
-    K = p.rho * c * c;
-  }
   r.rho = tcast<T>(p.rho);
-  r.irho = tcast<T>(1.0 / p.rho);
-  r.K = tcast<T>(K);
+  r.irho = tcast<T>(p.irho);
+  r.K = tcast<T>(p.K);
   r.lam = tcast<T>(p.lam);
   r.mu = tcast<T>(p.mu);
-  r.lam2mu = tcast<T>(p.lam + 2.0 * p.mu);
-  r.gm1 = tcast<T>(p.gamma - 1.0);
+  r.lam2mu = tcast<T>(p.lam2mu);
+  r.gm1 = tcast<T>(p.gm1);
   r.gamma = tcast<T>(p.gamma);
   r.g = tcast<T>(p.g);
-  r.halfg = tcast<T>(0.5 * p.g);
-  r.c = tcast<T>(c < 0 ? -c : c);
+  r.halfg = tcast<T>(p.halfg);
+  r.c = tcast<T>(p.c);
+  if (p.pde == 0 && p.cell_c) {
+    const double c = p.cell_c[cell];
+    r.c = tcast<T>(c < 0 ? -c : c);
+    r.K = tcast<T>(p.rho * c * c);
+  }
+  return r;
+}
+
+template <> __device__ __forceinline__ PP<float> make_pp<float>(const PdeParams& p, int cell) {
+  PP<float> r;
+  r.rho = p.f_rho;
+  r.irho = p.f_irho;
+  r.K = p.f_K;
+  r.lam = p.f_lam;
+  r.mu = p.f_mu;
+  r.lam2mu = p.f_lam2mu;
+  r.gm1 = p.f_gm1;
+  r.gamma = p.f_gamma;
+  r.g = p.f_g;
+  r.halfg = p.f_halfg;
+  r.c = p.f_c;
+  if (p.pde == 0 && p.cell_c) {
+    const float c = (float)p.cell_c[cell];
+    r.c = fabsf(c);
+    r.K = p.f_rho * c * c;
+  }
   return r;
 }
 
@@ -81,6 +104,8 @@ template <int D> struct Phys<0, D> {
     }
   }
   template <class T> __device__ static __forceinline__ T speed(const PP<T>& p, const T*, int) { return p.c; }
+  template <class T> __device__ static __forceinline__ T maxspeed(const PP<T>& p, const T*) { return p.c; }
+  __device__ static __forceinline__ bool speed_is_ill_conditioned(const float*) { return false; }
 };
 
 // ---- linear elasticity, velocity-stress form, eq. (lin_elastic) ------------------------------
@@ -124,6 +149,8 @@ template <> struct Phys<1, 3> {
     F[2][8] = -q[2] * p.irho;
   }
   template <class T> __device__ static __forceinline__ T speed(const PP<T>& p, const T*, int) { return p.c; }
+  template <class T> __device__ static __forceinline__ T maxspeed(const PP<T>& p, const T*) { return p.c; }
+  __device__ static __forceinline__ bool speed_is_ill_conditioned(const float*) { return false; }
 };
 
 template <> struct Phys<1, 2> {
@@ -144,6 +171,8 @@ template <> struct Phys<1, 2> {
     F[1][4] = -q[1] * p.irho;
   }
   template <class T> __device__ static __forceinline__ T speed(const PP<T>& p, const T*, int) { return p.c; }
+  template <class T> __device__ static __forceinline__ T maxspeed(const PP<T>& p, const T*) { return p.c; }
+  __device__ static __forceinline__ bool speed_is_ill_conditioned(const float*) { return false; }
 };
 
 // ---- compressible Euler, eq. (euler_eq), ideal gas ---------------------------------------------
@@ -174,10 +203,40 @@ template <int D> struct Phys<2, D> {
       F[dir][1 + D] = u[dir] * Ep;
     }
   }
+  // |u_dir| + sqrt(gamma p / rho) with one reciprocal of rho
   template <class T> __device__ static __forceinline__ T speed(const PP<T>& p, const T* q, int dir) {
     T u[D];
-    const T pr = pressure(p, q, u);
-    return tabs(u[dir]) + tsqrt(p.gamma * pr / q[0]);
+    const T ir = T(1) / q[0];
+    T ke = T(0);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      u[a] = q[1 + a] * ir;
+      ke += q[1 + a] * u[a];
+    }
+    const T pr = p.gm1 * (q[1 + D] - T(0.5) * ke);
+    return tabs(u[dir]) + tsqrt(p.gamma * pr * ir);
+  }
+  // max over directions of the spectral radius: max_d |u_d| + c
+  template <class T> __device__ static __forceinline__ T maxspeed(const PP<T>& p, const T* q) {
+    const T ir = T(1) / q[0];
+    T ke = T(0), um = T(0);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const T u = q[1 + a] * ir;
+      ke += q[1 + a] * u;
+      um = tmax(um, tabs(u));
+    }
+    const T pr = p.gm1 * (q[1 + D] - T(0.5) * ke);
+    return um + tsqrt(p.gamma * pr * ir);
+  }
+  // the FP32 speed loses accuracy when the internal energy E - |m|^2/(2 rho) is a small
+  // difference of large terms, or when rho is not positive
+  __device__ static __forceinline__ bool speed_is_ill_conditioned(const float* q) {
+    float ke = 0.0f;
+#pragma unroll
+    for (int a = 0; a < D; ++a) ke += q[1 + a] * q[1 + a];
+    ke *= 0.5f / q[0];
+    return !(q[0] > 0.0f) || !(q[1 + D] - ke > 1.0e-2f * q[1 + D]);
   }
 };
 
@@ -200,6 +259,10 @@ template <> struct Phys<3, 2> {
   template <class T> __device__ static __forceinline__ T speed(const PP<T>& p, const T* q, int dir) {
     return tabs(q[1 + dir] / q[0]) + tsqrt(p.g * q[0]);
   }
+  template <class T> __device__ static __forceinline__ T maxspeed(const PP<T>& p, const T* q) {
+    return tmax(tabs(q[1]), tabs(q[2])) / q[0] + tsqrt(p.g * q[0]);
+  }
+  __device__ static __forceinline__ bool speed_is_ill_conditioned(const float* q) { return !(q[0] > 0.0f); }
 };
 
 }  // namespace adg
