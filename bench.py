@@ -50,8 +50,14 @@ MIXES = {
     "fp32pred": {"picard": "fp32", "predictor": "fp32", "riemann": "fp64", "corrector": "fp64"},
     # all arithmetic outside the FP64 state/accumulation/CFL in FP32, traces stored in FP32
     "fp32": {"picard": "fp32", "predictor": "fp32", "riemann": "fp32", "corrector": "fp32"},
+    # Picard contractions on the tensor cores (16-bit inputs, FP32 accumulation, per-cell
+    # power-of-two scaling, compensated hi/lo last sweep); everything else as in "fp32"
+    "bf16tc": {"picard": "bf16", "predictor": "fp32", "riemann": "fp32", "corrector": "fp32"},
+    "fp16tc": {"picard": "fp16", "predictor": "fp32", "riemann": "fp32", "corrector": "fp32"},
 }
-DTYPE = {"fp64": "f64", "fp32pred": "f32+f64", "fp32": "f32+f64"}
+MIX_FLAGS = {"bf16tc": 1 | 2, "fp16tc": 1 | 2}
+DTYPE = {"fp64": "f64", "fp32pred": "f32+f64", "fp32": "f32+f64", "bf16tc": "bf16+f32+f64",
+         "fp16tc": "f16+f32+f64"}
 
 
 def predictor_flops_per_cell(pde, dim, N, iters=None):
@@ -239,7 +245,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="euler3d", choices=sorted(I.WORKLOADS))
     ap.add_argument("--cells", type=int, default=0, help="override cells per direction")
-    ap.add_argument("--mixes", default="fp64,fp32pred,fp32")
+    ap.add_argument("--mixes", default="fp64,fp32pred,fp32,bf16tc,fp16tc")
     ap.add_argument("--headline", default="fp32")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -267,7 +273,8 @@ def main():
     clocks = None
     for mix in mixes:
         prec = MIXES[mix]
-        s = adg.Solver(wl.dim, wl.N, wl.cells, wl.pde, wl.params, cfl=wl.cfl, precision=prec)
+        s = adg.Solver(wl.dim, wl.N, wl.cells, wl.pde, wl.params, cfl=wl.cfl, precision=prec,
+                       flags=MIX_FLAGS.get(mix, 0))
         s.set_initial(wl.scenario, wl.sp)
         s.step(args.warmup)
         torch.cuda.synchronize()
@@ -302,7 +309,7 @@ def main():
         # roofline of the dominant kernel (the predictor)
         cells = wl.ncells
         fl = predictor_flops_per_cell(wl.pde, wl.dim, wl.N) * cells
-        kind = "fp32" if prec["picard"] == "fp32" else "fp64"
+        kind = "fp64" if prec["picard"] == "fp64" else "fp32"
         sm_mhz = peaks.get("sm_max_mhz", 2070.0)
         pk = alu_peak_tflops(kind, sm_mhz)
         ach = fl / (ms_pred / args.steps * 1e-3) / 1e12

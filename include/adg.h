@@ -76,7 +76,8 @@ enum adg_prec { ADG_FP64 = 0, ADG_FP32 = 1, ADG_BF16 = 2, ADG_FP16 = 3, ADG_FP8E
 
 enum adg_flags {
   ADG_F_COMPENSATED_LAST = 1, /* tensor-core Picard: last sweep with split hi/lo products */
-  ADG_F_PER_CELL_SCALE = 2    /* tensor-core Picard: power-of-two scaling per cell */
+  ADG_F_PER_CELL_SCALE = 2,   /* tensor-core Picard: power-of-two scaling per cell */
+  ADG_F_COMPENSATED_TWO = 4   /* tensor-core Picard: last two sweeps with hi/lo products */
 };
 
 /* Scenario closed forms for adg_set_initial() / adg_error_vs_exact(); the
@@ -113,12 +114,15 @@ ADG_API int adg_init_mesh(adg_ctx* c, int dim, int order_N, const int* cells, co
 ADG_API int adg_set_pde(adg_ctx* c, int pde, const double* params, int nparams);
 
 /* Precision of one kernel (Sec. 3.1).  Built combinations:
- *   PICARD     FP64, FP32 (SIMT); BF16, FP16 (tensor cores, FP32 accumulation)
+ *   PICARD     FP64, FP32 (SIMT, must equal PREDICTOR); BF16, FP16 (tensor cores, FP32
+ *              accumulation, 3D meshes, PREDICTOR FP32, CORRECTOR FP32 or FP64); flags
+ *              (ADG_F_*) given with the PICARD call select compensation and per-cell scaling
  *   PREDICTOR  FP64, FP32
- *   RIEMANN    FP64, FP32, BF16
- *   CORRECTOR  FP64, FP32, BF16
+ *   RIEMANN    FP64, FP32, BF16 (bf16 built for shallow water)
+ *   CORRECTOR  FP64, FP32, BF16 (bf16 built for shallow water)
  *   STORAGE    FP64
- * Others return ADG_EUNSUPPORTED. */
+ * Others return ADG_EUNSUPPORTED (at the call, or at the first step for mixes that depend on
+ * the mesh and PDE). */
 ADG_API int adg_set_kernel_precision(adg_ctx* c, int kernel, int prec, int flags);
 
 /* C_CFL of eq. (CFL_condition) (dt = cfl h / (d (2N+1) lambda_max)) and the

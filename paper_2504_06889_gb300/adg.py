@@ -17,7 +17,7 @@ OK, EINVAL, ENOTINIT, ECUDA, ENONFINITE, ETIMEOUT, EUNSUPPORTED, ENOMEM = 0, -1,
 ACOUSTIC, ELASTIC, EULER, SWE = 0, 1, 2, 3
 K_PICARD, K_PREDICTOR, K_RIEMANN, K_CORRECTOR, K_STORAGE = 0, 1, 2, 3, 4
 FP64, FP32, BF16, FP16, FP8E4M3 = 0, 1, 2, 3, 4
-F_COMPENSATED_LAST, F_PER_CELL_SCALE = 1, 2
+F_COMPENSATED_LAST, F_PER_CELL_SCALE, F_COMPENSATED_TWO = 1, 2, 4
 SC_PLANAR, SC_EULER_WAVE, SC_SWE_MODES, SC_GAUSS_PULSE = 0, 1, 2, 3
 PREC_NAMES = {"fp64": FP64, "fp32": FP32, "bf16": BF16, "fp16": FP16, "fp8": FP8E4M3}
 
@@ -115,6 +115,8 @@ class Solver:
                   "corrector": K_CORRECTOR, "storage": K_STORAGE}[k] if isinstance(k, str) else k
             pv = PREC_NAMES[p] if isinstance(p, str) else p
             self._check(self.lib.adg_set_kernel_precision(self.ctx, kk, pv, flags))
+        if flags and "picard" not in (precision or {}):
+            self._check(self.lib.adg_set_kernel_precision(self.ctx, K_PICARD, FP64, flags))
         nd = C.c_size_t()
         nv = C.c_int()
         self._check(self.lib.adg_state_size(self.ctx, C.byref(nd), C.byref(nv)))

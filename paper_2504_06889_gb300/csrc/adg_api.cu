@@ -235,6 +235,8 @@ static void fill_step_args(const adg_ctx* c, StepArgs* a) {
   a->hmin = hmin;
   a->cfl = c->cfl;
   a->picard_iters = c->picard_iters > 0 ? c->picard_iters : c->N + 1;
+  a->comp_sweeps = (c->flags & ADG_F_COMPENSATED_TWO) ? 2 : (c->flags & ADG_F_COMPENSATED_LAST) ? 1 : 0;
+  a->per_cell_scale = (c->flags & ADG_F_PER_CELL_SCALE) ? 1 : 0;
   a->tab = c->tab;
   a->pp = c->pp;
 }
@@ -375,13 +377,14 @@ int adg_set_kernel_precision(adg_ctx* c, int kernel, int prec, int flags) {
   if (prec < 0 || prec > ADG_FP8E4M3) return fail(c, ADG_EINVAL, "unknown precision");
   if (kernel == ADG_K_STORAGE && prec != ADG_FP64)
     return fail(c, ADG_EUNSUPPORTED, "storage precision other than FP64 is not built");
-  if (prec == ADG_FP16 || prec == ADG_FP8E4M3)
-    return fail(c, ADG_EUNSUPPORTED, "precision not built for this kernel");
-  if ((kernel == ADG_K_PICARD || kernel == ADG_K_PREDICTOR) && prec == ADG_BF16)
-    return fail(c, ADG_EUNSUPPORTED, "bf16 predictor not built");
+  if (prec == ADG_FP8E4M3) return fail(c, ADG_EUNSUPPORTED, "fp8 not built");
+  if (kernel == ADG_K_PREDICTOR && (prec == ADG_BF16 || prec == ADG_FP16))
+    return fail(c, ADG_EUNSUPPORTED, "the predictor's final stage runs in FP32 or FP64");
+  if ((kernel == ADG_K_RIEMANN || kernel == ADG_K_CORRECTOR) && prec == ADG_FP16)
+    return fail(c, ADG_EUNSUPPORTED, "fp16 Riemann/corrector not built");
   if (kernel == ADG_K_CORRECTOR && prec != c->prec[ADG_K_CORRECTOR]) c->have_bufs = false;
   c->prec[kernel] = prec;
-  c->flags = flags;
+  if (kernel == ADG_K_PICARD) c->flags = flags;
   return ADG_OK;
 }
 
@@ -515,9 +518,16 @@ int adg_get_state(adg_ctx* c, double* Qout, int to_host) {
 static int select_kernels(adg_ctx* c, StepFn* pred, StepFn* corr) {
   const int pic = c->prec[ADG_K_PICARD], prd = c->prec[ADG_K_PREDICTOR];
   const int rie = c->prec[ADG_K_RIEMANN], cor = c->prec[ADG_K_CORRECTOR];
-  if (pic != prd) return fail(c, ADG_EUNSUPPORTED, "SIMT predictor needs PICARD == PREDICTOR precision");
-  if (pic > P32 || rie > PBF16 || cor > PBF16) return fail(c, ADG_EUNSUPPORTED, "precision mix not built");
-  *pred = c->entry->predictor[pic][cor];
+  if (rie > PBF16 || cor > PBF16) return fail(c, ADG_EUNSUPPORTED, "precision mix not built");
+  if (pic == PBF16 || pic == PF16) {
+    if (prd != P32) return fail(c, ADG_EUNSUPPORTED, "tensor-core Picard needs an FP32 predictor stage");
+    if (cor > P32) return fail(c, ADG_EUNSUPPORTED, "tensor-core Picard writes FP32 or FP64 traces");
+    *pred = c->entry->predictor_tc[pic == PF16 ? 1 : 0][cor];
+  } else {
+    if (pic != prd) return fail(c, ADG_EUNSUPPORTED, "SIMT predictor needs PICARD == PREDICTOR precision");
+    if (pic > P32) return fail(c, ADG_EUNSUPPORTED, "precision mix not built");
+    *pred = c->entry->predictor[pic][cor];
+  }
   *corr = c->entry->corrector[rie][cor];
   if (!*pred || !*corr) return fail(c, ADG_EUNSUPPORTED, "precision mix not built for this (PDE, d, N)");
   return ADG_OK;
@@ -550,6 +560,7 @@ int adg_step(adg_ctx* c, int nsteps, double* t_out, double* dt_last_out) {
   ADG_CUDA(c, cudaStreamSynchronize(c->stream));
   if (t_out) *t_out = s.t;
   if (dt_last_out) *dt_last_out = s.dt_last;
+  if (s.timeout) return fail(c, ADG_ETIMEOUT, "a bounded device wait ran out; the state is not valid");
   if (s.bad) return fail(c, ADG_ENONFINITE, "non-finite value in the state; t is the last good time");
   return ADG_OK;
 }
@@ -603,6 +614,7 @@ int adg_step_timed(adg_ctx* c, int nsteps, double* t_out, double* ms_kernels) {
   ADG_CUDA(c, cudaStreamSynchronize(c->stream));
   if (t_out) *t_out = sv.t;
   if (sv.bad) rc = fail(c, ADG_ENONFINITE, "non-finite value in the state; t is the last good time");
+  if (sv.timeout) rc = fail(c, ADG_ETIMEOUT, "a bounded device wait ran out; the state is not valid");
   return rc;
 }
 

@@ -45,6 +45,8 @@ struct DevScalars {
   unsigned int nonfinite;       // set by a corrector block that saw Inf/NaN this step
   unsigned int bad;             // latched by the last corrector block: stop advancing
   unsigned int steps;           // good steps taken since the state was set
+  unsigned int timeout;         // a bounded device wait ran out (tensor-core predictor)
+  unsigned int pad_;
 };
 
 struct StepArgs {
@@ -57,6 +59,8 @@ struct StepArgs {
   double hmin;
   double cfl;
   int picard_iters;
+  int comp_sweeps;     // tensor-core Picard: number of final sweeps with hi/lo compensation
+  int per_cell_scale;  // tensor-core Picard: power-of-two scaling of the flux per cell
   int pad;
   Tables tab;
   PdeParams pp;
@@ -103,6 +107,8 @@ struct Entry {
   int V, NS, NF;
   StepFn predictor[3][3];
   StepFn corrector[3][3];
+  // tensor-core Picard with FP32 final stage: [0 = bf16, 1 = fp16][trace prec]
+  StepFn predictor_tc[2][3];
   LamFn lambda;
   InitFn init;
   L2Fn l2;

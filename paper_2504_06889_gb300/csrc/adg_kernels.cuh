@@ -128,6 +128,107 @@ template <class C, class T, class TP> struct PredSmem {
   static constexpr size_t total = big + tables;
 };
 
+// Final stage of the predictor (shared by the SIMT and tensor-core predictors): fluxes of the
+// last iterate, time averages Qbar = sum_k w_k q_k and Fbar = sum_k w_k F(q_k), the volume
+// integral added to Q in FP64 and the face traces of Qbar and Fbar.n written in TS.
+// smem_fin: CPB * (D V PD + V NS) values of TP; must not alias the tables.
+template <class C, class T, class TP, class TS>
+__device__ __forceinline__ void predictor_final(const StepArgs& a, const T (*q)[C::V], TP* smem_fin,
+                                                const TP* sVm, const TP* sw, const TP* sp0, const TP* sp1,
+                                                double dt, int lc, int i, int cell, bool valid, int cl,
+                                                const int* idx, const int* pb, bool owner = true) {
+  using Ph = Phys<C::PDE, C::D>;
+  constexpr int n = C::n, V = C::V, D = C::D, NS = C::NS, NF = C::NF;
+  constexpr int S = Pencil<C>::S, PD = Pencil<C>::PER_DIR;
+  // ---- final flux, time averages (Qbar = sum_k w_k q_k, Fbar = sum_k w_k F(q_k)) ---------------
+  const PP<TP> ppP = make_pp<TP>(a.pp, cl);
+  TP Fb[D][V], Qb[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    Qb[v] = TP(0);
+#pragma unroll
+    for (int dir = 0; dir < D; ++dir) Fb[dir][v] = TP(0);
+  }
+#pragma unroll
+  for (int k = 0; k < n; ++k) {
+    TP qk[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) qk[v] = (TP)q[k][v];
+    TP F[D][V];
+    Ph::flux(ppP, qk, F);
+    const TP wk = sw[k];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      Qb[v] += wk * qk[v];
+#pragma unroll
+      for (int dir = 0; dir < D; ++dir) Fb[dir][v] += wk * F[dir][v];
+    }
+  }
+  // shared: Fbar [dir][v][pencil layout], Qbar [v][node]
+  TP* sFb = smem_fin + (size_t)lc * (D * V * PD + V * NS);
+  TP* sQb = sFb + D * V * PD;
+  if (owner) {
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      sQb[v * NS + i] = Qb[v];
+#pragma unroll
+      for (int dir = 0; dir < D; ++dir)
+        if (Ph::nz(dir, v)) sFb[(dir * V + v) * PD + pb[dir] + idx[dir]] = Fb[dir][v];
+    }
+  }
+  __syncthreads();
+
+  // ---- volume integral: Q_i += dt sum_dir (1/h_dir) sum_m Vm[i_dir][m] Fbar(i[dir<-m]) --------
+  if (valid && owner) {
+    double* Qw = a.Q + (size_t)cell * V * NS;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      TP vol = TP(0);
+#pragma unroll
+      for (int dir = 0; dir < D; ++dir) {
+        if (!Ph::nz(dir, v)) continue;
+        const TP* Fp = sFb + (dir * V + v) * PD + pb[dir];
+        const TP* Vr = sVm + idx[dir] * n;
+        TP s = TP(0);
+#pragma unroll
+        for (int m = 0; m < n; ++m) s += Vr[m] * Fp[m];
+        vol += s * (TP)a.invh[dir];
+      }
+      Qw[v * NS + i] += dt * (double)vol;
+    }
+  }
+
+  // ---- face traces: trace(dir, side)_j = sum_a psi_a(side) X(node(dir, j, a)) ------------------
+  if (valid && owner) {
+    TS* tr = reinterpret_cast<TS*>(a.traces) + (size_t)cell * D * 2 * 2 * V * NF;
+    constexpr int items = D * 2 * 2 * V * NF;
+    for (int it = i; it < items; it += NS) {
+      const int j = it % NF;
+      const int v = (it / NF) % V;
+      const int qf = (it / (NF * V)) % 2;
+      const int side = (it / (NF * V * 2)) % 2;
+      const int dir = it / (NF * V * 4);
+      const TP* psi = side ? sp1 : sp0;
+      TP s = TP(0);
+      if (qf == 0) {
+#pragma unroll
+        for (int m = 0; m < n; ++m) s += psi[m] * sQb[v * NS + node_of_face<D, n>(dir, j, m)];
+      } else {
+        bool nzv = false;
+#pragma unroll
+        for (int dd = 0; dd < D; ++dd)
+          if (dd == dir) nzv = Ph::nz(dd, v);
+        if (nzv) {
+          const TP* Fp = sFb + (dir * V + v) * PD + j * S;
+#pragma unroll
+          for (int m = 0; m < n; ++m) s += psi[m] * Fp[m];
+        }
+      }
+      tr[it] = (TS)s;
+    }
+  }
+}
+
 // ------------------------------------------------------------------------------------------------
 // predictor + volume integral + face traces
 // ------------------------------------------------------------------------------------------------
@@ -246,91 +347,8 @@ __global__ void __launch_bounds__(C::THREADS) k_predictor(const __grid_constant_
   }
   __syncthreads();
 
-  // ---- final flux, time averages (Qbar = sum_k w_k q_k, Fbar = sum_k w_k F(q_k)) ---------------
-  const PP<TP> ppP = make_pp<TP>(a.pp, cl);
-  TP Fb[D][V], Qb[V];
-#pragma unroll
-  for (int v = 0; v < V; ++v) {
-    Qb[v] = TP(0);
-#pragma unroll
-    for (int dir = 0; dir < D; ++dir) Fb[dir][v] = TP(0);
-  }
-#pragma unroll
-  for (int k = 0; k < n; ++k) {
-    TP qk[V];
-#pragma unroll
-    for (int v = 0; v < V; ++v) qk[v] = (TP)q[k][v];
-    TP F[D][V];
-    Ph::flux(ppP, qk, F);
-    const TP wk = sw[k];
-#pragma unroll
-    for (int v = 0; v < V; ++v) {
-      Qb[v] += wk * qk[v];
-#pragma unroll
-      for (int dir = 0; dir < D; ++dir) Fb[dir][v] += wk * F[dir][v];
-    }
-  }
-  // shared: Fbar [dir][v][pencil layout], Qbar [v][node]
-  TP* sFb = reinterpret_cast<TP*>(smem_raw) + (size_t)lc * (D * V * PD + V * NS);
-  TP* sQb = sFb + D * V * PD;
-#pragma unroll
-  for (int v = 0; v < V; ++v) {
-    sQb[v * NS + i] = Qb[v];
-#pragma unroll
-    for (int dir = 0; dir < D; ++dir)
-      if (Ph::nz(dir, v)) sFb[(dir * V + v) * PD + pb[dir] + idx[dir]] = Fb[dir][v];
-  }
-  __syncthreads();
-
-  // ---- volume integral: Q_i += dt sum_dir (1/h_dir) sum_m Vm[i_dir][m] Fbar(i[dir<-m]) --------
-  if (valid) {
-    double* Qw = a.Q + (size_t)cell * V * NS;
-#pragma unroll
-    for (int v = 0; v < V; ++v) {
-      TP vol = TP(0);
-#pragma unroll
-      for (int dir = 0; dir < D; ++dir) {
-        if (!Ph::nz(dir, v)) continue;
-        const TP* Fp = sFb + (dir * V + v) * PD + pb[dir];
-        const TP* Vr = sVm + idx[dir] * n;
-        TP s = TP(0);
-#pragma unroll
-        for (int m = 0; m < n; ++m) s += Vr[m] * Fp[m];
-        vol += s * (TP)a.invh[dir];
-      }
-      Qw[v * NS + i] += dt * (double)vol;
-    }
-  }
-
-  // ---- face traces: trace(dir, side)_j = sum_a psi_a(side) X(node(dir, j, a)) ------------------
-  if (valid) {
-    TS* tr = reinterpret_cast<TS*>(a.traces) + (size_t)cell * D * 2 * 2 * V * NF;
-    constexpr int items = D * 2 * 2 * V * NF;
-    for (int it = i; it < items; it += NS) {
-      const int j = it % NF;
-      const int v = (it / NF) % V;
-      const int qf = (it / (NF * V)) % 2;
-      const int side = (it / (NF * V * 2)) % 2;
-      const int dir = it / (NF * V * 4);
-      const TP* psi = side ? sp1 : sp0;
-      TP s = TP(0);
-      if (qf == 0) {
-#pragma unroll
-        for (int m = 0; m < n; ++m) s += psi[m] * sQb[v * NS + node_of_face<D, n>(dir, j, m)];
-      } else {
-        bool nzv = false;
-#pragma unroll
-        for (int dd = 0; dd < D; ++dd)
-          if (dd == dir) nzv = Ph::nz(dd, v);
-        if (nzv) {
-          const TP* Fp = sFb + (dir * V + v) * PD + j * S;
-#pragma unroll
-          for (int m = 0; m < n; ++m) s += psi[m] * Fp[m];
-        }
-      }
-      tr[it] = (TS)s;
-    }
-  }
+  predictor_final<C, T, TP, TS>(a, q, reinterpret_cast<TP*>(smem_raw), sVm, sw, sp0, sp1, dt, lc, i, cell,
+                                valid, cl, idx, pb);
 }
 
 // ------------------------------------------------------------------------------------------------

@@ -55,6 +55,7 @@ __global__ void k_noalloc_reset(DevScalars* sc, double t) {
     sc->nonfinite = 0u;
     sc->bad = 0u;
     sc->steps = 0u;
+    sc->timeout = 0u;
   }
 }
 

@@ -1,10 +1,19 @@
 // Kernel instantiations: linear elasticity, velocity-stress form (Sec. 4.2).
 #include "adg_kernels.cuh"
+#include "adg_tc.cuh"
 
 namespace adg {
 void register_elastic() {
-  register_entry(make_entry<1, 3, 6, false>());  // 3D, N = 6 (P+S wave workload)
-  register_entry(make_entry<1, 3, 2, false>());
+  {
+    Entry e = make_entry<1, 3, 6, false>();
+    add_tc<1, 3, 6>(e);
+    register_entry(e);
+  }  // 3D, N = 6 (P+S wave workload)
+  {
+    Entry e = make_entry<1, 3, 2, false>();
+    add_tc<1, 3, 2>(e);
+    register_entry(e);
+  }
   register_entry(make_entry<1, 2, 3, false>());
 }
 }  // namespace adg

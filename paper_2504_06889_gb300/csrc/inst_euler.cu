@@ -1,10 +1,19 @@
 // Kernel instantiations: compressible Euler (Sec. 4.3).
 #include "adg_kernels.cuh"
+#include "adg_tc.cuh"
 
 namespace adg {
 void register_euler() {
-  register_entry(make_entry<2, 3, 5, false>());  // 3D, N = 5 (density-wave workload)
+  {
+    Entry e = make_entry<2, 3, 5, false>();
+    add_tc<2, 3, 5>(e);
+    register_entry(e);
+  }  // 3D, N = 5 (density-wave workload)
   register_entry(make_entry<2, 2, 3, false>());
-  register_entry(make_entry<2, 3, 2, false>());
+  {
+    Entry e = make_entry<2, 3, 2, false>();
+    add_tc<2, 3, 2>(e);
+    register_entry(e);
+  }
 }
 }  // namespace adg

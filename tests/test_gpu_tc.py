@@ -1,0 +1,133 @@
+"""Tensor-core (tcgen05) Picard predictor: 16-bit inputs, FP32 accumulation, per-cell
+power-of-two scaling and a compensated (hi/lo split) last sweep, against the FP64 oracle.
+
+Bound: with the last sweep compensated, the predictor's error is the rounding of the 16-bit
+inputs (unit roundoff u = 2^-9 for bf16, 2^-12 for fp16) damped once by the Picard map
+(about the local Courant number) and multiplied by dt/h in the update, so the relative
+eq.-(L2gauss) distance after s steps stays below s * u * 0.1 for these CFL numbers.
+"""
+import numpy as np
+import pytest
+
+from paper_2504_06889_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+U = {"bf16": 2.0 ** -9, "fp16": 2.0 ** -12}
+
+
+@pytest.fixture(scope="module")
+def adg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2504_06889_gb300 import adg as A
+    from paper_2504_06889_gb300 import build
+
+    build.build()
+    A.load()
+    return A
+
+
+def acoustic3d(cells, N=2):
+    w = I.acoustic_wave((2 * np.pi, -2 * np.pi, 4 * np.pi), 1.0, 2.0)
+    return I.Workload("ac3", 3, N, cells, I.ACOUSTIC, (1.0, 2.0), I.SC_PLANAR, I.planar(4, [w]), 3)
+
+
+CASES = [
+    I.euler3d_wave(N=5).with_cells((3, 2, 2), 3),
+    I.euler3d_wave(N=2).with_cells((3, 3, 3), 3),
+    I.elastic3d_planar(N=6).with_cells((2, 2, 2), 2),
+    I.elastic3d_planar(N=2).with_cells((3, 2, 2), 3),
+    I.acoustic3d_pulse(N=4).with_cells((3, 3, 2), 3),
+    acoustic3d((3, 3, 3)),
+]
+IDS = [f"{w.name.split('_')[0]}_N{w.N}_{'x'.join(map(str, w.cells))}" for w in CASES]
+
+
+def run(adg, wl, pic, flags, steps, corrector="fp32"):
+    s = adg.Solver(wl.dim, wl.N, wl.cells, wl.pde, wl.params, cfl=wl.cfl,
+                   precision={"picard": pic, "predictor": "fp32", "riemann": corrector,
+                              "corrector": corrector}, flags=flags)
+    s.set_initial(wl.scenario, wl.sp)
+    t, _ = s.step(steps)
+    return s.state(), t
+
+
+@pytest.mark.parametrize("pic", ["bf16", "fp16"])
+@pytest.mark.parametrize("wl", CASES, ids=IDS)
+def test_tc_picard_compensated_within_bound(adg, oracle_mod, wl, pic):
+    M = oracle_mod.Mesh(wl.dim, wl.N, wl.cells, wl.pde, wl.params, cfl=wl.cfl)
+    Qo = M.interpolate(wl.scenario, wl.sp)
+    to, _ = M.run(Qo, wl.steps)
+    Qg, tg = run(adg, wl, pic, adg.F_COMPENSATED_LAST | adg.F_PER_CELL_SCALE, wl.steps)
+    assert np.all(np.isfinite(Qg))
+    rel = M.l2_diff(Qg, Qo)[1] / M.l2_diff(Qo, M.zeros())[1]
+    assert rel <= wl.steps * U[pic] * 0.1, rel
+    assert abs(tg - to) <= 1e-5 * to
+
+
+@pytest.mark.parametrize("wl", CASES[:3], ids=IDS[:3])
+def test_compensation_and_format_order(adg, oracle_mod, wl):
+    """Compensation reduces the error; fp16 (10-bit mantissa) beats bf16 (7-bit)."""
+    M = oracle_mod.Mesh(wl.dim, wl.N, wl.cells, wl.pde, wl.params, cfl=wl.cfl)
+    Qo = M.interpolate(wl.scenario, wl.sp)
+    M.run(Qo, wl.steps)
+    norm = M.l2_diff(Qo, M.zeros())[1]
+    err = {}
+    for pic in ("bf16", "fp16"):
+        for flags in (adg.F_PER_CELL_SCALE, adg.F_PER_CELL_SCALE | adg.F_COMPENSATED_LAST,
+                      adg.F_PER_CELL_SCALE | adg.F_COMPENSATED_TWO):
+            Qg, _ = run(adg, wl, pic, flags, wl.steps)
+            err[(pic, flags)] = M.l2_diff(Qg, Qo)[1] / norm
+    S, C1, C2 = adg.F_PER_CELL_SCALE, adg.F_PER_CELL_SCALE | adg.F_COMPENSATED_LAST, \
+        adg.F_PER_CELL_SCALE | adg.F_COMPENSATED_TWO
+    for pic in ("bf16", "fp16"):
+        assert err[(pic, C1)] < err[(pic, S)], err
+        assert err[(pic, C2)] <= err[(pic, C1)] * 1.01, err
+    assert err[("fp16", C1)] < err[("bf16", C1)], err
+
+
+def test_tc_fp64_traces(adg, oracle_mod):
+    wl = CASES[0]
+    M = oracle_mod.Mesh(wl.dim, wl.N, wl.cells, wl.pde, wl.params, cfl=wl.cfl)
+    Qo = M.interpolate(wl.scenario, wl.sp)
+    M.run(Qo, wl.steps)
+    Qg, _ = run(adg, wl, "fp16", adg.F_COMPENSATED_LAST | adg.F_PER_CELL_SCALE, wl.steps,
+                corrector="fp64")
+    rel = M.l2_diff(Qg, Qo)[1] / M.l2_diff(Qo, M.zeros())[1]
+    assert rel <= wl.steps * U["fp16"] * 0.1
+
+
+def test_tc_full_size_sampled_cells(adg, oracle_mod):
+    """Euler N=5 on 64^3 cells (the benchmark configuration), one step, sampled cells."""
+    wl = I.euler3d_wave()
+    M = oracle_mod.Mesh(wl.dim, wl.N, wl.cells, wl.pde, wl.params, cfl=wl.cfl)
+    Q0 = M.interpolate(wl.scenario, wl.sp)
+    dt = M.dt(Q0)
+    ids = np.unique(np.concatenate([[0, M.ncells - 1],
+                                    np.random.default_rng(12).integers(0, M.ncells, size=14)]))
+    ref = M.step_cells(Q0, dt, ids)
+    for pic in ("bf16", "fp16"):
+        s = adg.Solver(wl.dim, wl.N, wl.cells, wl.pde, wl.params, cfl=wl.cfl,
+                       precision={"picard": pic, "predictor": "fp32", "riemann": "fp32",
+                                  "corrector": "fp32"},
+                       flags=adg.F_COMPENSATED_LAST | adg.F_PER_CELL_SCALE)
+        s.set_state(Q0, 0.0)
+        s.step(1)
+        Qg = s.Q[torch.from_numpy(ids).cuda()].cpu().numpy()
+        for j in range(len(ids)):
+            rel = np.sqrt(np.sum((Qg[j] - ref[j]) ** 2) / np.sum(ref[j] ** 2))
+            assert rel <= U[pic] * 0.1, (pic, ids[j], rel)
+        s.close()
+        del s
+        torch.cuda.empty_cache()
+
+
+def test_unsupported_tc_combinations(adg):
+    with pytest.raises(adg.AdgError) as e:
+        s = adg.Solver(2, 3, (4, 4), adg.ACOUSTIC, (1.0, 1.0),
+                       precision={"picard": "bf16", "predictor": "fp32"})
+        s.set_initial(adg.SC_PLANAR, I.planar(3, []) + 0.0)
+        s.step(1)
+    assert e.value.code == adg.EUNSUPPORTED
