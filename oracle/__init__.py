@@ -78,6 +78,13 @@ def _load():
             lib.or_step.restype = C.c_double
             lib.or_run.argtypes = [P, dp, C.c_int, dp, dp]
             lib.or_step_cells.argtypes = [P, dp, C.c_double, C.c_int, ip, dp]
+            lib.or_receiver_weights.argtypes = [P, dp, ip, dp]
+            lib.or_receivers_eval.argtypes = [P, dp, C.c_int, dp, dp]
+            lib.or_misfit.argtypes = [P, dp, C.c_int, C.c_int, dp, dp, dp]
+            lib.or_misfit.restype = C.c_double
+            lib.or_adjoint_step.argtypes = [P, dp, C.c_double, dp, dp, dp]
+            lib.or_adjoint.argtypes = [P, dp, C.c_int, C.c_int, dp, dp, dp, dp]
+            lib.or_adjoint.restype = C.c_double
             lib.or_rusanov.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int, dp, dp, dp, dp, dp]
             _lib = lib
     return _lib
@@ -235,6 +242,51 @@ class Mesh:
         _load().or_step_cells(self._h, _dp(Q), dt, len(ids), ids.ctypes.data_as(C.POINTER(C.c_int)),
                               _dp(out))
         return out
+
+    # -- receivers, misfit, discrete adjoint (linear acoustics) -------------
+    def receiver_weights(self, x):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        c = C.c_int()
+        w = np.zeros(self.NS)
+        _load().or_receiver_weights(self._h, _dp(x), C.byref(c), _dp(w))
+        return c.value, w
+
+    def receivers(self, Q, xyz):
+        Q = np.ascontiguousarray(Q, dtype=np.float64)
+        xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+        out = np.zeros(len(xyz))
+        _load().or_receivers_eval(self._h, _dp(Q), len(xyz), _dp(xyz), _dp(out))
+        return out
+
+    def misfit(self, Q, nsteps, xyz, observed=None):
+        """Forward nsteps from Q (in place); returns (J, record[nsteps][nrecv])."""
+        assert Q.dtype == np.float64 and Q.flags["C_CONTIGUOUS"]
+        xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+        rec = np.zeros((nsteps, len(xyz)))
+        obs = None if observed is None else np.ascontiguousarray(observed, dtype=np.float64)
+        J = _load().or_misfit(self._h, _dp(Q), int(nsteps), len(xyz), _dp(xyz),
+                              _dp(obs) if obs is not None else C.POINTER(C.c_double)(), _dp(rec))
+        return J, rec
+
+    def adjoint_step(self, Qn, dt, lam):
+        """lam: dJ/dQ^{n+1} -> dJ/dQ^n (in place); returns (gK, gS) of this step."""
+        Qn = np.ascontiguousarray(Qn, dtype=np.float64)
+        assert lam.dtype == np.float64 and lam.flags["C_CONTIGUOUS"]
+        gK = np.zeros(self.ncells)
+        gS = np.zeros(self.ncells)
+        _load().or_adjoint_step(self._h, _dp(Qn), dt, _dp(lam), _dp(gK), _dp(gS))
+        return gK, gS
+
+    def adjoint(self, Q0, nsteps, xyz, observed):
+        """J and (dJ/dp0 [cells][NS], dJ/dc [cells]) by the discrete adjoint."""
+        Q0 = np.ascontiguousarray(Q0, dtype=np.float64)
+        xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+        obs = np.ascontiguousarray(observed, dtype=np.float64)
+        gq = np.zeros((self.ncells, self.NS))
+        gc = np.zeros(self.ncells)
+        J = _load().or_adjoint(self._h, _dp(Q0), int(nsteps), len(xyz), _dp(xyz), _dp(obs),
+                               _dp(gq), _dp(gc))
+        return J, gq, gc
 
     def rusanov(self, qm, qp, Fm, Fp, dir, cellL=0, cellR=0):
         qm, qp, Fm, Fp = (np.ascontiguousarray(a, dtype=np.float64) for a in (qm, qp, Fm, Fp))

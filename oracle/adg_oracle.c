@@ -825,3 +825,300 @@ void or_destroy(or_mesh* M) { free(M); }
 void or_set_ck(or_mesh* M, int use_ck) { M->use_ck = use_ck; }
 
 void or_set_picard_iters(or_mesh* M, int iters) { M->picard_iters = iters; }
+
+/* ------------------------------------------------------------------------ */
+/* Receivers and misfit (acoustics).  A receiver samples the pressure of the */
+/* DG polynomial (eq. piecewise_solution) of the cell that contains it.      */
+/* ------------------------------------------------------------------------ */
+
+void or_receiver_weights(const or_mesh* M, const double* x, int* cell, double* wts) {
+  int cc[3] = {0, 0, 0};
+  double xi[3] = {0, 0, 0};
+  for (int a = 0; a < M->dim; ++a) {
+    double s = (x[a] - M->lo[a]) / M->h[a];
+    double f = floor(s);
+    int ci = (int)f;
+    xi[a] = s - f;
+    ci %= M->m[a];
+    if (ci < 0) ci += M->m[a];
+    cc[a] = ci;
+  }
+  *cell = cc[0] + M->m[0] * (cc[1] + M->m[1] * cc[2]);
+  const int NS = ipow(M->n, M->dim);
+  for (int i = 0; i < NS; ++i) {
+    double w = 1.0;
+    int r = i;
+    for (int a = 0; a < M->dim; ++a) {
+      w *= or_lagrange(M->n, M->xi, r % M->n, xi[a]);
+      r /= M->n;
+    }
+    wts[i] = w;
+  }
+}
+
+void or_receivers_eval(const or_mesh* M, const double* Q, int nrecv, const double* xyz, double* out) {
+  const int V = M->nvar, NS = ipow(M->n, M->dim);
+  double* w = (double*)malloc(sizeof(double) * NS);
+  for (int r = 0; r < nrecv; ++r) {
+    int c;
+    or_receiver_weights(M, xyz + (size_t)r * M->dim, &c, w);
+    double p = 0.0;
+    for (int i = 0; i < NS; ++i) p += w[i] * Q[((size_t)c * V + 0) * NS + i];
+    out[r] = p;
+  }
+  free(w);
+}
+
+/* Forward run from Q (overwritten with Q^nsteps): J = 1/2 sum_{n=1..nsteps} sum_r (p_h(x_r, t^n)
+ * - d_r^n)^2 with observed[n-1][r]; the sampled pressures go to record[n-1][r] if not NULL. */
+double or_misfit(const or_mesh* M, double* Q, int nsteps, int nrecv, const double* xyz,
+                 const double* observed, double* record) {
+  double J = 0.0;
+  double* p = (double*)malloc(sizeof(double) * (nrecv > 0 ? nrecv : 1));
+  for (int s = 0; s < nsteps; ++s) {
+    or_step(M, Q, or_dt(M, Q));
+    or_receivers_eval(M, Q, nrecv, xyz, p);
+    for (int r = 0; r < nrecv; ++r) {
+      double e = p[r] - (observed ? observed[(size_t)s * nrecv + r] : 0.0);
+      J += 0.5 * e * e;
+      if (record) record[(size_t)s * nrecv + r] = p[r];
+    }
+  }
+  free(p);
+  return J;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Discrete adjoint of one step for linear acoustics with per-cell c.  dt is */
+/* that of the forward step, held fixed.  The step is linear in Q; each part */
+/* of or_step is transposed in reverse order.  On entry lam holds dJ/dQ^{n+1};*/
+/* on exit dJ/dQ^n (without the misfit source of step n).  gK[c] accumulates */
+/* dJ/dK_c (K = rho c^2, through the fluxes), gS[c] dJ/dc_c through the      */
+/* Rusanov face speed s = max(c_minus, c_plus).                              */
+/* ------------------------------------------------------------------------ */
+
+void or_adjoint_step(const or_mesh* M, const double* Qn, double dt, double* lam, double* gK,
+                     double* gS) {
+  const int n = M->n, V = M->nvar, d = M->dim, NS = ipow(n, d), NF = ipow(n, d - 1), C = ncells(M);
+  const double rho = M->pp[0];
+  /* forward traces of Q^n (for the face-speed term) */
+  size_t tsz = (size_t)C * d * 2 * V * NF;
+  double* TQ = (double*)malloc(sizeof(double) * tsz);
+  double* TF = (double*)malloc(sizeof(double) * tsz);
+  {
+    double* Qv = (double*)malloc(sizeof(double) * (size_t)V * NS);
+    for (int c = 0; c < C; ++c)
+      predict_cell(M, c, Qn + (size_t)c * V * NS, dt, Qv, TQ + (size_t)c * d * 2 * V * NF,
+                   TF + (size_t)c * d * 2 * V * NF);
+    free(Qv);
+  }
+  /* 1. adjoint of the surface update: face-flux adjoints from each side's own lam.
+   * lamG(c, dir, side)[v][j]: side 1 is c's right face, side 0 its left face. */
+  size_t gsz = (size_t)C * d * 2 * V * NF;
+  double* lamG = (double*)calloc(gsz, sizeof(double));
+  for (int c = 0; c < C; ++c)
+    for (int dir = 0; dir < d; ++dir)
+      for (int v = 0; v < V; ++v)
+        for (int i = 0; i < NS; ++i) {
+          int a = node_dir_index(M, i, dir), j = face_index(M, i, dir);
+          double l = lam[((size_t)c * V + v) * NS + i];
+          /* Q_i -= dt (psi1[a] G+ - psi0[a] G-) / (h w_a) */
+          lamG[(((size_t)c * d + dir) * 2 + 1) * V * NF + v * NF + j] += -dt * M->psi1[a] / (M->h[dir] * M->w[a]) * l;
+          lamG[(((size_t)c * d + dir) * 2 + 0) * V * NF + v * NF + j] += dt * M->psi0[a] / (M->h[dir] * M->w[a]) * l;
+        }
+  double* out = (double*)malloc(sizeof(double) * (size_t)C * V * NS);
+  for (int c = 0; c < C; ++c) {
+    const double* Qc = Qn + (size_t)c * V * NS;
+    const double* lc = lam + (size_t)c * V * NS;
+    /* forward predictor of this cell, keeping every iterate (linear flux, K = rho c^2) */
+    const int I = M->picard_iters;
+    double* it = (double*)malloc(sizeof(double) * (size_t)(I + 1) * n * V * NS);
+    for (int k = 0; k < n; ++k)
+      for (int v = 0; v < V; ++v)
+        for (int i = 0; i < NS; ++i) it[((size_t)k * V + v) * NS + i] = Qc[v * NS + i];
+    double* R = (double*)malloc(sizeof(double) * (size_t)n * V * NS);
+    for (int r = 1; r <= I; ++r) {
+      const double* qp = it + (size_t)(r - 1) * n * V * NS;
+      double* qr = it + (size_t)r * n * V * NS;
+      space_derivative_of_flux(M, c, qp, n, R);
+      for (int v = 0; v < V; ++v)
+        for (int i = 0; i < NS; ++i) {
+          double rhs[OR_MAXN];
+          for (int l = 0; l < n; ++l) rhs[l] = M->psi0[l] * Qc[v * NS + i] - dt * M->w[l] * R[(l * V + v) * NS + i];
+          for (int k = 0; k < n; ++k) {
+            double s = 0.0;
+            for (int l = 0; l < n; ++l) s += M->K1inv[k][l] * rhs[l];
+            qr[(k * V + v) * NS + i] = s;
+          }
+        }
+    }
+    const double* qI = it + (size_t)I * n * V * NS;
+    double Qbar[OR_MAXV * 512];
+    for (int j = 0; j < V * NS; ++j) Qbar[j] = 0.0;
+    for (int k = 0; k < n; ++k)
+      for (int j = 0; j < V * NS; ++j) Qbar[j] += M->w[k] * qI[(size_t)k * V * NS + j];
+    const double K = M->cell_c ? rho * M->cell_c[c] * M->cell_c[c] : M->pp[1];
+
+    /* 2./3. Rusanov and trace adjoints -> lamQbar, lamFbar[dir] */
+    double* lamQbar = (double*)calloc((size_t)V * NS, sizeof(double));
+    double* lamFbar = (double*)calloc((size_t)d * V * NS, sizeof(double));
+    for (int dir = 0; dir < d; ++dir) {
+      int cl = neighbour(M, c, dir, 0), cr = neighbour(M, c, dir, 1);
+      double sL = fmax(or_speed(M, cl, NULL, dir), or_speed(M, c, NULL, dir));
+      double sR = fmax(or_speed(M, c, NULL, dir), or_speed(M, cr, NULL, dir));
+      for (int v = 0; v < V; ++v)
+        for (int j = 0; j < NF; ++j) {
+          /* right face: c is the minus side; left face: c is the plus side */
+          double gR = lamG[(((size_t)c * d + dir) * 2 + 1) * V * NF + v * NF + j] +
+                      lamG[(((size_t)cr * d + dir) * 2 + 0) * V * NF + v * NF + j];
+          double gL = lamG[(((size_t)cl * d + dir) * 2 + 1) * V * NF + v * NF + j] +
+                      lamG[(((size_t)c * d + dir) * 2 + 0) * V * NF + v * NF + j];
+          double lTF1 = 0.5 * gR, lTQ1 = 0.5 * sR * gR;   /* G = (Fm+Fp)/2 + s/2 (qm - qp) */
+          double lTF0 = 0.5 * gL, lTQ0 = -0.5 * sL * gL;
+          /* s = max(c_minus, c_plus): dG/ds = (qm - qp)/2 goes to the side holding the max
+           * (half to each side on a tie); counted once per face, at its right-hand cell */
+          {
+            double qm = TQ[(((size_t)c * d + dir) * 2 + 1) * V * NF + v * NF + j];
+            double qp = TQ[(((size_t)cr * d + dir) * 2 + 0) * V * NF + v * NF + j];
+            double g = gR * 0.5 * (qm - qp);
+            double cm = or_speed(M, c, NULL, dir), cp = or_speed(M, cr, NULL, dir);
+            if (cm > cp) gS[c] += g;
+            else if (cp > cm) gS[cr] += g;
+            else {
+              gS[c] += 0.5 * g;
+              gS[cr] += 0.5 * g;
+            }
+          }
+          for (int a = 0; a < n; ++a) {
+            int node = 0;
+            /* node with face index j and coordinate a along dir */
+            for (int i = 0; i < NS; ++i)
+              if (face_index(M, i, dir) == j && node_dir_index(M, i, dir) == a) { node = i; break; }
+            lamQbar[v * NS + node] += M->psi1[a] * lTQ1 + M->psi0[a] * lTQ0;
+            lamFbar[(dir * V + v) * NS + node] += M->psi1[a] * lTF1 + M->psi0[a] * lTF0;
+          }
+        }
+    }
+    /* 4. volume adjoint: Q_i += dt sum_dir (1/h)(1/w_{i_dir}) sum_a w_a D[a][i_dir] Fbar(i[dir<-a]) */
+    for (int dir = 0; dir < d; ++dir)
+      for (int v = 0; v < V; ++v)
+        for (int i = 0; i < NS; ++i) {
+          int id = node_dir_index(M, i, dir);
+          for (int a = 0; a < n; ++a)
+            lamFbar[(dir * V + v) * NS + node_with(M, i, dir, a)] +=
+                dt * M->w[a] * M->D[a][id] / (M->h[dir] * M->w[id]) * lc[v * NS + i];
+        }
+    /* 5. Fbar_dir = A_dir Qbar: acoustic F_dir = (K v_dir, p / rho e_dir) */
+    for (int dir = 0; dir < d; ++dir)
+      for (int i = 0; i < NS; ++i) {
+        double lp = lamFbar[(dir * V + 0) * NS + i], lv = lamFbar[(dir * V + 1 + dir) * NS + i];
+        lamQbar[(1 + dir) * NS + i] += K * lp;
+        lamQbar[0 * NS + i] += lv / rho;
+        gK[c] += lp * Qbar[(1 + dir) * NS + i];
+      }
+    /* 6. time average: Qbar = sum_k w_k q_k */
+    double* mu = (double*)malloc(sizeof(double) * (size_t)n * V * NS);
+    for (int k = 0; k < n; ++k)
+      for (int j = 0; j < V * NS; ++j) mu[(size_t)k * V * NS + j] = M->w[k] * lamQbar[j];
+    /* 7. Picard sweeps in reverse: q^r = K1inv (psi0 Q - dt w o R(q^{r-1})) */
+    double* lamQ = (double*)calloc((size_t)V * NS, sizeof(double));
+    double* nu = (double*)malloc(sizeof(double) * (size_t)n * V * NS);
+    for (int r = I; r >= 1; --r) {
+      const double* qp = it + (size_t)(r - 1) * n * V * NS;
+      for (int v = 0; v < V; ++v)
+        for (int i = 0; i < NS; ++i)
+          for (int l = 0; l < n; ++l) {
+            double s = 0.0;
+            for (int k = 0; k < n; ++k) s += M->K1inv[k][l] * mu[((size_t)k * V + v) * NS + i];
+            lamQ[v * NS + i] += M->psi0[l] * s;
+            nu[((size_t)l * V + v) * NS + i] = -dt * M->w[l] * s; /* adjoint of R_l */
+          }
+      /* R(q)_{k,i,v} = sum_dir (1/h) sum_a D[i_dir][a] F_dir,v(q_{k, i[dir<-a]}):
+       * adjoint to q and, through K in F_dir,p = K v_dir, to K */
+      for (int j = 0; j < n * V * NS; ++j) mu[j] = 0.0;
+      for (int k = 0; k < n; ++k)
+        for (int dir = 0; dir < d; ++dir)
+          for (int i = 0; i < NS; ++i) {
+            int id = node_dir_index(M, i, dir);
+            for (int a = 0; a < n; ++a) {
+              int m = node_with(M, i, dir, a);
+              double coef = M->D[id][a] / M->h[dir];
+              double np = nu[((size_t)k * V + 0) * NS + i], nv = nu[((size_t)k * V + 1 + dir) * NS + i];
+              /* F_dir,p(q_m) = K v_dir(q_m), F_dir,v_dir(q_m) = p(q_m) / rho */
+              mu[((size_t)k * V + 1 + dir) * NS + m] += coef * K * np;
+              mu[((size_t)k * V + 0) * NS + m] += coef * nv / rho;
+              gK[c] += coef * np * qp[((size_t)k * V + 1 + dir) * NS + m];
+            }
+          }
+    }
+    /* q^0 = Q at every time node */
+    for (int k = 0; k < n; ++k)
+      for (int j = 0; j < V * NS; ++j) lamQ[j] += mu[(size_t)k * V * NS + j];
+    /* 8. identity part of Q^{n+1} = Q^n + vol - surf */
+    for (int j = 0; j < V * NS; ++j) out[(size_t)c * V * NS + j] = lc[j] + lamQ[j];
+    free(it);
+    free(R);
+    free(lamQbar);
+    free(lamFbar);
+    free(mu);
+    free(lamQ);
+    free(nu);
+  }
+  memcpy(lam, out, sizeof(double) * (size_t)C * V * NS);
+  free(out);
+  free(lamG);
+  free(TQ);
+  free(TF);
+}
+
+/* J and its gradients for acoustics with per-cell c: gq0[c][NS] = dJ/dp(Q^0) at every node,
+ * gc[c] = dJ/dc_c.  Forward states are all kept (small meshes only). */
+double or_adjoint(const or_mesh* M, const double* Q0, int nsteps, int nrecv, const double* xyz,
+                  const double* observed, double* gq0, double* gc) {
+  const int V = M->nvar, NS = ipow(M->n, M->dim), C = ncells(M);
+  const size_t sz = (size_t)C * V * NS;
+  double* Qs = (double*)malloc(sizeof(double) * sz * (nsteps + 1));
+  double* dts = (double*)malloc(sizeof(double) * (nsteps > 0 ? nsteps : 1));
+  double* res = (double*)malloc(sizeof(double) * (size_t)(nsteps > 0 ? nsteps : 1) * (nrecv > 0 ? nrecv : 1));
+  double* p = (double*)malloc(sizeof(double) * (nrecv > 0 ? nrecv : 1));
+  memcpy(Qs, Q0, sizeof(double) * sz);
+  double J = 0.0;
+  for (int s = 0; s < nsteps; ++s) {
+    memcpy(Qs + (size_t)(s + 1) * sz, Qs + (size_t)s * sz, sizeof(double) * sz);
+    dts[s] = or_dt(M, Qs + (size_t)s * sz);
+    or_step(M, Qs + (size_t)(s + 1) * sz, dts[s]);
+    or_receivers_eval(M, Qs + (size_t)(s + 1) * sz, nrecv, xyz, p);
+    for (int r = 0; r < nrecv; ++r) {
+      double e = p[r] - observed[(size_t)s * nrecv + r];
+      res[(size_t)s * nrecv + r] = e;
+      J += 0.5 * e * e;
+    }
+  }
+  double* lam = (double*)calloc(sz, sizeof(double));
+  double* gK = (double*)calloc((size_t)C, sizeof(double));
+  double* gS = (double*)calloc((size_t)C, sizeof(double));
+  double* w = (double*)malloc(sizeof(double) * NS);
+  for (int s = nsteps; s >= 1; --s) {
+    /* misfit source of step s: dJ/dQ^s */
+    for (int r = 0; r < nrecv; ++r) {
+      int c;
+      or_receiver_weights(M, xyz + (size_t)r * M->dim, &c, w);
+      for (int i = 0; i < NS; ++i) lam[((size_t)c * V + 0) * NS + i] += res[(size_t)(s - 1) * nrecv + r] * w[i];
+    }
+    or_adjoint_step(M, Qs + (size_t)(s - 1) * sz, dts[s - 1], lam, gK, gS);
+  }
+  for (int c = 0; c < C; ++c) {
+    for (int i = 0; i < NS; ++i) gq0[(size_t)c * NS + i] = lam[((size_t)c * V + 0) * NS + i];
+    double cc = M->cell_c ? M->cell_c[c] : sqrt(M->pp[1] / M->pp[0]);
+    gc[c] = gK[c] * 2.0 * M->pp[0] * cc + gS[c];
+  }
+  free(Qs);
+  free(dts);
+  free(res);
+  free(p);
+  free(lam);
+  free(gK);
+  free(gS);
+  free(w);
+  return J;
+}

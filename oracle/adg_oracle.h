@@ -87,6 +87,16 @@ int or_run(const or_mesh* M, double* Q, int nsteps, double* t, double* dt_last);
 void or_step_cells(const or_mesh* M, const double* Q, double dt, int nsample, const int* cells,
                    double* out);
 
+/* receivers, misfit and the discrete adjoint (linear acoustics, per-cell c) */
+void or_receiver_weights(const or_mesh* M, const double* x, int* cell, double* wts);
+void or_receivers_eval(const or_mesh* M, const double* Q, int nrecv, const double* xyz, double* out);
+double or_misfit(const or_mesh* M, double* Q, int nsteps, int nrecv, const double* xyz,
+                 const double* observed, double* record);
+void or_adjoint_step(const or_mesh* M, const double* Qn, double dt, double* lam, double* gK,
+                     double* gS);
+double or_adjoint(const or_mesh* M, const double* Q0, int nsteps, int nrecv, const double* xyz,
+                  const double* observed, double* gq0, double* gc);
+
 /* Rusanov flux on one face node set, exposed for unit tests */
 void or_rusanov(const or_mesh* M, int cellL, int cellR, int dir, int nface, const double* qm,
                 const double* qp, const double* Fm, const double* Fp, double* G);

@@ -5,8 +5,8 @@
 //
 // Data flow per time slice k of a sweep (one CTA per cell, one thread per spatial node):
 //  1. each node computes F_dir(q_k) (FP32), scales it by the cell's power of two and writes it as
-//     a 16-bit value into the A operand of direction dir: row = (v, pair of pencils along dir),
-//     column = slot * 8 + position along the pencil (K-major, 8x8 core matrices, no swizzle);
+//     a 16-bit value into the A operand of direction dir: row = (v, pencil p mod NPP), column =
+//     (p / NPP) * 8 + position along the pencil (K-major, 8x8 core matrices, no swizzle);
 //  2. one thread issues, per direction and 128-row tile, tcgen05.mma with B = diag(D, D)
 //     (K = N = 16: two pencils per row); for the compensated sweeps x = x_hi + x_lo and
 //     D = D_hi + D_lo and the products hi*hi + hi*lo + lo*hi accumulate in the same tile;
@@ -123,7 +123,9 @@ template <class C> struct TcCfg {
   static constexpr size_t A_ALL = 2 * C::D * A_DIR;
   static constexpr size_t B_OFF = A_ALL;                // B hi, B lo: 512 bytes each
   static constexpr size_t R_OFF = B_OFF + 1024;         // per-direction derivatives, FP32
-  static constexpr size_t SWEEP = R_OFF + sizeof(float) * C::D * C::V * C::NS;
+  static constexpr int RS = Pencil<C>::S;                 // pencil stride of the derivative buffer
+  static constexpr int R_PER_V = 2 * NPP * RS;            // one direction, one variable
+  static constexpr size_t SWEEP = R_OFF + sizeof(float) * C::D * C::V * R_PER_V;
   static constexpr size_t FIN = sizeof(float) * (C::D * C::V * Pencil<C>::PER_DIR + C::V * C::NS);
   static constexpr size_t BIG = ((SWEEP > FIN ? SWEEP : FIN) + 127) / 128 * 128;
   static constexpr size_t TABLES = sizeof(float) * (2 * C::n * C::n + 3 * C::n);
@@ -209,12 +211,15 @@ __global__ void __launch_bounds__(TcCfg<C>::THREADS) k_predictor_tc(const __grid
     pen[1] = idx[0] + n * idx[2];
     pen[2] = idx[0] + n * idx[1];
   }
-  // this node's A-tile row (within a variable's block of rows) and column per direction
-  int arow[3], acol[3];
+  // pencil p of a direction sits in A row p % NPP, slot p / NPP (consecutive pencils in
+  // consecutive 16-byte rows of a core matrix: conflict-free stores); its derivatives come back
+  // to position (2 (p % NPP) + p / NPP) * RS of the derivative buffer
+  int arow[3], acol[3], rpos[3];
 #pragma unroll
   for (int dir = 0; dir < D; ++dir) {
-    arow[dir] = pen[dir] >> 1;
-    acol[dir] = (pen[dir] & 1) * 8 + idx[dir];
+    arow[dir] = pen[dir] % NPP;
+    acol[dir] = (pen[dir] / NPP) * 8 + idx[dir];
+    rpos[dir] = (2 * arow[dir] + pen[dir] / NPP) * G::RS + idx[dir];
   }
   const PP<T> pp = make_pp<T>(a.pp, cl);
   T Qh[V];
@@ -259,7 +264,7 @@ __global__ void __launch_bounds__(TcCfg<C>::THREADS) k_predictor_tc(const __grid
   const uint32_t idesc = tc::idesc_m128_n16<TIN>();
   const uint32_t a_base = tc::smem_u32(smem_raw);
   const uint32_t b_hi = a_base + (uint32_t)G::B_OFF, b_lo = b_hi + 512u;
-  float* sR = reinterpret_cast<float*>(smem_raw + G::R_OFF);  // [dir][v][node]
+  float* sR = reinterpret_cast<float*>(smem_raw + G::R_OFF);  // [dir][v][pencil layout]
   const float invh[3] = {(float)a.invh[0], (float)a.invh[1], (float)a.invh[2]};
   uint32_t phase = 0;
   bool stop = false;
@@ -330,17 +335,16 @@ __global__ void __launch_bounds__(TcCfg<C>::THREADS) k_predictor_tc(const __grid
           tc::ld16(tmem + ((uint32_t)(qtr * 32) << 16) + (uint32_t)((dir * TILES + t) * 16), o);
           const int row = t * 128 + qtr * 32 + lane;
           if (row < G::ROWS) {
+            // the two pencils of this row, contiguous in the pencil layout: 8-byte stores
             const int v = row / NPP, pr = row % NPP;
             const float f = inv_sc * invh[dir];
+            float* dst = sR + (dir * V + v) * G::R_PER_V + 2 * pr * G::RS;
 #pragma unroll
-            for (int s2 = 0; s2 < 2; ++s2) {
-              const int p = 2 * pr + s2;
-              if (p < G::NP) {
+            for (int s2 = 0; s2 < 2; ++s2)
 #pragma unroll
-                for (int m = 0; m < n; ++m)
-                  sR[(dir * V + v) * NS + node_of_face<D, n>(dir, p, m)] = o[s2 * 8 + m] * f;
-              }
-            }
+              for (int m = 0; m < G::RS; m += 2)
+                *reinterpret_cast<float2*>(dst + s2 * G::RS + m) =
+                    make_float2(o[s2 * 8 + m] * f, o[s2 * 8 + m + 1] * f);
           }
         }
       }
@@ -356,7 +360,7 @@ __global__ void __launch_bounds__(TcCfg<C>::THREADS) k_predictor_tc(const __grid
           T rv = T(0);
 #pragma unroll
           for (int dir = 0; dir < D; ++dir)
-            if (Ph::nz(dir, v)) rv += sR[(dir * V + v) * NS + i];
+            if (Ph::nz(dir, v)) rv += sR[(dir * V + v) * G::R_PER_V + rpos[dir]];
 #pragma unroll
           for (int kk = 0; kk < n; ++kk) qn[kk][v] -= sdtP[kk * n + k] * rv;
         }
