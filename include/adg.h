@@ -175,6 +175,36 @@ ADG_API int adg_l2_diff(adg_ctx* c, const double* d_Qref, double* l2_per_var, do
 /* Text for the last failure on this context (never NULL). */
 ADG_API const char* adg_last_error(const adg_ctx* c);
 
+/* ---- receivers, misfit and the adjoint (not in the paper) -------------------------------------
+ * Linear acoustics with a per-cell wave speed c (K = rho c^2).  Receivers sample the pressure of
+ * the cell's DG polynomial (eq. piecewise_solution) at points x_r after every step; the misfit
+ * is J = 1/2 sum_{n=1..nsteps} sum_r (p_h(x_r, t^n) - d_r^n)^2 with observed d[n-1][r].
+ *
+ * adg_set_material: d_c_per_cell is a caller-owned device array of ncells wave speeds, kept by
+ * the context (NULL: uniform c = sqrt(K/rho)); recomputes dt of the current state. */
+ADG_API int adg_set_material(adg_ctx* c, const double* d_c_per_cell);
+
+/* Device workspace for adg_misfit / adg_adjoint (256-byte aligned, caller-owned): nsnap
+ * checkpoints of the state plus the adjoint state and receiver buffers. */
+ADG_API int adg_adjoint_workspace_bytes(const adg_ctx* c, int nsteps, int nsnap, int nrecv, size_t* bytes);
+
+/* Forward nsteps from the current state (advanced in place), sampling the receivers
+ * (recv_xyz: host [nrecv][dim]); J_out: the misfit against observed (host [nsteps][nrecv], or
+ * NULL for zero data); record (host, may be NULL): the samples [nsteps][nrecv]. */
+ADG_API int adg_misfit(adg_ctx* c, int nsteps, const double* recv_xyz, int nrecv, const double* observed,
+                       double* J_out, double* record, void* d_workspace, size_t ws_bytes);
+
+/* J and its gradient by the hand-written discrete adjoint of the whole step: the transposes of
+ * the surface update, Rusanov flux, face extrapolation, volume integral, time average and Picard
+ * sweeps, with dt of the forward run held fixed (it depends on max c only).  Outputs (device):
+ * d_grad_p0[cell][(N+1)^d] = dJ/dp at every node of Q^0, d_grad_c[cell] = dJ/dc (through the
+ * fluxes and the Rusanov face speed max(c-, c+), half to each side on a tie).  Forward states are
+ * recomputed from nsnap checkpoints with the optimal binomial (revolve) schedule.  Needs
+ * RIEMANN = CORRECTOR = FP64 and PICARD = PREDICTOR in {FP64, FP32}; the state is left at Q^0. */
+ADG_API int adg_adjoint(adg_ctx* c, int nsteps, int nsnap, const double* recv_xyz, int nrecv,
+                        const double* observed, double* J_out, double* d_grad_p0, double* d_grad_c,
+                        void* d_workspace, size_t ws_bytes);
+
 /* Number of variables of a PDE in dim dimensions, or -1. */
 ADG_API int adg_nvar(int pde, int dim);
 

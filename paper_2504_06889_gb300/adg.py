@@ -55,6 +55,10 @@ _SIGS = {
     "adg_l2_diff": [_P, _P, _dp, _dp],
     "adg_last_error": [_P],
     "adg_nvar": [C.c_int, C.c_int],
+    "adg_set_material": [_P, _P],
+    "adg_adjoint_workspace_bytes": [_P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_size_t)],
+    "adg_misfit": [_P, C.c_int, _dp, C.c_int, _dp, _dp, _dp, _P, C.c_size_t],
+    "adg_adjoint": [_P, C.c_int, C.c_int, _dp, C.c_int, _dp, _dp, _P, _P, _P, C.c_size_t],
     "adg_step_noalloc": [C.c_int, C.c_int, C.c_int, _ip, _dp, _dp, _dp, C.c_int, C.c_double, C.c_int,
                          _P, C.c_int, _dp, _dp, _P],
 }
@@ -198,6 +202,51 @@ class Solver:
         self._check(self.lib.adg_error_vs_exact(self.ctx, per.ctypes.data_as(_dp), C.byref(tot)))
         return per, tot.value
 
+    # -- acoustics: material, receivers, misfit and adjoint --------------------------------
+    def set_material(self, c):
+        """Per-cell wave speed (torch CUDA float64 tensor [cells], kept alive here); None: uniform."""
+        if c is None:
+            self._material = None
+            self._check(self.lib.adg_set_material(self.ctx, None))
+            return
+        c = c.detach().to(device="cuda", dtype=self._torch.float64).contiguous()
+        assert c.numel() == self.ncells
+        self._material = c
+        self._check(self.lib.adg_set_material(self.ctx, C.c_void_p(c.data_ptr())))
+
+    def _adj_ws(self, nsteps, nsnap, nrecv):
+        wb = C.c_size_t()
+        self._check(self.lib.adg_adjoint_workspace_bytes(self.ctx, nsteps, nsnap, nrecv, C.byref(wb)))
+        buf = self._torch.empty(wb.value + 256, dtype=self._torch.uint8, device="cuda")
+        return buf, buf.data_ptr() + (-buf.data_ptr()) % 256, wb.value
+
+    def misfit(self, nsteps, xyz, observed=None):
+        """Forward nsteps (state advanced); returns (J, samples[nsteps][nrecv])."""
+        xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+        nrecv = len(xyz)
+        rec = np.zeros((nsteps, nrecv))
+        obs = None if observed is None else np.ascontiguousarray(observed, dtype=np.float64)
+        buf, ptr, nb = self._adj_ws(nsteps, 0, nrecv)
+        J = C.c_double()
+        self._check(self.lib.adg_misfit(self.ctx, nsteps, xyz.ctypes.data_as(_dp), nrecv,
+                                        obs.ctypes.data_as(_dp) if obs is not None else None,
+                                        C.byref(J), rec.ctypes.data_as(_dp), C.c_void_p(ptr), nb))
+        return J.value, rec
+
+    def adjoint(self, nsteps, nsnap, xyz, observed):
+        """J, dJ/dp0 [cells][NS] and dJ/dc [cells] (torch CUDA tensors); the state stays at Q^0."""
+        torch = self._torch
+        xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+        obs = np.ascontiguousarray(observed, dtype=np.float64)
+        buf, ptr, nb = self._adj_ws(nsteps, nsnap, len(xyz))
+        gp = torch.empty((self.ncells, self.NS), dtype=torch.float64, device="cuda")
+        gc = torch.empty(self.ncells, dtype=torch.float64, device="cuda")
+        J = C.c_double()
+        self._check(self.lib.adg_adjoint(self.ctx, nsteps, nsnap, xyz.ctypes.data_as(_dp), len(xyz),
+                                         obs.ctypes.data_as(_dp), C.byref(J), C.c_void_p(gp.data_ptr()),
+                                         C.c_void_p(gc.data_ptr()), C.c_void_p(ptr), nb))
+        return J.value, gp, gc
+
     def l2_diff(self, Qref):
         Qref = Qref.contiguous()
         per = np.zeros(self.V)
@@ -205,3 +254,42 @@ class Solver:
         self._check(self.lib.adg_l2_diff(self.ctx, C.c_void_p(Qref.data_ptr()), per.ctypes.data_as(_dp),
                                          C.byref(tot)))
         return per, tot.value
+
+
+def _autograd_function():
+    import torch
+
+    class AcousticMisfit(torch.autograd.Function):
+        """J(p0, c) = 1/2 sum_n sum_r (p_h(x_r, t^n) - d_r^n)^2 of an acoustic Solver run.
+
+        forward: the misfit of nsteps steps from the state whose pressure is p0 [cells][NS]
+        (the other variables are taken from `rest`, [cells][V][NS]) with per-cell wave speed
+        c [cells]; backward: the hand-written discrete adjoint (adg_adjoint) with nsnap
+        checkpoints."""
+
+        @staticmethod
+        def forward(ctx, p0, c, solver, rest, xyz, observed, nsteps, nsnap):
+            Q0 = rest.detach().clone()
+            Q0[:, 0, :] = p0.detach()
+            solver.set_material(c)
+            solver.set_state(Q0, 0.0)
+            J, _ = solver.misfit(nsteps, xyz, observed)
+            ctx.solver, ctx.Q0, ctx.c = solver, Q0, c.detach()
+            ctx.args = (xyz, observed, nsteps, nsnap)
+            return torch.tensor(J, dtype=torch.float64, device=p0.device)
+
+        @staticmethod
+        def backward(ctx, gJ):
+            xyz, observed, nsteps, nsnap = ctx.args
+            s = ctx.solver
+            s.set_material(ctx.c)
+            s.set_state(ctx.Q0, 0.0)
+            _, gp, gc = s.adjoint(nsteps, nsnap, xyz, observed)
+            return gJ * gp, gJ * gc, None, None, None, None, None, None
+
+    return AcousticMisfit
+
+
+def acoustic_misfit(p0, c, solver, rest, xyz, observed, nsteps, nsnap=10):
+    """Differentiable receiver misfit (see AcousticMisfit)."""
+    return _autograd_function().apply(p0, c, solver, rest, xyz, observed, nsteps, nsnap)

@@ -6,7 +6,11 @@
 #include <string>
 #include <vector>
 
+#include <algorithm>
+#include <functional>
+
 #include "../../include/adg.h"
+#include "adg_adjoint.cuh"
 #include "adg_internal.h"
 
 namespace adg {
@@ -187,7 +191,7 @@ struct adg_ctx {
   double* d_sp = nullptr;  // scenario parameters
   int d_sp_cap = 0;
   double* d_l2 = nullptr;  // [kMaxV + 1]
-  double* d_cell_c = nullptr;
+  const double* d_cell_c = nullptr;  // caller-owned per-cell wave speed (acoustics)
   int scenario = -1;
   std::vector<double> sp;
   Tables tab{};
@@ -277,7 +281,6 @@ int adg_destroy(adg_ctx* c) {
   if (c->sc) cudaFree(c->sc);
   if (c->d_l2) cudaFree(c->d_l2);
   if (c->d_sp) cudaFree(c->d_sp);
-  if (c->d_cell_c) cudaFree(c->d_cell_c);
   delete c;
   return ADG_OK;
 }
@@ -684,6 +687,360 @@ int adg_l2_diff(adg_ctx* c, const double* d_Qref, double* per, double* tot) {
   if (!c) return ADG_EINVAL;
   if (!d_Qref) return fail(c, ADG_EINVAL, "null reference state");
   return run_l2(c, d_Qref, per, tot);
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------------------------------
+// Receivers, misfit and the adjoint (linear acoustics with a per-cell wave speed)
+// ------------------------------------------------------------------------------------------------
+namespace adg {
+
+// p_h at each receiver: sum_i w[r][i] Q[cell_r][0][i]
+__global__ void k_recv_eval(const double* Q, int V, int NS, int nrecv, const int* rcell, const double* rw,
+                            double* out) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrecv) return;
+  const double* q = Q + (size_t)rcell[r] * V * NS;
+  double s = 0.0;
+  for (int i = 0; i < NS; ++i) s += rw[(size_t)r * NS + i] * q[i];
+  out[r] = s;
+}
+
+// lam[cell_r][0][i] += res[r] w[r][i], receivers in order (one block: deterministic)
+__global__ void k_recv_source(double* lam, int V, int NS, int nrecv, const int* rcell, const double* rw,
+                              const double* res) {
+  for (int r = 0; r < nrecv; ++r) {
+    double* l = lam + (size_t)rcell[r] * V * NS;
+    for (int i = threadIdx.x; i < NS; i += blockDim.x) l[i] += res[r] * rw[(size_t)r * NS + i];
+    __syncthreads();
+  }
+}
+
+// dJ/dc = dJ/dK 2 rho c + (face-speed part)
+__global__ void k_grad_c(int ncells, const double* gK, const double* gS, const double* cc, double cu, double rho,
+                         double* out) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x) {
+    const double ci = cc ? cc[c] : cu;
+    out[c] = gK[c] * 2.0 * rho * ci + gS[c];
+  }
+}
+
+}  // namespace adg
+
+namespace {
+
+struct AdjLayout {
+  size_t snap, lam, scratch, padj, gK, gS, rw, rcell, samples, res, total, state_bytes;
+};
+
+AdjLayout adj_layout(const adg_ctx* c, int nsteps, int nsnap, int nrecv) {
+  AdjLayout L{};
+  const size_t sb = sizeof(double) * (size_t)c->ncells * c->V * c->NS;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o = align256(o + bytes);
+    return at;
+  };
+  L.state_bytes = sb;
+  L.snap = take(sb * (size_t)(nsnap > 0 ? nsnap : 1));
+  L.lam = take(sb);
+  L.scratch = take(sb);
+  L.padj = take(sizeof(double) * (size_t)c->ncells * c->dim * 2 * c->V * c->NF);
+  L.gK = take(sizeof(double) * (size_t)c->ncells);
+  L.gS = take(sizeof(double) * (size_t)c->ncells);
+  L.rw = take(sizeof(double) * (size_t)(nrecv > 0 ? nrecv : 1) * c->NS);
+  L.rcell = take(sizeof(int) * (size_t)(nrecv > 0 ? nrecv : 1));
+  L.samples = take(sizeof(double) * (size_t)(nsteps > 0 ? nsteps : 1) * (nrecv > 0 ? nrecv : 1));
+  L.res = take(sizeof(double) * (size_t)(nsteps > 0 ? nsteps : 1) * (nrecv > 0 ? nrecv : 1));
+  L.total = o;
+  return L;
+}
+
+// receiver cell and tensor-product Lagrange weights at its local coordinates (barycentric form)
+void receiver_weights(const adg_ctx* c, const double* x, int* cell, double* w) {
+  int cc[3] = {0, 0, 0};
+  double xi[3] = {0, 0, 0};
+  for (int d = 0; d < c->dim; ++d) {
+    const double s = (x[d] - c->lo[d]) / c->h[d];
+    const double f = std::floor(s);
+    int ci = (int)f;
+    xi[d] = s - f;
+    ci %= c->m[d];
+    if (ci < 0) ci += c->m[d];
+    cc[d] = ci;
+  }
+  *cell = cc[0] + c->m[0] * (cc[1] + c->m[1] * cc[2]);
+  const int n = c->n;
+  double L[3][kMaxN1];
+  for (int d = 0; d < c->dim; ++d) {
+    // psi_j(s) = prod_{m != j} (s - xi_m) / (xi_j - xi_m)
+    for (int j = 0; j < n; ++j) {
+      double v = 1.0;
+      for (int m = 0; m < n; ++m)
+        if (m != j) v *= (xi[d] - c->tab.xi[m]) / (c->tab.xi[j] - c->tab.xi[m]);
+      L[d][j] = v;
+    }
+  }
+  for (int i = 0; i < c->NS; ++i) {
+    double v = 1.0;
+    int r = i;
+    for (int d = 0; d < c->dim; ++d) {
+      v *= L[d][r % n];
+      r /= n;
+    }
+    w[i] = v;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int adg_set_material(adg_ctx* c, const double* d_c_per_cell) {
+  if (!c) return ADG_EINVAL;
+  if (!c->have_pde) return fail(c, ADG_ENOTINIT, "adg_set_pde first");
+  if (c->pde != ADG_ACOUSTIC) return fail(c, ADG_EUNSUPPORTED, "a per-cell wave speed is built for acoustics");
+  c->d_cell_c = d_c_per_cell;
+  c->pp.cell_c = d_c_per_cell;
+  if (c->have_state) {
+    DevScalars s;
+    ADG_CUDA(c, cudaMemcpyAsync(&s, c->sc, sizeof(s), cudaMemcpyDeviceToHost, c->stream));
+    ADG_CUDA(c, cudaStreamSynchronize(c->stream));
+    return reset_scalars_and_lambda(c, s.t);
+  }
+  return ADG_OK;
+}
+
+int adg_adjoint_workspace_bytes(const adg_ctx* c, int nsteps, int nsnap, int nrecv, size_t* bytes) {
+  if (!c || !bytes || nsteps < 0 || nsnap < 0 || nrecv < 0) return ADG_EINVAL;
+  if (!c->have_mesh || !c->have_pde) return ADG_ENOTINIT;
+  *bytes = adj_layout(c, nsteps, nsnap, nrecv).total;
+  return ADG_OK;
+}
+
+static int adj_setup(adg_ctx* c, int nsteps, int nsnap, const double* xyz, int nrecv, void* ws, size_t ws_bytes,
+                     AdjLayout* L) {
+  if (!c->have_state) return fail(c, ADG_ENOTINIT, "set a state first");
+  if (nsteps < 1 || nrecv < 0 || (nrecv > 0 && !xyz) || !ws) return fail(c, ADG_EINVAL, "bad arguments");
+  if ((uintptr_t)ws & 255) return fail(c, ADG_EINVAL, "workspace must be 256-byte aligned");
+  *L = adj_layout(c, nsteps, nsnap, nrecv);
+  if (ws_bytes < L->total) return fail(c, ADG_ENOMEM, "adjoint workspace too small");
+  std::vector<double> w((size_t)(nrecv > 0 ? nrecv : 1) * c->NS);
+  std::vector<int> rc((size_t)(nrecv > 0 ? nrecv : 1));
+  for (int r = 0; r < nrecv; ++r) receiver_weights(c, xyz + (size_t)r * c->dim, &rc[r], w.data() + (size_t)r * c->NS);
+  char* b = static_cast<char*>(ws);
+  ADG_CUDA(c, cudaMemcpyAsync(b + L->rw, w.data(), sizeof(double) * w.size(), cudaMemcpyHostToDevice, c->stream));
+  ADG_CUDA(c, cudaMemcpyAsync(b + L->rcell, rc.data(), sizeof(int) * rc.size(), cudaMemcpyHostToDevice, c->stream));
+  ADG_CUDA(c, cudaStreamSynchronize(c->stream));  // host vectors go out of scope
+  return ADG_OK;
+}
+
+static int forward_steps(adg_ctx* c, int nsteps, char* b, const AdjLayout& L, int nrecv, int sample_from) {
+  StepFn pred = nullptr, corr = nullptr;
+  int st = select_kernels(c, &pred, &corr);
+  if (st != ADG_OK) return st;
+  StepArgs a;
+  fill_step_args(c, &a);
+  for (int s = 0; s < nsteps; ++s) {
+    ADG_CUDA(c, pred(a, c->stream));
+    ADG_CUDA(c, corr(a, c->stream));
+    if (sample_from >= 0 && nrecv > 0) {
+      k_recv_eval<<<(nrecv + 127) / 128, 128, 0, c->stream>>>(
+          c->Q, c->V, c->NS, nrecv, reinterpret_cast<const int*>(b + L.rcell),
+          reinterpret_cast<const double*>(b + L.rw),
+          reinterpret_cast<double*>(b + L.samples) + (size_t)(sample_from + s) * nrecv);
+      ADG_CUDA(c, cudaGetLastError());
+    }
+  }
+  return ADG_OK;
+}
+
+int adg_misfit(adg_ctx* c, int nsteps, const double* xyz, int nrecv, const double* observed, double* J_out,
+               double* record, void* d_workspace, size_t ws_bytes) {
+  if (!c) return ADG_EINVAL;
+  AdjLayout L;
+  int st = adj_setup(c, nsteps, 0, xyz, nrecv, d_workspace, ws_bytes, &L);
+  if (st != ADG_OK) return st;
+  char* b = static_cast<char*>(d_workspace);
+  st = forward_steps(c, nsteps, b, L, nrecv, 0);
+  if (st != ADG_OK) return st;
+  std::vector<double> smp((size_t)nsteps * nrecv);
+  if (nrecv > 0)
+    ADG_CUDA(c, cudaMemcpyAsync(smp.data(), b + L.samples, sizeof(double) * smp.size(), cudaMemcpyDeviceToHost,
+                                c->stream));
+  ADG_CUDA(c, cudaStreamSynchronize(c->stream));
+  double J = 0.0;
+  for (size_t k = 0; k < smp.size(); ++k) {
+    const double e = smp[k] - (observed ? observed[k] : 0.0);
+    J += 0.5 * e * e;
+  }
+  if (record) std::copy(smp.begin(), smp.end(), record);
+  if (J_out) *J_out = J;
+  DevScalars sv;
+  ADG_CUDA(c, cudaMemcpyAsync(&sv, c->sc, sizeof(sv), cudaMemcpyDeviceToHost, c->stream));
+  ADG_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (sv.bad) return fail(c, ADG_ENONFINITE, "non-finite value in the state");
+  return ADG_OK;
+}
+
+int adg_adjoint(adg_ctx* c, int nsteps, int nsnap, const double* xyz, int nrecv, const double* observed,
+                double* J_out, double* d_grad_p0, double* d_grad_c, void* d_workspace, size_t ws_bytes) {
+  if (!c) return ADG_EINVAL;
+  if (c->pde != ADG_ACOUSTIC || !c->entry || !c->entry->adj_trace)
+    return fail(c, ADG_EUNSUPPORTED, "the adjoint is built for acoustics (2D N=3, 3D N=2, 4)");
+  if (nsnap < 1) return fail(c, ADG_EINVAL, "nsnap must be >= 1");
+  if (c->prec[ADG_K_CORRECTOR] != P64 || c->prec[ADG_K_RIEMANN] != P64)
+    return fail(c, ADG_EUNSUPPORTED, "the adjoint needs the FP64 Riemann/corrector");
+  if (c->prec[ADG_K_PICARD] != c->prec[ADG_K_PREDICTOR] || c->prec[ADG_K_PICARD] > P32)
+    return fail(c, ADG_EUNSUPPORTED, "the adjoint is built for the FP64 and FP32 predictors");
+  if (!observed || !d_grad_p0 || !d_grad_c) return fail(c, ADG_EINVAL, "null output/observation");
+  AdjLayout L;
+  int st = adj_setup(c, nsteps, nsnap, xyz, nrecv, d_workspace, ws_bytes, &L);
+  if (st != ADG_OK) return st;
+  char* b = static_cast<char*>(d_workspace);
+  cudaStream_t S = c->stream;
+  const size_t SB = L.state_bytes;
+  double* lam = reinterpret_cast<double*>(b + L.lam);
+  double* scratch = reinterpret_cast<double*>(b + L.scratch);
+  auto slot = [&](int k) { return reinterpret_cast<double*>(b + L.snap + SB * (size_t)k); };
+  DevScalars s0;
+  ADG_CUDA(c, cudaMemcpyAsync(&s0, c->sc, sizeof(s0), cudaMemcpyDeviceToHost, S));
+  ADG_CUDA(c, cudaStreamSynchronize(S));
+  double lam_max;
+  std::memcpy(&lam_max, &s0.lam_cur, sizeof(lam_max));
+  double hmin = c->h[0];
+  for (int d = 1; d < c->dim; ++d) hmin = std::min(hmin, c->h[d]);
+  const double dt = c->cfl * hmin / ((double)c->dim * (2.0 * c->N + 1.0) * lam_max);
+  const double t0 = s0.t;
+
+  // forward pass: Q^0 to slot 0, receiver samples of every step
+  ADG_CUDA(c, cudaMemcpyAsync(slot(0), c->Q, SB, cudaMemcpyDeviceToDevice, S));
+  st = forward_steps(c, nsteps, b, L, nrecv, 0);
+  if (st != ADG_OK) return st;
+  std::vector<double> smp((size_t)nsteps * nrecv), res((size_t)nsteps * nrecv);
+  if (nrecv > 0)
+    ADG_CUDA(c, cudaMemcpyAsync(smp.data(), b + L.samples, sizeof(double) * smp.size(), cudaMemcpyDeviceToHost, S));
+  ADG_CUDA(c, cudaStreamSynchronize(S));
+  double J = 0.0;
+  for (size_t k = 0; k < smp.size(); ++k) {
+    res[k] = smp[k] - observed[k];
+    J += 0.5 * res[k] * res[k];
+  }
+  if (nrecv > 0)
+    ADG_CUDA(c, cudaMemcpyAsync(b + L.res, res.data(), sizeof(double) * res.size(), cudaMemcpyHostToDevice, S));
+
+  // optimal binomial checkpointing: cost[l][k] forward steps to reverse l steps with k free slots
+  const int K = nsnap - 1;
+  std::vector<std::vector<long long>> cost(nsteps + 1, std::vector<long long>(K + 1, 0));
+  std::vector<std::vector<int>> split(nsteps + 1, std::vector<int>(K + 1, 0));
+  for (int l = 2; l <= nsteps; ++l) {
+    cost[l][0] = (long long)l * (l - 1) / 2;
+    for (int k = 1; k <= K; ++k) {
+      long long best = -1;
+      int bj = 1;
+      for (int j = 1; j < l; ++j) {
+        const long long cst = j + cost[l - j][k - 1] + cost[j][k];
+        if (best < 0 || cst < best) {
+          best = cst;
+          bj = j;
+        }
+      }
+      cost[l][k] = best;
+      split[l][k] = bj;
+    }
+  }
+
+  // adjoint machinery
+  const AdjFn adj_trace = reinterpret_cast<AdjFn>(c->entry->adj_trace);
+  const AdjFn adj_cell = reinterpret_cast<AdjFn>(c->entry->adj_cell[c->prec[ADG_K_PICARD] == P32 ? 1 : 0]);
+  StepFn pred = nullptr, corr = nullptr;
+  st = select_kernels(c, &pred, &corr);
+  if (st != ADG_OK) return st;
+  ADG_CUDA(c, cudaMemsetAsync(lam, 0, SB, S));
+  ADG_CUDA(c, cudaMemsetAsync(b + L.gK, 0, sizeof(double) * c->ncells, S));
+  ADG_CUDA(c, cudaMemsetAsync(b + L.gS, 0, sizeof(double) * c->ncells, S));
+  auto source = [&](int step) -> int {  // dJ/dQ^step, step >= 1
+    if (nrecv == 0) return ADG_OK;
+    k_recv_source<<<1, 128, 0, S>>>(lam, c->V, c->NS, nrecv, reinterpret_cast<const int*>(b + L.rcell),
+                                    reinterpret_cast<const double*>(b + L.rw),
+                                    reinterpret_cast<const double*>(b + L.res) + (size_t)(step - 1) * nrecv);
+    ADG_CUDA(c, cudaGetLastError());
+    return ADG_OK;
+  };
+  StepArgs fa;
+  fill_step_args(c, &fa);
+  auto advance = [&](int nst) -> int {  // nst forward steps on the state buffer
+    for (int s = 0; s < nst; ++s) {
+      ADG_CUDA(c, pred(fa, S));
+      ADG_CUDA(c, corr(fa, S));
+    }
+    return ADG_OK;
+  };
+  auto adjoint_step = [&](int step) -> int {  // state buffer holds Q^step; lam = dJ/dQ^{step+1}
+    ADG_CUDA(c, cudaMemcpyAsync(scratch, c->Q, SB, cudaMemcpyDeviceToDevice, S));
+    StepArgs ps = fa;
+    ps.Q = scratch;  // the predictor writes Q + vol into scratch and the FP64 traces of Q^step
+    ADG_CUDA(c, pred(ps, S));
+    AdjArgs aa;
+    std::memset(&aa, 0, sizeof(aa));
+    aa.s = fa;
+    aa.s.Q = c->Q;
+    aa.lam = lam;
+    aa.padj = reinterpret_cast<double*>(b + L.padj);
+    aa.gK = reinterpret_cast<double*>(b + L.gK);
+    aa.gS = reinterpret_cast<double*>(b + L.gS);
+    aa.dt = dt;
+    ADG_CUDA(c, adj_trace(aa, S));
+    ADG_CUDA(c, adj_cell(aa, S));
+    if (step >= 1) return source(step);
+    return ADG_OK;
+  };
+  // reverse(s, e, k, slot_s): Q^s in slot slot_s, lam = dJ/dQ^e; k free slots after slot_s
+  std::function<int(int, int, int, int)> reverse = [&](int s, int e, int k, int ss) -> int {
+    if (e - s == 1) {
+      ADG_CUDA(c, cudaMemcpyAsync(c->Q, slot(ss), SB, cudaMemcpyDeviceToDevice, S));
+      return adjoint_step(s);
+    }
+    if (k == 0) {
+      for (int t = e - 1; t >= s; --t) {
+        ADG_CUDA(c, cudaMemcpyAsync(c->Q, slot(ss), SB, cudaMemcpyDeviceToDevice, S));
+        int r = advance(t - s);
+        if (r != ADG_OK) return r;
+        r = adjoint_step(t);
+        if (r != ADG_OK) return r;
+      }
+      return ADG_OK;
+    }
+    const int m = s + split[e - s][k];
+    ADG_CUDA(c, cudaMemcpyAsync(c->Q, slot(ss), SB, cudaMemcpyDeviceToDevice, S));
+    int r = advance(m - s);
+    if (r != ADG_OK) return r;
+    ADG_CUDA(c, cudaMemcpyAsync(slot(ss + 1), c->Q, SB, cudaMemcpyDeviceToDevice, S));
+    r = reverse(m, e, k - 1, ss + 1);
+    if (r != ADG_OK) return r;
+    return reverse(s, m, k, ss);
+  };
+  st = source(nsteps);
+  if (st != ADG_OK) return st;
+  st = reverse(0, nsteps, K, 0);
+  if (st != ADG_OK) return st;
+
+  // gradients: dJ/dp(Q^0) and dJ/dc
+  ADG_CUDA(c, cudaMemcpy2DAsync(d_grad_p0, sizeof(double) * c->NS, lam, sizeof(double) * c->NS * c->V,
+                                sizeof(double) * c->NS, c->ncells, cudaMemcpyDeviceToDevice, S));
+  k_grad_c<<<(c->ncells + 255) / 256, 256, 0, S>>>(c->ncells, reinterpret_cast<const double*>(b + L.gK),
+                                                  reinterpret_cast<const double*>(b + L.gS), c->d_cell_c,
+                                                  c->pp.c, c->pp.rho, d_grad_c);
+  ADG_CUDA(c, cudaGetLastError());
+  // leave the state as it was: Q^0 at t0
+  ADG_CUDA(c, cudaMemcpyAsync(c->Q, slot(0), SB, cudaMemcpyDeviceToDevice, S));
+  st = reset_scalars_and_lambda(c, t0);
+  if (st != ADG_OK) return st;
+  ADG_CUDA(c, cudaStreamSynchronize(S));
+  if (J_out) *J_out = J;
+  return ADG_OK;
 }
 
 }  // extern "C"

@@ -109,6 +109,9 @@ struct Entry {
   StepFn corrector[3][3];
   // tensor-core Picard with FP32 final stage: [0 = bf16, 1 = fp16][trace prec]
   StepFn predictor_tc[2][3];
+  // discrete adjoint (linear acoustics): face projections, per-cell adjoint [0 = FP64, 1 = FP32]
+  void* adj_trace;
+  void* adj_cell[2];
   LamFn lambda;
   InitFn init;
   L2Fn l2;
