@@ -180,6 +180,7 @@ __device__ __forceinline__ void predictor_final(const StepArgs& a, const T (*q)[
 
   // ---- volume integral: Q_i += dt sum_dir (1/h_dir) sum_m Vm[i_dir][m] Fbar(i[dir<-m]) --------
   if (valid && owner) {
+    const TP ihp[3] = {(TP)a.invh[0], (TP)a.invh[1], (TP)a.invh[2]};
     double* Qw = a.Q + (size_t)cell * V * NS;
 #pragma unroll
     for (int v = 0; v < V; ++v) {
@@ -192,7 +193,7 @@ __device__ __forceinline__ void predictor_final(const StepArgs& a, const T (*q)[
         TP s = TP(0);
 #pragma unroll
         for (int m = 0; m < n; ++m) s += Vr[m] * Fp[m];
-        vol += s * (TP)a.invh[dir];
+        vol += s * ihp[dir];
       }
       Qw[v * NS + i] += dt * (double)vol;
     }
@@ -401,22 +402,29 @@ __global__ void __launch_bounds__(C::THREADS) k_corrector(const __grid_constant_
   const TS* trc = reinterpret_cast<const TS*>(a.traces);
   constexpr size_t cellsz = (size_t)D * 2 * 2 * V * NF;
 
-  // load both sides of the 2d faces: face f = 2 dir + side; minus = left cell's side-1 trace,
-  // plus = right cell's side-0 trace
-  for (int it = i; it < 2 * D * 2 * 2 * V * NF; it += NS) {
-    const int j = it % NF;
-    const int v = (it / NF) % V;
-    const int qf = (it / (NF * V)) % 2;
-    const int pm = (it / (NF * V * 2)) % 2;  // 0 minus, 1 plus
-    const int f = it / (NF * V * 4);
-    const int dir = f / 2, side = f % 2;
-    // right face (side 1): minus = own side 1, plus = right neighbour side 0
-    // left face  (side 0): minus = left neighbour side 1, plus = own side 0
-    const bool own = (side == 1) ? (pm == 0) : (pm == 1);
-    const int src = own ? cl : neighbour(a, cl, dir, side);
-    const int sside = pm == 0 ? 1 : 0;
-    const TS val = trc[(size_t)src * cellsz + (((dir * 2 + sside) * 2 + qf) * V + v) * NF + j];
-    sT[it] = tcast<TR>(todouble(val));
+  // neighbour across each face f = 2 dir + side (computed once per thread)
+  int nbr[2 * D];
+#pragma unroll
+  for (int f = 0; f < 2 * D; ++f) nbr[f] = neighbour(a, cl, f / 2, f % 2);
+
+  // load both sides of the 2d faces: minus = left cell's side-1 trace, plus = right cell's
+  // side-0 trace.  Each thread takes element e = v * NF + j of all 2d x 2 x 2 trace blocks.
+  for (int e = i; e < V * NF; e += NS) {
+#pragma unroll
+    for (int f = 0; f < 2 * D; ++f) {
+      const int dir = f / 2, side = f % 2;
+#pragma unroll
+      for (int pm = 0; pm < 2; ++pm) {
+        // right face (side 1): minus = own side 1, plus = neighbour side 0
+        // left face  (side 0): minus = neighbour side 1, plus = own side 0
+        const bool own = (side == 1) ? (pm == 0) : (pm == 1);
+        const int src = own ? cl : nbr[f];
+        const int sside = pm == 0 ? 1 : 0;
+        const TS* tp = trc + (size_t)src * cellsz + (size_t)((dir * 2 + sside) * 2) * V * NF + e;
+#pragma unroll
+        for (int qf = 0; qf < 2; ++qf) sT[((f * 2 + pm) * 2 + qf) * V * NF + e] = conv<TR>(tp[qf * V * NF]);
+      }
+    }
   }
   __syncthreads();
   const PP<TR> ppL = make_pp<TR>(a.pp, cl);
@@ -429,8 +437,7 @@ __global__ void __launch_bounds__(C::THREADS) k_corrector(const __grid_constant_
       qm[v] = sT[(((f * 2 + 0) * 2 + 0) * V + v) * NF + j];
       qp[v] = sT[(((f * 2 + 1) * 2 + 0) * V + v) * NF + j];
     }
-    const int nb = neighbour(a, cl, dir, side);
-    const PP<TR> ppN = make_pp<TR>(a.pp, nb);
+    const PP<TR> ppN = make_pp<TR>(a.pp, nbr[f]);
     const TR sm = side ? Ph::speed(ppL, qm, dir) : Ph::speed(ppN, qm, dir);
     const TR sp = side ? Ph::speed(ppN, qp, dir) : Ph::speed(ppL, qp, dir);
     sS[it] = tmax(sm, sp);
@@ -443,16 +450,20 @@ __global__ void __launch_bounds__(C::THREADS) k_corrector(const __grid_constant_
   }
   __syncthreads();
   // Rusanov: G = (Fm + Fp)/2 + s/2 (qm - qp), s = max over the face's nodes
-  for (int it = i; it < 2 * D * V * NF; it += NS) {
-    const int j = it % NF, v = (it / NF) % V, f = it / (NF * V);
-    const TR s = sSmax[f];
-    const TR qm = sT[(((f * 2 + 0) * 2 + 0) * V + v) * NF + j];
-    const TR qp = sT[(((f * 2 + 1) * 2 + 0) * V + v) * NF + j];
-    const TR Fm = sT[(((f * 2 + 0) * 2 + 1) * V + v) * NF + j];
-    const TR Fp = sT[(((f * 2 + 1) * 2 + 1) * V + v) * NF + j];
+  {
     const TR half = tcast<TR>(0.5);
-    const TR G = half * (Fm + Fp) + half * s * (qm - qp);
-    sG[it] = tcast<TC>(todouble(G));
+    for (int e = i; e < V * NF; e += NS) {
+#pragma unroll
+      for (int f = 0; f < 2 * D; ++f) {
+        const TR s = sSmax[f];
+        const TR qm = sT[((f * 2 + 0) * 2 + 0) * V * NF + e];
+        const TR qp = sT[((f * 2 + 1) * 2 + 0) * V * NF + e];
+        const TR Fm = sT[((f * 2 + 0) * 2 + 1) * V * NF + e];
+        const TR Fp = sT[((f * 2 + 1) * 2 + 1) * V * NF + e];
+        const TR G = half * (Fm + Fp) + half * s * (qm - qp);
+        sG[f * V * NF + e] = conv<TC>(G);
+      }
+    }
   }
   __syncthreads();
 

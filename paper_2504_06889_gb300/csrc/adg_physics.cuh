@@ -23,6 +23,26 @@ template <class T> __device__ __forceinline__ double todouble(T x) { return (dou
 template <> __device__ __forceinline__ double todouble<__nv_bfloat16>(__nv_bfloat16 x) {
   return (double)__bfloat162float(x);
 }
+// direct conversions between the storage and arithmetic types (no detour through FP64, whose
+// conversions run on the slow FP64 pipe of this part)
+template <class To, class From> __device__ __forceinline__ To conv(From x) { return (To)x; }
+template <> __device__ __forceinline__ __nv_bfloat16 conv<__nv_bfloat16, float>(float x) {
+  return __float2bfloat16(x);
+}
+template <> __device__ __forceinline__ float conv<float, __nv_bfloat16>(__nv_bfloat16 x) {
+  return __bfloat162float(x);
+}
+template <> __device__ __forceinline__ __nv_bfloat16 conv<__nv_bfloat16, double>(double x) {
+  return __double2bfloat16(x);
+}
+template <> __device__ __forceinline__ double conv<double, __nv_bfloat16>(__nv_bfloat16 x) {
+  return (double)__bfloat162float(x);
+}
+template <>
+__device__ __forceinline__ __nv_bfloat16 conv<__nv_bfloat16, __nv_bfloat16>(__nv_bfloat16 x) {
+  return x;
+}
+
 template <class T> __device__ __forceinline__ T tsqrt(T x) { return sqrt(x); }
 template <> __device__ __forceinline__ float tsqrt<float>(float x) { return sqrtf(x); }
 template <> __device__ __forceinline__ __nv_bfloat16 tsqrt<__nv_bfloat16>(__nv_bfloat16 x) {
