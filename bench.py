@@ -56,6 +56,27 @@ MIXES = {
     "fp16tc": {"picard": "fp16", "predictor": "fp32", "riemann": "fp32", "corrector": "fp32"},
 }
 MIX_FLAGS = {"bf16tc": 1 | 2, "fp16tc": 1 | 2}
+
+# default mixes per workload (the tensor-core predictor is built for the 3D meshes)
+DEFAULT_MIXES = {
+    "euler3d": "fp64,fp32pred,fp32,bf16tc,fp16tc",
+    "elastic3d": "fp64,fp32,fp16tc,bf16tc",
+    "acoustic3d": "fp64,fp32,fp16tc",
+    "acoustic2d": "fp64,fp32",
+    "swe2d": "fp64,fp32pred,fp32",
+}
+
+
+def sweep_mixes():
+    """Per-kernel sweep: predictor (Picard and final stage), Riemann, corrector each in
+    {FP64, FP32, bf16} (27 mixes); the bf16 predictor computes everything in bf16."""
+    out = {}
+    for p in ("fp64", "fp32", "bf16"):
+        for r in ("fp64", "fp32", "bf16"):
+            for c in ("fp64", "fp32", "bf16"):
+                out[f"pred-{p}_riem-{r}_corr-{c}"] = {"picard": p, "predictor": p, "riemann": r,
+                                                    "corrector": c}
+    return out
 DTYPE = {"fp64": "f64", "fp32pred": "f32+f64", "fp32": "f32+f64", "bf16tc": "bf16+f32+f64",
          "fp16tc": "f16+f32+f64"}
 
@@ -96,9 +117,10 @@ def load_peaks():
 
 
 def alu_peak_tflops(kind, sm_mhz):
-    """FP32: 152 SMs x 128 FP32 lanes x 2 flop per FMA x SM clock.  FP64: GB300's nominal
-    1.25 TFLOP/s (FP64 runs at a small fraction of the FP32 rate on this part)."""
-    if kind == "fp32":
+    """FP32 (and scalar bf16, which issues at the same rate): 152 SMs x 128 lanes x 2 flop per
+    FMA x SM clock.  FP64: GB300's nominal 1.25 TFLOP/s (FP64 runs at a small fraction of the
+    FP32 rate on this part)."""
+    if kind in ("fp32", "bf16"):
         return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
     return 1.25
 
@@ -174,12 +196,14 @@ def barrier(ws):
 
 
 def max_over_ranks(x, ws):
+    """The slowest rank's time (the timing contract); works with nccl and gloo."""
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -202,6 +226,34 @@ def cpu_oracle_sample(wl, sample_cells, steps=1):
             "kind": "oracle",
             "sample": f"{sw.name}: {steps} step(s) on {sample_cells}^{wl.dim} cells of the same "
                       f"workload ({sw.dofs} DOF), {el:.2f} s"}
+
+
+def time_adjoint(adg, wl, nsnap):
+    """Receiver misfit and its gradient w.r.t. p0 and c by the discrete adjoint (checkpointed)."""
+    import torch
+
+    s = adg.Solver(wl.dim, wl.N, wl.cells, wl.pde, wl.params, cfl=wl.cfl)
+    xyz = I.receivers(count=64, dim=wl.dim)
+    s.set_material(torch.from_numpy(I.material_blob(m=wl.cells[0], dim=wl.dim)).cuda())
+    s.set_initial(wl.scenario, wl.sp)
+    _, obs = s.misfit(wl.steps, xyz)
+    s.set_material(torch.ones(wl.ncells, dtype=torch.float64, device="cuda"))
+    s.set_initial(wl.scenario, wl.sp)
+    out = {}
+    for label in ("misfit", "adjoint"):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if label == "misfit":
+            J, _ = s.misfit(wl.steps, xyz, obs)
+            s.set_initial(wl.scenario, wl.sp)
+        else:
+            J, gq, gc = s.adjoint(wl.steps, nsnap, xyz, obs)
+        torch.cuda.synchronize()
+        out[label + "_s"] = time.perf_counter() - t0
+    out.update({"J": J, "steps": wl.steps, "nsnap": nsnap, "receivers": len(xyz),
+                "grad_p0_norm": float(gq.norm()), "grad_c_norm": float(gc.norm()),
+                "adjoint_over_forward": out["adjoint_s"] / out["misfit_s"]})
+    return out
 
 
 def run_reference(args, wl):
@@ -245,7 +297,10 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="euler3d", choices=sorted(I.WORKLOADS))
     ap.add_argument("--cells", type=int, default=0, help="override cells per direction")
-    ap.add_argument("--mixes", default="fp64,fp32pred,fp32,bf16tc,fp16tc")
+    ap.add_argument("--mixes", default="")
+    ap.add_argument("--sweep", action="store_true", help="per-kernel precision sweep (27 mixes)")
+    ap.add_argument("--adjoint", action="store_true", help="also time the adjoint (acoustics)")
+    ap.add_argument("--nsnap", type=int, default=10)
     ap.add_argument("--headline", default="fp32")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -265,14 +320,20 @@ def main():
     ws, rank, local = dist_setup()
     adg.load()
     peaks, peak_src = load_peaks()
-    mixes = [m for m in args.mixes.split(",") if m]
-    headline = args.headline if args.headline in mixes else mixes[-1]
+    table = dict(MIXES)
+    if args.sweep:
+        table.update(sweep_mixes())
+        mixes = list(sweep_mixes())
+    else:
+        mixes = [m for m in (args.mixes or DEFAULT_MIXES[args.workload]).split(",") if m]
+    headline = args.headline if args.headline in mixes else (
+        "fp32" if "fp32" in mixes else "pred-fp32_riem-fp32_corr-fp32" if args.sweep else mixes[-1])
     results = {}
     ref_state = None
     launches = 0
     clocks = None
     for mix in mixes:
-        prec = MIXES[mix]
+        prec = table[mix]
         s = adg.Solver(wl.dim, wl.N, wl.cells, wl.pde, wl.params, cfl=wl.cfl, precision=prec,
                        flags=MIX_FLAGS.get(mix, 0))
         s.set_initial(wl.scenario, wl.sp)
@@ -299,8 +360,10 @@ def main():
         r = {"dof_per_s": ws * wl.dofs * args.steps / (ms * 1e-3), "ms_per_step": ms / args.steps,
              "ms_predictor": ms_pred / args.steps, "ms_corrector": ms_corr / args.steps, "t": t}
         if wl.has_exact:
-            r["l2_vs_exact"] = s.error_vs_exact()[1]
-        if mix == "fp64":
+            per, tot = s.error_vs_exact()
+            r["l2_vs_exact"] = tot
+            r["l2_vs_exact_per_var"] = [float(x) for x in per]
+        if all(v == "fp64" for v in prec.values()):  # the plain FP64 reference
             ref_state = s.Q.clone()
             ref_norm = s.l2_diff(torch.zeros_like(s.Q))[1]
             r["l2_rel_vs_fp64_gpu"] = 0.0
@@ -309,14 +372,15 @@ def main():
         # roofline of the dominant kernel (the predictor)
         cells = wl.ncells
         fl = predictor_flops_per_cell(wl.pde, wl.dim, wl.N) * cells
-        kind = "fp64" if prec["picard"] == "fp64" else "fp32"
+        kind = {"fp64": "fp64", "bf16": "fp32" if prec["predictor"] == "fp32" else "bf16"}.get(
+            prec["picard"], "fp32")
         sm_mhz = peaks.get("sm_max_mhz", 2070.0)
         pk = alu_peak_tflops(kind, sm_mhz)
         ach = fl / (ms_pred / args.steps * 1e-3) / 1e12
         r["roofline"] = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
                          "frac": ach / pk, "traffic": None,
                          "kernel": "k_predictor", "peak_source": f"{kind} ALU derived at {sm_mhz:.0f} MHz"}
-        tb = 8 if prec["corrector"] == "fp64" else 4
+        tb = {"fp64": 8, "fp32": 4, "bf16": 2}[prec["corrector"]]
         bts = predictor_bytes_per_cell(wl.pde, wl.dim, wl.N, tb) * cells
         r["predictor_gbs"] = bts / (ms_pred / args.steps * 1e-3) / 1e9
         results[mix] = r
@@ -341,6 +405,9 @@ def main():
         del s
         torch.cuda.empty_cache()
 
+    adjoint = None
+    if args.adjoint and wl.pde == I.ACOUSTIC and wl.dim == 3:
+        adjoint = time_adjoint(adg, wl, args.nsnap)
     if rank != 0:
         return
     h = results[headline]
@@ -361,6 +428,8 @@ def main():
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    if adjoint is not None:
+        line["adjoint"] = adjoint
     print(json.dumps(line), flush=True)
 
 

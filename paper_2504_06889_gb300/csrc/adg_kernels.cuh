@@ -59,6 +59,15 @@ template <class T> struct Tab {
   __device__ static __forceinline__ T psi0(const Tables& t, int r) { return (T)t.psi0[r]; }
   __device__ static __forceinline__ T psi1(const Tables& t, int r) { return (T)t.psi1[r]; }
 };
+template <> struct Tab<__nv_bfloat16> {
+  using B = __nv_bfloat16;
+  __device__ static __forceinline__ B D(const Tables& t, int r, int c) { return __float2bfloat16(t.fD[r][c]); }
+  __device__ static __forceinline__ B P(const Tables& t, int r, int c) { return __float2bfloat16(t.fP[r][c]); }
+  __device__ static __forceinline__ B Vm(const Tables& t, int r, int c) { return __float2bfloat16(t.fVm[r][c]); }
+  __device__ static __forceinline__ B w(const Tables& t, int r) { return __float2bfloat16(t.fw[r]); }
+  __device__ static __forceinline__ B psi0(const Tables& t, int r) { return __float2bfloat16(t.fpsi0[r]); }
+  __device__ static __forceinline__ B psi1(const Tables& t, int r) { return __float2bfloat16(t.fpsi1[r]); }
+};
 template <> struct Tab<float> {
   __device__ static __forceinline__ float D(const Tables& t, int r, int c) { return t.fD[r][c]; }
   __device__ static __forceinline__ float P(const Tables& t, int r, int c) { return t.fP[r][c]; }
@@ -118,6 +127,17 @@ template <int S> struct VecLoad<double, S> {
   }
 };
 
+template <int S> struct VecLoad<__nv_bfloat16, S> {
+  __device__ static __forceinline__ void load(const __nv_bfloat16* p, __nv_bfloat16* out) {
+#pragma unroll
+    for (int j = 0; j < S; j += 2) {
+      const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162*>(p + j);
+      out[j] = v.x;
+      out[j + 1] = v.y;
+    }
+  }
+};
+
 template <class C, class T, class TP> struct PredSmem {
   // two flux-slice buffers (double buffering) during the sweeps
   static constexpr size_t sweep = sizeof(T) * 2 * C::CPB * C::D * C::V * Pencil<C>::PER_DIR;
@@ -153,7 +173,7 @@ __device__ __forceinline__ void predictor_final(const StepArgs& a, const T (*q)[
   for (int k = 0; k < n; ++k) {
     TP qk[V];
 #pragma unroll
-    for (int v = 0; v < V; ++v) qk[v] = (TP)q[k][v];
+    for (int v = 0; v < V; ++v) qk[v] = conv<TP>(q[k][v]);
     TP F[D][V];
     Ph::flux(ppP, qk, F);
     const TP wk = sw[k];
@@ -180,7 +200,7 @@ __device__ __forceinline__ void predictor_final(const StepArgs& a, const T (*q)[
 
   // ---- volume integral: Q_i += dt sum_dir (1/h_dir) sum_m Vm[i_dir][m] Fbar(i[dir<-m]) --------
   if (valid && owner) {
-    const TP ihp[3] = {(TP)a.invh[0], (TP)a.invh[1], (TP)a.invh[2]};
+    const TP ihp[3] = {conv<TP>(a.invh[0]), conv<TP>(a.invh[1]), conv<TP>(a.invh[2])};
     double* Qw = a.Q + (size_t)cell * V * NS;
 #pragma unroll
     for (int v = 0; v < V; ++v) {
@@ -195,7 +215,7 @@ __device__ __forceinline__ void predictor_final(const StepArgs& a, const T (*q)[
         for (int m = 0; m < n; ++m) s += Vr[m] * Fp[m];
         vol += s * ihp[dir];
       }
-      Qw[v * NS + i] += dt * (double)vol;
+      Qw[v * NS + i] += dt * conv<double>(vol);
     }
   }
 
@@ -225,7 +245,7 @@ __device__ __forceinline__ void predictor_final(const StepArgs& a, const T (*q)[
           for (int m = 0; m < n; ++m) s += psi[m] * Fp[m];
         }
       }
-      tr[it] = (TS)s;
+      tr[it] = conv<TS>(s);
     }
   }
 }
@@ -249,7 +269,7 @@ __global__ void __launch_bounds__(C::THREADS) k_predictor(const __grid_constant_
   TP* sw = sVm + n * n;
   TP* sp0 = sw + n;
   TP* sp1 = sp0 + n;
-  const T dtT = (T)dt;
+  const T dtT = conv<T>(dt);
   for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
     const int r = t / n, cidx = t % n;
     sdtP[t] = dtT * Tab<T>::P(a.tab, r, cidx);
@@ -280,7 +300,7 @@ __global__ void __launch_bounds__(C::THREADS) k_predictor(const __grid_constant_
   T Dr[D][S];
 #pragma unroll
   for (int dir = 0; dir < D; ++dir) {
-    const T ih = (T)a.invh[dir];
+    const T ih = conv<T>(a.invh[dir]);
 #pragma unroll
     for (int m = 0; m < S; ++m) Dr[dir][m] = m < n ? Tab<T>::D(a.tab, idx[dir], m) * ih : T(0);
   }
@@ -289,7 +309,7 @@ __global__ void __launch_bounds__(C::THREADS) k_predictor(const __grid_constant_
   T Qh[V];
   const double* Qc = a.Q + (size_t)cl * V * NS;
 #pragma unroll
-  for (int v = 0; v < V; ++v) Qh[v] = (T)Qc[v * NS + i];
+  for (int v = 0; v < V; ++v) Qh[v] = conv<T>(Qc[v * NS + i]);
 
   T* sFbuf = reinterpret_cast<T*>(smem_raw);
   constexpr size_t bufsz = (size_t)CPB * D * V * PD;
@@ -819,6 +839,10 @@ Entry make_entry() {
   e.corrector[P64][P32] = launch_corrector<C, double, float, float>;
   e.corrector[P32][P64] = launch_corrector<C, float, double, double>;
   if constexpr (with_bf16) {
+    // the whole predictor in bf16 arithmetic (the paper's "kernel computed in bf16")
+    e.predictor[PBF16][P64] = launch_predictor<C, __nv_bfloat16, __nv_bfloat16, double>;
+    e.predictor[PBF16][P32] = launch_predictor<C, __nv_bfloat16, __nv_bfloat16, float>;
+    e.predictor[PBF16][PBF16] = launch_predictor<C, __nv_bfloat16, __nv_bfloat16, __nv_bfloat16>;
     e.predictor[P64][PBF16] = launch_predictor<C, double, double, __nv_bfloat16>;
     e.predictor[P32][PBF16] = launch_predictor<C, float, float, __nv_bfloat16>;
     e.corrector[PBF16][PBF16] = launch_corrector<C, __nv_bfloat16, __nv_bfloat16, __nv_bfloat16>;

@@ -140,6 +140,17 @@ def test_swe_bf16_riemann_corrector_bounded(adg, oracle_mod, pic, rie, cor):
     assert np.all(np.isfinite(Qg))
 
 
+@pytest.mark.parametrize("cor", ["fp64", "fp32", "bf16"])
+def test_swe_bf16_predictor_bounded(adg, oracle_mod, cor):
+    """The whole predictor in bf16 arithmetic (the paper's lowered-kernel semantics)."""
+    wl = SMALL[8]
+    M, Qo, to = oracle_run(oracle_mod, wl, wl.steps)
+    _, Qg, _ = gpu_run(adg, wl, wl.steps,
+                       precision={"picard": "bf16", "predictor": "bf16", "riemann": cor, "corrector": cor})
+    assert np.all(np.isfinite(Qg))
+    assert rel_l2(M, Qg, Qo) <= wl.steps * 2.0 ** -8
+
+
 def test_single_cell_periodic_mesh(adg, oracle_mod):
     """m = 1 along a direction: the cell is its own neighbour."""
     wl = I.euler3d_wave(N=2).with_cells((1, 2, 1), 3)
