@@ -85,17 +85,19 @@ def predictor_flops_per_cell(pde, dim, N, iters=None):
     """Algorithmic flops of the predictor kernel for one cell (sum-factorised, no padding):
     I sweeps x n time slices x NS nodes x (flux + derivative contractions on the nonzero flux
     components + time operator), then the final flux, time averages, volume integral and
-    face extrapolation."""
+    face extrapolation.  The first sweep starts from q = Q at every time node, so its n slices
+    are one: it costs one slice's flux and contraction plus the n updates per variable."""
     n = N + 1
     NS, NF = n ** dim, n ** (dim - 1)
     V = I.nvar(pde, dim)
     fl, nz = FLUX_FLOPS[(pde, dim)], NZ[(pde, dim)]
     it = n if iters is None else iters
     sweep = n * NS * (fl + nz * 2 * n + V * 2 * n)
+    first = NS * (fl + nz * 2 * n + V * 2 * n)
     final = n * NS * (fl + 2 * V + 2 * nz)
     vol = NS * nz * 2 * n
     traces = 2 * dim * NF * 2 * V * 2 * n
-    return it * sweep + final + vol + traces
+    return (first + (it - 1) * sweep if it > 0 else 0) + final + vol + traces
 
 
 def predictor_bytes_per_cell(pde, dim, N, trace_bytes):

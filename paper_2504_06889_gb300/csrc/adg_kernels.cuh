@@ -144,7 +144,7 @@ template <class C, class T, class TP> struct PredSmem {
   // final stage: Fbar in pencil layout + Qbar
   static constexpr size_t fin = sizeof(TP) * C::CPB * (C::D * C::V * Pencil<C>::PER_DIR + C::V * C::NS);
   static constexpr size_t big = ((sweep > fin ? sweep : fin) + 15) / 16 * 16;
-  static constexpr size_t tables = sizeof(T) * C::n * C::n + sizeof(TP) * (C::n * C::n + 3 * C::n);
+  static constexpr size_t tables = sizeof(T) * (C::n * C::n + C::n + 1) + sizeof(TP) * (C::n * C::n + 3 * C::n);
   static constexpr size_t total = big + tables;
 };
 
@@ -263,9 +263,11 @@ __global__ void __launch_bounds__(C::THREADS) k_predictor(const __grid_constant_
   if (a.sc->bad) return;
   const double dt = block_dt(a, D, C::N, &s_dt);
 
-  // tables: dt P (T), then Vm, w, psi0, psi1 (TP)
+  // tables: dt P and its row sums (T), then Vm, w, psi0, psi1 (TP)
   T* sdtP = reinterpret_cast<T*>(smem_raw + PredSmem<C, T, TP>::big);
-  TP* sVm = reinterpret_cast<TP*>(sdtP + n * n);
+  T* sdtProw = sdtP + n * n;
+  TP* sVm = reinterpret_cast<TP*>(reinterpret_cast<unsigned char*>(smem_raw + PredSmem<C, T, TP>::big) +
+                                  ((sizeof(T) * (n * n + n) + sizeof(TP) - 1) / sizeof(TP)) * sizeof(TP));
   TP* sw = sVm + n * n;
   TP* sp0 = sw + n;
   TP* sp1 = sp0 + n;
@@ -279,6 +281,9 @@ __global__ void __launch_bounds__(C::THREADS) k_predictor(const __grid_constant_
     sw[t] = Tab<TP>::w(a.tab, t);
     sp0[t] = Tab<TP>::psi0(a.tab, t);
     sp1[t] = Tab<TP>::psi1(a.tab, t);
+    T rs = T(0);
+    for (int l = 0; l < n; ++l) rs += Tab<T>::P(a.tab, t, l);
+    sdtProw[t] = dtT * rs;
   }
 
   const int lc = threadIdx.x / NS, i = threadIdx.x % NS;
@@ -325,7 +330,37 @@ __global__ void __launch_bounds__(C::THREADS) k_predictor(const __grid_constant_
 
   __syncthreads();
   int buf = 0;
-  for (int r = 0; r < a.picard_iters; ++r) {
+  // Sweep 1 starts from q = Q at every time node, so all time slices share one flux and one
+  // derivative R: q^1[kk] = Q - dt (sum_l P[kk][l]) R.
+  if (a.picard_iters > 0) {
+    T* sF = sFbuf + (size_t)lc * D * V * PD;
+    {
+      T F[D][V];
+      Ph::flux(pp, Qh, F);
+#pragma unroll
+      for (int dir = 0; dir < D; ++dir)
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+          if (Ph::nz(dir, v)) sF[(dir * V + v) * PD + pb[dir] + idx[dir]] = F[dir][v];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      T rv = T(0);
+#pragma unroll
+      for (int dir = 0; dir < D; ++dir) {
+        if (!Ph::nz(dir, v)) continue;
+        T f[S];
+        VecLoad<T, S>::load(sF + (dir * V + v) * PD + pb[dir], f);
+#pragma unroll
+        for (int m = 0; m < n; ++m) rv += Dr[dir][m] * f[m];
+      }
+#pragma unroll
+      for (int kk = 0; kk < n; ++kk) q[kk][v] = Qh[v] - sdtProw[kk] * rv;
+    }
+    buf = 1;
+  }
+  for (int r = 1; r < a.picard_iters; ++r) {
     T qn[n][V];
 #pragma unroll
     for (int k = 0; k < n; ++k)
