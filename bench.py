@@ -54,13 +54,15 @@ MIXES = {
     # power-of-two scaling, compensated hi/lo last sweep); everything else as in "fp32"
     "bf16tc": {"picard": "bf16", "predictor": "fp32", "riemann": "fp32", "corrector": "fp32"},
     "fp16tc": {"picard": "fp16", "predictor": "fp32", "riemann": "fp32", "corrector": "fp32"},
+    # E4M3 inputs (kind::f8f6f4, K = 32 per instruction: four pencils per accumulator row)
+    "fp8tc": {"picard": "fp8", "predictor": "fp32", "riemann": "fp32", "corrector": "fp32"},
 }
-MIX_FLAGS = {"bf16tc": 1 | 2, "fp16tc": 1 | 2}
+MIX_FLAGS = {"bf16tc": 1 | 2, "fp16tc": 1 | 2, "fp8tc": 1 | 2}
 
 # default mixes per workload (the tensor-core predictor is built for the 3D meshes)
 DEFAULT_MIXES = {
-    "euler3d": "fp64,fp32pred,fp32,bf16tc,fp16tc",
-    "elastic3d": "fp64,fp32,fp16tc,bf16tc",
+    "euler3d": "fp64,fp32pred,fp32,bf16tc,fp16tc,fp8tc",
+    "elastic3d": "fp64,fp32,fp16tc,bf16tc,fp8tc",
     "acoustic3d": "fp64,fp32,fp16tc",
     "acoustic2d": "fp64,fp32",
     "swe2d": "fp64,fp32pred,fp32",
@@ -78,7 +80,7 @@ def sweep_mixes():
                                                     "corrector": c}
     return out
 DTYPE = {"fp64": "f64", "fp32pred": "f32+f64", "fp32": "f32+f64", "bf16tc": "bf16+f32+f64",
-         "fp16tc": "f16+f32+f64"}
+         "fp16tc": "f16+f32+f64", "fp8tc": "e4m3+f32+f64"}
 
 
 def predictor_flops_per_cell(pde, dim, N, iters=None):

@@ -114,8 +114,8 @@ ADG_API int adg_init_mesh(adg_ctx* c, int dim, int order_N, const int* cells, co
 ADG_API int adg_set_pde(adg_ctx* c, int pde, const double* params, int nparams);
 
 /* Precision of one kernel (Sec. 3.1).  Built combinations:
- *   PICARD     FP64, FP32 (SIMT, must equal PREDICTOR); BF16, FP16 with PREDICTOR FP32
- *              (tensor cores, FP32 accumulation, 3D meshes, CORRECTOR FP32 or FP64; flags
+ *   PICARD     FP64, FP32 (SIMT, must equal PREDICTOR); BF16, FP16, FP8E4M3 with PREDICTOR
+ *              FP32 (tensor cores, FP32 accumulation, 3D meshes, CORRECTOR FP32 or FP64; flags
  *              (ADG_F_*) given with the PICARD call select compensation and per-cell scaling);
  *              BF16 with PREDICTOR BF16: the whole predictor in bf16 arithmetic (SIMT, built
  *              for shallow water)

@@ -380,7 +380,8 @@ int adg_set_kernel_precision(adg_ctx* c, int kernel, int prec, int flags) {
   if (prec < 0 || prec > ADG_FP8E4M3) return fail(c, ADG_EINVAL, "unknown precision");
   if (kernel == ADG_K_STORAGE && prec != ADG_FP64)
     return fail(c, ADG_EUNSUPPORTED, "storage precision other than FP64 is not built");
-  if (prec == ADG_FP8E4M3) return fail(c, ADG_EUNSUPPORTED, "fp8 not built");
+  if (prec == ADG_FP8E4M3 && kernel != ADG_K_PICARD)
+    return fail(c, ADG_EUNSUPPORTED, "fp8 is built for the Picard contractions only");
   if (kernel == ADG_K_PREDICTOR && prec == ADG_FP16)
     return fail(c, ADG_EUNSUPPORTED, "the predictor's final stage runs in FP64, FP32 or bf16");
   if ((kernel == ADG_K_RIEMANN || kernel == ADG_K_CORRECTOR) && prec == ADG_FP16)
@@ -522,10 +523,10 @@ static int select_kernels(adg_ctx* c, StepFn* pred, StepFn* corr) {
   const int pic = c->prec[ADG_K_PICARD], prd = c->prec[ADG_K_PREDICTOR];
   const int rie = c->prec[ADG_K_RIEMANN], cor = c->prec[ADG_K_CORRECTOR];
   if (rie > PBF16 || cor > PBF16) return fail(c, ADG_EUNSUPPORTED, "precision mix not built");
-  if ((pic == PBF16 && prd == P32) || pic == PF16) {
+  if ((pic == PBF16 && prd == P32) || pic == PF16 || pic == PF8) {
     if (prd != P32) return fail(c, ADG_EUNSUPPORTED, "tensor-core Picard needs an FP32 predictor stage");
     if (cor > P32) return fail(c, ADG_EUNSUPPORTED, "tensor-core Picard writes FP32 or FP64 traces");
-    *pred = c->entry->predictor_tc[pic == PF16 ? 1 : 0][cor];
+    *pred = c->entry->predictor_tc[pic == PF16 ? 1 : pic == PF8 ? 2 : 0][cor];
   } else if (pic == PBF16 && prd == PBF16) {
     *pred = c->entry->predictor[PBF16][cor];  // SIMT, all arithmetic in bf16 (shallow water)
   } else {

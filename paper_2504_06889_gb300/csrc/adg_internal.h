@@ -107,8 +107,8 @@ struct Entry {
   int V, NS, NF;
   StepFn predictor[3][3];
   StepFn corrector[3][3];
-  // tensor-core Picard with FP32 final stage: [0 = bf16, 1 = fp16][trace prec]
-  StepFn predictor_tc[2][3];
+  // tensor-core Picard with FP32 final stage: [0 = bf16, 1 = fp16, 2 = fp8 E4M3][trace prec]
+  StepFn predictor_tc[3][3];
   // discrete adjoint (linear acoustics): face projections, per-cell adjoint [0 = FP64, 1 = FP32]
   void* adj_trace;
   void* adj_cell[2];

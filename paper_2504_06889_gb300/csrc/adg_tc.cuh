@@ -19,6 +19,7 @@
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include "adg_kernels.cuh"
 
@@ -40,36 +41,65 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
   return d;
 }
 
-// byte offset of (row, col) in a K-major 16-bit tile: core matrices of 8 rows x 16 bytes,
-// the two K cores of a row group 128 bytes apart, row groups 256 bytes apart
-__host__ __device__ constexpr int koff(int r, int c) {
-  return (r >> 3) * 256 + (c >> 3) * 128 + (r & 7) * 16 + (c & 7) * 2;
-}
-
 template <class TIN> struct In;
 template <> struct In<__nv_bfloat16> {
-  static constexpr uint32_t fmt = 1;  // instruction-descriptor A/B format: BF16
+  static constexpr int ES = 2;        // bytes per element
+  static constexpr uint32_t fmt = 1;  // instruction-descriptor A/B format (kind::f16): BF16
+  static constexpr int scale_exp = 0; // per-cell scaling puts max|F| in [2^e, 2^(e+1))
   __device__ static __forceinline__ __nv_bfloat16 cvt(float x) { return __float2bfloat16_rn(x); }
   __device__ static __forceinline__ float back(__nv_bfloat16 x) { return __bfloat162float(x); }
 };
 template <> struct In<__half> {
+  static constexpr int ES = 2;
   static constexpr uint32_t fmt = 0;  // F16
+  static constexpr int scale_exp = 0;
   __device__ static __forceinline__ __half cvt(float x) { return __float2half_rn(x); }
   __device__ static __forceinline__ float back(__half x) { return __half2float(x); }
 };
+template <> struct In<__nv_fp8_e4m3> {
+  static constexpr int ES = 1;
+  static constexpr uint32_t fmt = 0;  // kind::f8f6f4: E4M3
+  static constexpr int scale_exp = 7; // max 448: scaled max in [128, 256)
+  __device__ static __forceinline__ __nv_fp8_e4m3 cvt(float x) { return __nv_fp8_e4m3(x); }  // RNE, satfinite
+  __device__ static __forceinline__ float back(__nv_fp8_e4m3 x) { return float(x); }
+};
 
-// kind::f16 instruction descriptor: FP32 accumulator, A and B K-major, M = 128, N = 16
-template <class TIN> __host__ __device__ constexpr uint32_t idesc_m128_n16() {
-  return (1u << 4) | (In<TIN>::fmt << 7) | (In<TIN>::fmt << 10) | ((16u >> 3) << 17) |
+// Geometry of one UMMA: a core-matrix row is 16 bytes (8 or 16 elements); K spans two K cores
+// (16 for 16-bit, 32 for 8-bit inputs); a pencil of <= 8 nodes takes an 8-wide slot of K, so an
+// A row holds SLOTS pencils and N = 8 SLOTS outputs.
+template <class TIN> struct Geo {
+  static constexpr int ES = In<TIN>::ES;
+  static constexpr int CE = 16 / ES;
+  static constexpr int K = 2 * CE;
+  static constexpr int SLOTS = K / 8;
+  static constexpr int N = SLOTS * 8;
+  static constexpr int B_BYTES = N * K * ES;
+};
+
+// byte offset of (row, col) in a K-major tile: core matrices of 8 rows x 16 bytes, the two K
+// cores of a row group 128 bytes apart, row groups 256 bytes apart
+template <class TIN> __host__ __device__ constexpr int koff(int r, int c) {
+  return (r >> 3) * 256 + (c / Geo<TIN>::CE) * 128 + (r & 7) * 16 + (c % Geo<TIN>::CE) * Geo<TIN>::ES;
+}
+
+// instruction descriptor: FP32 accumulator, A and B K-major, M = 128, N = Geo::N
+template <class TIN> __host__ __device__ constexpr uint32_t idesc_m128() {
+  return (1u << 4) | (In<TIN>::fmt << 7) | (In<TIN>::fmt << 10) | ((uint32_t)(Geo<TIN>::N >> 3) << 17) |
          ((128u >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                    uint32_t accumulate) {
-  asm volatile(
-      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+template <class TIN> __device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                                         uint32_t accumulate) {
+  if constexpr (In<TIN>::ES == 1)
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+  else
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
 }
 
 __device__ __forceinline__ void commit(uint64_t* mbar) {
@@ -111,34 +141,39 @@ constexpr int pow2_cols(int c) { return c <= 32 ? 32 : c <= 64 ? 64 : c <= 128 ?
 
 }  // namespace tc
 
-template <class C> struct TcCfg {
+template <class C, class TIN> struct TcCfg {
+  using GE = tc::Geo<TIN>;
+  static constexpr int SLOTS = GE::SLOTS;   // pencils per A row
+  static constexpr int NCOL = GE::N;        // accumulator columns per tile
   static constexpr int NP = C::NF;          // pencils per direction
-  static constexpr int NPP = (NP + 1) / 2;  // pencil pairs: A rows per variable
+  static constexpr int NPP = (NP + SLOTS - 1) / SLOTS;  // A rows per variable
   static constexpr int ROWS = C::V * NPP;
   static constexpr int TILES = (ROWS + 127) / 128;
   static constexpr int THREADS = (((C::NS + 31) / 32) * 32) < 128 ? 128 : ((C::NS + 31) / 32) * 32;
   static constexpr int NWARPS = THREADS / 32;
-  static constexpr int TCOLS = tc::pow2_cols(C::D * TILES * 16);
+  static constexpr int TCOLS = tc::pow2_cols(C::D * TILES * NCOL);
   static constexpr size_t A_DIR = (size_t)TILES * 4096;  // one direction, one of hi/lo
   static constexpr size_t A_ALL = 2 * C::D * A_DIR;
-  static constexpr size_t B_OFF = A_ALL;                // B hi, B lo: 512 bytes each
-  static constexpr size_t R_OFF = B_OFF + 1024;         // per-direction derivatives, FP32
+  static constexpr size_t B_OFF = A_ALL;                // B hi, B lo
+  static constexpr size_t R_OFF = B_OFF + 2 * GE::B_BYTES;  // per-direction derivatives, FP32
   static constexpr int RS = Pencil<C>::S;                 // pencil stride of the derivative buffer
-  static constexpr int R_PER_V = 2 * NPP * RS;            // one direction, one variable
+  static constexpr int R_PER_V = SLOTS * NPP * RS;        // one direction, one variable
   static constexpr size_t SWEEP = R_OFF + sizeof(float) * C::D * C::V * R_PER_V;
   static constexpr size_t FIN = sizeof(float) * (C::D * C::V * Pencil<C>::PER_DIR + C::V * C::NS);
   static constexpr size_t BIG = ((SWEEP > FIN ? SWEEP : FIN) + 127) / 128 * 128;
   static constexpr size_t TABLES = sizeof(float) * (2 * C::n * C::n + 3 * C::n);
   static constexpr size_t TOTAL = BIG + TABLES;
   // one cell per CTA (independent of the SIMT kernels' cells per block)
-  static_assert(C::n <= 8, "pencils must fit one 8-wide core matrix");
+  static_assert(C::n <= 8, "pencils must fit one 8-wide slot");
+  static_assert(TCOLS <= 512, "accumulators must fit tensor memory");
 };
 
 template <class C, class TIN, class TS>
-__global__ void __launch_bounds__(TcCfg<C>::THREADS) k_predictor_tc(const __grid_constant__ StepArgs a,
-                                                                    int comp_sweeps, int per_cell_scale) {
+__global__ void __launch_bounds__(TcCfg<C, TIN>::THREADS)
+    k_predictor_tc(const __grid_constant__ StepArgs a, int comp_sweeps, int per_cell_scale) {
   using Ph = Phys<C::PDE, C::D>;
-  using G = TcCfg<C>;
+  using G = TcCfg<C, TIN>;
+  using GE = tc::Geo<TIN>;
   using T = float;
   constexpr int n = C::n, V = C::V, D = C::D, NS = C::NS;
   constexpr int NPP = G::NPP, TILES = G::TILES, NWARPS = G::NWARPS;
@@ -177,14 +212,14 @@ __global__ void __launch_bounds__(TcCfg<C>::THREADS) k_predictor_tc(const __grid
   // zero the operand tiles (pads stay zero), build B = diag(D, D) split into hi + lo
   for (size_t t = tid; t < G::R_OFF / 4; t += blockDim.x) reinterpret_cast<uint32_t*>(smem_raw)[t] = 0u;
   __syncthreads();
-  for (int t = tid; t < 256; t += blockDim.x) {
-    const int nn = t / 16, kk = t % 16;  // B[n][k]: output n, contraction index k
+  for (int t = tid; t < GE::N * GE::K; t += blockDim.x) {
+    const int nn = t / GE::K, kk = t % GE::K;  // B[n][k]: output n, contraction index k
     float dv = 0.0f;
     if ((nn >> 3) == (kk >> 3) && (nn & 7) < n && (kk & 7) < n) dv = Tab<float>::D(a.tab, nn & 7, kk & 7);
     const TIN hi = tc::In<TIN>::cvt(dv);
     const TIN lo = tc::In<TIN>::cvt(dv - tc::In<TIN>::back(hi));
-    *reinterpret_cast<TIN*>(smem_raw + G::B_OFF + tc::koff(nn, kk)) = hi;
-    *reinterpret_cast<TIN*>(smem_raw + G::B_OFF + 512 + tc::koff(nn, kk)) = lo;
+    *reinterpret_cast<TIN*>(smem_raw + G::B_OFF + tc::koff<TIN>(nn, kk)) = hi;
+    *reinterpret_cast<TIN*>(smem_raw + G::B_OFF + GE::B_BYTES + tc::koff<TIN>(nn, kk)) = lo;
   }
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(&s_mbar)));
@@ -213,13 +248,13 @@ __global__ void __launch_bounds__(TcCfg<C>::THREADS) k_predictor_tc(const __grid
   }
   // pencil p of a direction sits in A row p % NPP, slot p / NPP (consecutive pencils in
   // consecutive 16-byte rows of a core matrix: conflict-free stores); its derivatives come back
-  // to position (2 (p % NPP) + p / NPP) * RS of the derivative buffer
+  // to position (SLOTS (p % NPP) + p / NPP) * RS of the derivative buffer
   int arow[3], acol[3], rpos[3];
 #pragma unroll
   for (int dir = 0; dir < D; ++dir) {
     arow[dir] = pen[dir] % NPP;
     acol[dir] = (pen[dir] / NPP) * 8 + idx[dir];
-    rpos[dir] = (2 * arow[dir] + pen[dir] / NPP) * G::RS + idx[dir];
+    rpos[dir] = (G::SLOTS * arow[dir] + pen[dir] / NPP) * G::RS + idx[dir];
   }
   const PP<T> pp = make_pp<T>(a.pp, cl);
   T Qh[V];
@@ -247,11 +282,12 @@ __global__ void __launch_bounds__(TcCfg<C>::THREADS) k_predictor_tc(const __grid
   tc::fence_after();
   const uint32_t tmem = s_tmem;
   auto scale_from = [&](uint32_t bits) {
-    // 2^-floor(log2(max|F|)): scaled magnitudes below 2
+    // 2^(e0 - floor(log2(max|F|))): scaled magnitudes in [2^e0, 2^(e0+1)) (e0 = 0 for 16-bit,
+    // 7 for E4M3 whose largest value is 448)
     if (!per_cell_scale) return 1.0f;
     const int e = (int)((bits >> 23) & 0xFFu) - 127;
     if (bits == 0u || e > 100 || e < -100) return 1.0f;
-    return __uint_as_float((uint32_t)(127 - e) << 23);
+    return __uint_as_float((uint32_t)(127 + tc::In<TIN>::scale_exp - e) << 23);
   };
   float sc = scale_from(s_fmax[1]);
 
@@ -261,9 +297,9 @@ __global__ void __launch_bounds__(TcCfg<C>::THREADS) k_predictor_tc(const __grid
 #pragma unroll
     for (int v = 0; v < V; ++v) q[k][v] = Qh[v];
 
-  const uint32_t idesc = tc::idesc_m128_n16<TIN>();
+  const uint32_t idesc = tc::idesc_m128<TIN>();
   const uint32_t a_base = tc::smem_u32(smem_raw);
-  const uint32_t b_hi = a_base + (uint32_t)G::B_OFF, b_lo = b_hi + 512u;
+  const uint32_t b_hi = a_base + (uint32_t)G::B_OFF, b_lo = b_hi + (uint32_t)GE::B_BYTES;
   float* sR = reinterpret_cast<float*>(smem_raw + G::R_OFF);  // [dir][v][pencil layout]
   const float invh[3] = {(float)a.invh[0], (float)a.invh[1], (float)a.invh[2]};
   uint32_t phase = 0;
@@ -293,7 +329,7 @@ __global__ void __launch_bounds__(TcCfg<C>::THREADS) k_predictor_tc(const __grid
             if (!Ph::nz(dir, v)) continue;
             const float x = F[dir][v] * sc;
             const TIN hi = tc::In<TIN>::cvt(x);
-            const int off = dir * (int)G::A_DIR + tc::koff(v * NPP + arow[dir], acol[dir]);
+            const int off = dir * (int)G::A_DIR + tc::koff<TIN>(v * NPP + arow[dir], acol[dir]);
             *reinterpret_cast<TIN*>(smem_raw + off) = hi;
             if (comp)
               *reinterpret_cast<TIN*>(smem_raw + D * G::A_DIR + off) =
@@ -309,13 +345,13 @@ __global__ void __launch_bounds__(TcCfg<C>::THREADS) k_predictor_tc(const __grid
         for (int dir = 0; dir < D; ++dir)
 #pragma unroll
           for (int t = 0; t < TILES; ++t) {
-            const uint32_t d_t = tmem + (uint32_t)((dir * TILES + t) * 16);
+            const uint32_t d_t = tmem + (uint32_t)((dir * TILES + t) * G::NCOL);
             const uint32_t ahi = a_base + (uint32_t)(dir * G::A_DIR + t * 4096);
-            tc::mma(d_t, tc::sdesc(ahi, 128, 256), tc::sdesc(b_hi, 128, 256), idesc, 0u);
+            tc::mma<TIN>(d_t, tc::sdesc(ahi, 128, 256), tc::sdesc(b_hi, 128, 256), idesc, 0u);
             if (comp) {
               const uint32_t alo = ahi + (uint32_t)(D * G::A_DIR);
-              tc::mma(d_t, tc::sdesc(ahi, 128, 256), tc::sdesc(b_lo, 128, 256), idesc, 1u);
-              tc::mma(d_t, tc::sdesc(alo, 128, 256), tc::sdesc(b_hi, 128, 256), idesc, 1u);
+              tc::mma<TIN>(d_t, tc::sdesc(ahi, 128, 256), tc::sdesc(b_lo, 128, 256), idesc, 1u);
+              tc::mma<TIN>(d_t, tc::sdesc(alo, 128, 256), tc::sdesc(b_hi, 128, 256), idesc, 1u);
             }
           }
         tc::commit(&s_mbar);
@@ -331,16 +367,19 @@ __global__ void __launch_bounds__(TcCfg<C>::THREADS) k_predictor_tc(const __grid
         for (int u = slot; u < D * TILES; u += nwq) {
           const int dir = u / TILES, t = u % TILES;
           if (t * 128 + qtr * 32 >= G::ROWS) continue;  // whole quarter is padding (warp-uniform)
-          float o[16];
-          tc::ld16(tmem + ((uint32_t)(qtr * 32) << 16) + (uint32_t)((dir * TILES + t) * 16), o);
+          float o[G::NCOL];
+#pragma unroll
+          for (int h = 0; h < G::NCOL / 16; ++h)
+            tc::ld16(tmem + ((uint32_t)(qtr * 32) << 16) + (uint32_t)((dir * TILES + t) * G::NCOL + 16 * h),
+                     o + 16 * h);
           const int row = t * 128 + qtr * 32 + lane;
           if (row < G::ROWS) {
-            // the two pencils of this row, contiguous in the pencil layout: 8-byte stores
+            // the SLOTS pencils of this row, contiguous in the pencil layout: 8-byte stores
             const int v = row / NPP, pr = row % NPP;
             const float f = inv_sc * invh[dir];
-            float* dst = sR + (dir * V + v) * G::R_PER_V + 2 * pr * G::RS;
+            float* dst = sR + (dir * V + v) * G::R_PER_V + G::SLOTS * pr * G::RS;
 #pragma unroll
-            for (int s2 = 0; s2 < 2; ++s2)
+            for (int s2 = 0; s2 < G::SLOTS; ++s2)
 #pragma unroll
               for (int m = 0; m < G::RS; m += 2)
                 *reinterpret_cast<float2*>(dst + s2 * G::RS + m) =
@@ -400,7 +439,7 @@ __global__ void __launch_bounds__(TcCfg<C>::THREADS) k_predictor_tc(const __grid
 
 template <class C, class TIN, class TS>
 cudaError_t launch_predictor_tc(const StepArgs& a, cudaStream_t s) {
-  using G = TcCfg<C>;
+  using G = TcCfg<C, TIN>;
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_predictor_tc<C, TIN, TS>,
@@ -412,7 +451,7 @@ cudaError_t launch_predictor_tc(const StepArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// Add the tensor-core predictors (bf16 and fp16 inputs, FP32 / FP64 traces) to an Entry.
+// Add the tensor-core predictors (bf16, fp16 and fp8-E4M3 inputs, FP32 / FP64 traces) to an Entry.
 template <int PDE, int D, int N>
 void add_tc(Entry& e) {
   using C = Cfg<PDE, D, N>;
@@ -420,6 +459,8 @@ void add_tc(Entry& e) {
   e.predictor_tc[0][P64] = launch_predictor_tc<C, __nv_bfloat16, double>;
   e.predictor_tc[1][P32] = launch_predictor_tc<C, __half, float>;
   e.predictor_tc[1][P64] = launch_predictor_tc<C, __half, double>;
+  e.predictor_tc[2][P32] = launch_predictor_tc<C, __nv_fp8_e4m3, float>;
+  e.predictor_tc[2][P64] = launch_predictor_tc<C, __nv_fp8_e4m3, double>;
 }
 
 }  // namespace adg
