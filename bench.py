@@ -57,14 +57,18 @@ MIXES = {
     # E4M3 inputs (kind::f8f6f4, K = 32 per instruction: four pencils per accumulator row)
     "fp8tc": {"picard": "fp8", "predictor": "fp32", "riemann": "fp32", "corrector": "fp32"},
 }
+# Cauchy-Kowalevskaya predictor (linear PDEs) in place of the Picard sweeps
+MIXES["fp64ck"] = dict(MIXES["fp64"])
+MIXES["fp32ck"] = dict(MIXES["fp32"])
+MIX_SCHEME = {"fp64ck": "ck", "fp32ck": "ck"}
 MIX_FLAGS = {"bf16tc": 1 | 2, "fp16tc": 1 | 2, "fp8tc": 1 | 2}
 
 # default mixes per workload (the tensor-core predictor is built for the 3D meshes)
 DEFAULT_MIXES = {
     "euler3d": "fp64,fp32pred,fp32,bf16tc,fp16tc,fp8tc",
-    "elastic3d": "fp64,fp32,fp16tc,bf16tc,fp8tc",
-    "acoustic3d": "fp64,fp32,fp16tc",
-    "acoustic2d": "fp64,fp32",
+    "elastic3d": "fp64,fp32,fp16tc,bf16tc,fp8tc,fp64ck,fp32ck",
+    "acoustic3d": "fp64,fp32,fp16tc,fp64ck,fp32ck",
+    "acoustic2d": "fp64,fp32,fp64ck,fp32ck",
     "swe2d": "fp64,fp32pred,fp32",
 }
 
@@ -80,15 +84,17 @@ def sweep_mixes():
                                                     "corrector": c}
     return out
 DTYPE = {"fp64": "f64", "fp32pred": "f32+f64", "fp32": "f32+f64", "bf16tc": "bf16+f32+f64",
-         "fp16tc": "f16+f32+f64", "fp8tc": "e4m3+f32+f64"}
+         "fp16tc": "f16+f32+f64", "fp8tc": "e4m3+f32+f64", "fp64ck": "f64", "fp32ck": "f32+f64"}
 
 
-def predictor_flops_per_cell(pde, dim, N, iters=None):
+def predictor_flops_per_cell(pde, dim, N, iters=None, scheme="picard"):
     """Algorithmic flops of the predictor kernel for one cell (sum-factorised, no padding):
     I sweeps x n time slices x NS nodes x (flux + derivative contractions on the nonzero flux
     components + time operator), then the final flux, time averages, volume integral and
     face extrapolation.  The first sweep starts from q = Q at every time node, so its n slices
-    are one: it costs one slice's flux and contraction plus the n updates per variable."""
+    are one: it costs one slice's flux and contraction plus the n updates per variable.
+    The Cauchy-Kowalevskaya scheme instead takes N derivative evaluations (flux, contraction,
+    and the n Taylor updates per variable) before the same final stage."""
     n = N + 1
     NS, NF = n ** dim, n ** (dim - 1)
     V = I.nvar(pde, dim)
@@ -99,6 +105,8 @@ def predictor_flops_per_cell(pde, dim, N, iters=None):
     final = n * NS * (fl + 2 * V + 2 * nz)
     vol = NS * nz * 2 * n
     traces = 2 * dim * NF * 2 * V * 2 * n
+    if scheme == "ck":
+        return N * first + final + vol + traces
     return (first + (it - 1) * sweep if it > 0 else 0) + final + vol + traces
 
 
@@ -333,13 +341,14 @@ def main():
     headline = args.headline if args.headline in mixes else (
         "fp32" if "fp32" in mixes else "pred-fp32_riem-fp32_corr-fp32" if args.sweep else mixes[-1])
     results = {}
-    ref_state = None
+    ref_state = {}
     launches = 0
     clocks = None
     for mix in mixes:
         prec = table[mix]
+        scheme = MIX_SCHEME.get(mix, "picard")
         s = adg.Solver(wl.dim, wl.N, wl.cells, wl.pde, wl.params, cfl=wl.cfl, precision=prec,
-                       flags=MIX_FLAGS.get(mix, 0))
+                       flags=MIX_FLAGS.get(mix, 0), scheme=scheme)
         s.set_initial(wl.scenario, wl.sp)
         s.step(args.warmup)
         torch.cuda.synchronize()
@@ -367,15 +376,14 @@ def main():
             per, tot = s.error_vs_exact()
             r["l2_vs_exact"] = tot
             r["l2_vs_exact_per_var"] = [float(x) for x in per]
-        if all(v == "fp64" for v in prec.values()):  # the plain FP64 reference
-            ref_state = s.Q.clone()
-            ref_norm = s.l2_diff(torch.zeros_like(s.Q))[1]
+        if all(v == "fp64" for v in prec.values()):  # the plain FP64 path of this scheme
+            ref_state[scheme] = (s.Q.clone(), s.l2_diff(torch.zeros_like(s.Q))[1])
             r["l2_rel_vs_fp64_gpu"] = 0.0
-        elif ref_state is not None:
-            r["l2_rel_vs_fp64_gpu"] = s.l2_diff(ref_state)[1] / ref_norm
+        elif scheme in ref_state:
+            r["l2_rel_vs_fp64_gpu"] = s.l2_diff(ref_state[scheme][0])[1] / ref_state[scheme][1]
         # roofline of the dominant kernel (the predictor)
         cells = wl.ncells
-        fl = predictor_flops_per_cell(wl.pde, wl.dim, wl.N) * cells
+        fl = predictor_flops_per_cell(wl.pde, wl.dim, wl.N, scheme=scheme) * cells
         kind = {"fp64": "fp64", "bf16": "fp32" if prec["predictor"] == "fp32" else "bf16"}.get(
             prec["picard"], "fp32")
         sm_mhz = peaks.get("sm_max_mhz", 2070.0)

@@ -74,6 +74,9 @@ enum adg_kernel {
 
 enum adg_prec { ADG_FP64 = 0, ADG_FP32 = 1, ADG_BF16 = 2, ADG_FP16 = 3, ADG_FP8E4M3 = 4 };
 
+/* Predictor schemes of Sec. 2.1 (adg_set_predictor) */
+enum adg_predictor { ADG_PRED_PICARD = 0, ADG_PRED_CK = 1 };
+
 enum adg_flags {
   ADG_F_COMPENSATED_LAST = 1, /* tensor-core Picard: last sweep with split hi/lo products */
   ADG_F_PER_CELL_SCALE = 2,   /* tensor-core Picard: power-of-two scaling per cell */
@@ -130,6 +133,16 @@ ADG_API int adg_set_kernel_precision(adg_ctx* c, int kernel, int prec, int flags
 /* C_CFL of eq. (CFL_condition) (dt = cfl h / (d (2N+1) lambda_max)) and the
  * number of Picard sweeps (<= 0: N+1). */
 ADG_API int adg_set_numerics(adg_ctx* c, double cfl, int picard_iters);
+
+/* Predictor scheme (Sec. 2.1).  ADG_PRED_PICARD (default): the Picard sweeps of eq. (Picard),
+ * any PDE.  ADG_PRED_CK: the Cauchy-Kowalevskaya procedure of the last paragraph of Sec. 2.1,
+ * for the linear PDEs only (acoustic, elastic): d_t^{m+1} Q = -sum_d d_d F_d(d_t^m Q) for
+ * m = 0..N-1 and q(tau) = sum_m (tau dt)^m / m! d_t^m Q at the time nodes, followed by the
+ * same time averages, volume integral and face traces.  CK runs with PICARD == PREDICTOR in
+ * {FP64, FP32}.  Unknown schemes return ADG_EINVAL; a nonlinear PDE or another precision
+ * returns ADG_EUNSUPPORTED at the first step; adg_adjoint needs the Picard scheme.  The
+ * allocation-free adg_step_noalloc always runs the FP64 Picard kernels. */
+ADG_API int adg_set_predictor(adg_ctx* c, int scheme);
 
 /* Bytes the caller must provide as workspace for this mesh/PDE/precision. */
 ADG_API int adg_workspace_bytes(const adg_ctx* c, size_t* bytes);

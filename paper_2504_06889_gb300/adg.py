@@ -18,6 +18,7 @@ ACOUSTIC, ELASTIC, EULER, SWE = 0, 1, 2, 3
 K_PICARD, K_PREDICTOR, K_RIEMANN, K_CORRECTOR, K_STORAGE = 0, 1, 2, 3, 4
 FP64, FP32, BF16, FP16, FP8E4M3 = 0, 1, 2, 3, 4
 F_COMPENSATED_LAST, F_PER_CELL_SCALE, F_COMPENSATED_TWO = 1, 2, 4
+PRED_PICARD, PRED_CK = 0, 1
 SC_PLANAR, SC_EULER_WAVE, SC_SWE_MODES, SC_GAUSS_PULSE = 0, 1, 2, 3
 PREC_NAMES = {"fp64": FP64, "fp32": FP32, "bf16": BF16, "fp16": FP16, "fp8": FP8E4M3, "fp8e4m3": FP8E4M3}
 
@@ -41,6 +42,7 @@ _SIGS = {
     "adg_set_pde": [_P, C.c_int, _dp, C.c_int],
     "adg_set_kernel_precision": [_P, C.c_int, C.c_int, C.c_int],
     "adg_set_numerics": [_P, C.c_double, C.c_int],
+    "adg_set_predictor": [_P, C.c_int],
     "adg_workspace_bytes": [_P, C.POINTER(C.c_size_t)],
     "adg_state_size": [_P, C.POINTER(C.c_size_t), _ip],
     "adg_bind_buffers": [_P, _P, _P, C.c_size_t],
@@ -93,7 +95,7 @@ class Solver:
     """One ADER-DG context with torch-allocated state and workspace on the current device."""
 
     def __init__(self, dim, N, cells, pde, params, lo=None, hi=None, cfl=0.9, picard_iters=0,
-                 precision=None, flags=0, stream=None):
+                 precision=None, flags=0, stream=None, scheme=PRED_PICARD):
         import torch
 
         self._torch = torch
@@ -114,6 +116,9 @@ class Solver:
         pa, pp = _d(params)
         self._check(self.lib.adg_set_pde(self.ctx, pde, pp, len(pa)))
         self._check(self.lib.adg_set_numerics(self.ctx, cfl, picard_iters))
+        if isinstance(scheme, str):
+            scheme = {"picard": PRED_PICARD, "ck": PRED_CK}[scheme]
+        self._check(self.lib.adg_set_predictor(self.ctx, scheme))
         for k, p in (precision or {}).items():
             kk = {"picard": K_PICARD, "predictor": K_PREDICTOR, "riemann": K_RIEMANN,
                   "corrector": K_CORRECTOR, "storage": K_STORAGE}[k] if isinstance(k, str) else k

@@ -184,6 +184,7 @@ struct adg_ctx {
   int flags = 0;
   double cfl = 0.9;
   int picard_iters = 0;
+  int scheme = ADG_PRED_PICARD;
   double* Q = nullptr;
   void* ws = nullptr;
   size_t ws_bytes = 0;
@@ -401,6 +402,13 @@ int adg_set_numerics(adg_ctx* c, double cfl, int picard_iters) {
   return ADG_OK;
 }
 
+int adg_set_predictor(adg_ctx* c, int scheme) {
+  if (!c) return ADG_EINVAL;
+  if (scheme != ADG_PRED_PICARD && scheme != ADG_PRED_CK) return fail(c, ADG_EINVAL, "unknown predictor scheme");
+  c->scheme = scheme;
+  return ADG_OK;
+}
+
 int adg_state_size(const adg_ctx* c, size_t* ndouble, int* nvar) {
   if (!c) return ADG_EINVAL;
   if (!c->have_mesh || !c->have_pde) return ADG_ENOTINIT;
@@ -523,7 +531,13 @@ static int select_kernels(adg_ctx* c, StepFn* pred, StepFn* corr) {
   const int pic = c->prec[ADG_K_PICARD], prd = c->prec[ADG_K_PREDICTOR];
   const int rie = c->prec[ADG_K_RIEMANN], cor = c->prec[ADG_K_CORRECTOR];
   if (rie > PBF16 || cor > PBF16) return fail(c, ADG_EUNSUPPORTED, "precision mix not built");
-  if ((pic == PBF16 && prd == P32) || pic == PF16 || pic == PF8) {
+  if (c->scheme == ADG_PRED_CK) {
+    if (c->pde != ADG_ACOUSTIC && c->pde != ADG_ELASTIC)
+      return fail(c, ADG_EUNSUPPORTED, "the Cauchy-Kowalevskaya predictor needs a linear PDE");
+    if (pic != prd || pic > P32)
+      return fail(c, ADG_EUNSUPPORTED, "Cauchy-Kowalevskaya predictor: PICARD == PREDICTOR in {FP64, FP32}");
+    *pred = c->entry->predictor_ck[pic][cor];
+  } else if ((pic == PBF16 && prd == P32) || pic == PF16 || pic == PF8) {
     if (prd != P32) return fail(c, ADG_EUNSUPPORTED, "tensor-core Picard needs an FP32 predictor stage");
     if (cor > P32) return fail(c, ADG_EUNSUPPORTED, "tensor-core Picard writes FP32 or FP64 traces");
     *pred = c->entry->predictor_tc[pic == PF16 ? 1 : pic == PF8 ? 2 : 0][cor];
@@ -898,6 +912,8 @@ int adg_adjoint(adg_ctx* c, int nsteps, int nsnap, const double* xyz, int nrecv,
     return fail(c, ADG_EUNSUPPORTED, "the adjoint needs the FP64 Riemann/corrector");
   if (c->prec[ADG_K_PICARD] != c->prec[ADG_K_PREDICTOR] || c->prec[ADG_K_PICARD] > P32)
     return fail(c, ADG_EUNSUPPORTED, "the adjoint is built for the FP64 and FP32 predictors");
+  if (c->scheme != ADG_PRED_PICARD)
+    return fail(c, ADG_EUNSUPPORTED, "the adjoint transposes the Picard predictor");
   if (!observed || !d_grad_p0 || !d_grad_c) return fail(c, ADG_EINVAL, "null output/observation");
   AdjLayout L;
   int st = adj_setup(c, nsteps, nsnap, xyz, nrecv, d_workspace, ws_bytes, &L);

@@ -109,6 +109,8 @@ struct Entry {
   StepFn corrector[3][3];
   // tensor-core Picard with FP32 final stage: [0 = bf16, 1 = fp16, 2 = fp8 E4M3][trace prec]
   StepFn predictor_tc[3][3];
+  // Cauchy-Kowalevskaya predictor (linear PDEs): [P64 / P32 arithmetic][trace prec]
+  StepFn predictor_ck[2][3];
   // discrete adjoint (linear acoustics): face projections, per-cell adjoint [0 = FP64, 1 = FP32]
   void* adj_trace;
   void* adj_cell[2];

@@ -252,8 +252,12 @@ __device__ __forceinline__ void predictor_final(const StepArgs& a, const T (*q)[
 
 // ------------------------------------------------------------------------------------------------
 // predictor + volume integral + face traces
+// CK = false: Picard sweeps (Sec. 2.1, eq. Picard).  CK = true: Cauchy-Kowalevskaya for the
+// linear PDEs (Sec. 2.1, last paragraph): d_t^{m+1} Q = -sum_dir d_dir F_dir(d_t^m Q) for
+// m < N, q_k = sum_m (xi_k dt)^m / m! d_t^m Q at the time nodes; N derivative evaluations per
+// cell instead of about (N+1)^2 flux slices.  Both end in the same final stage.
 // ------------------------------------------------------------------------------------------------
-template <class C, class T, class TP, class TS>
+template <class C, class T, class TP, class TS, bool CK = false>
 __global__ void __launch_bounds__(C::THREADS) k_predictor(const __grid_constant__ StepArgs a) {
   using Ph = Phys<C::PDE, C::D>;
   constexpr int n = C::n, V = C::V, D = C::D, NS = C::NS, NF = C::NF, CPB = C::CPB;
@@ -274,7 +278,15 @@ __global__ void __launch_bounds__(C::THREADS) k_predictor(const __grid_constant_
   const T dtT = conv<T>(dt);
   for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
     const int r = t / n, cidx = t % n;
-    sdtP[t] = dtT * Tab<T>::P(a.tab, r, cidx);
+    if constexpr (CK) {
+      // Taylor factor of time derivative r at time node cidx: (xi dt)^r / r!, built up one
+      // factor (xi dt)/j at a time in FP64
+      double f = 1.0;
+      for (int j = 1; j <= r; ++j) f *= (a.tab.xi[cidx] * dt) / j;
+      sdtP[t] = conv<T>(f);
+    } else {
+      sdtP[t] = dtT * Tab<T>::P(a.tab, r, cidx);
+    }
     sVm[t] = Tab<TP>::Vm(a.tab, r, cidx);
   }
   for (int t = threadIdx.x; t < n; t += blockDim.x) {
@@ -330,9 +342,46 @@ __global__ void __launch_bounds__(C::THREADS) k_predictor(const __grid_constant_
 
   __syncthreads();
   int buf = 0;
+  if constexpr (CK) {
+    // d_t^m Q of this node, and q_k += (xi_k dt)^m / m! d_t^m Q for m = 1..N
+    T dq[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) dq[v] = Qh[v];
+#pragma unroll 1
+    for (int m = 1; m <= C::N; ++m) {
+      T* sF = sFbuf + buf * bufsz + (size_t)lc * D * V * PD;
+      {
+        T F[D][V];
+        Ph::flux(pp, dq, F);
+#pragma unroll
+        for (int dir = 0; dir < D; ++dir)
+#pragma unroll
+          for (int v = 0; v < V; ++v)
+            if (Ph::nz(dir, v)) sF[(dir * V + v) * PD + pb[dir] + idx[dir]] = F[dir][v];
+      }
+      __syncthreads();
+      const T* fac = sdtP + m * n;
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        T rv = T(0);
+#pragma unroll
+        for (int dir = 0; dir < D; ++dir) {
+          if (!Ph::nz(dir, v)) continue;
+          T f[S];
+          VecLoad<T, S>::load(sF + (dir * V + v) * PD + pb[dir], f);
+#pragma unroll
+          for (int mm = 0; mm < n; ++mm) rv += Dr[dir][mm] * f[mm];
+        }
+        dq[v] = -rv;
+#pragma unroll
+        for (int k = 0; k < n; ++k) q[k][v] += fac[k] * dq[v];
+      }
+      buf ^= 1;  // double buffering: one barrier per derivative
+    }
+  }
   // Sweep 1 starts from q = Q at every time node, so all time slices share one flux and one
   // derivative R: q^1[kk] = Q - dt (sum_l P[kk][l]) R.
-  if (a.picard_iters > 0) {
+  if (!CK && a.picard_iters > 0) {
     T* sF = sFbuf + (size_t)lc * D * V * PD;
     {
       T F[D][V];
@@ -360,7 +409,7 @@ __global__ void __launch_bounds__(C::THREADS) k_predictor(const __grid_constant_
     }
     buf = 1;
   }
-  for (int r = 1; r < a.picard_iters; ++r) {
+  for (int r = 1; !CK && r < a.picard_iters; ++r) {
     T qn[n][V];
 #pragma unroll
     for (int k = 0; k < n; ++k)
@@ -790,18 +839,18 @@ __global__ void k_l2_final(const double* partial, int nblocks, double* out) {
 // ------------------------------------------------------------------------------------------------
 // launchers
 // ------------------------------------------------------------------------------------------------
-template <class C, class T, class TP, class TS>
+template <class C, class T, class TP, class TS, bool CK = false>
 cudaError_t launch_predictor(const StepArgs& a, cudaStream_t s) {
   const size_t smem = PredSmem<C, T, TP>::total;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_predictor<C, T, TP, TS>,
+    cudaError_t e = cudaFuncSetAttribute(k_predictor<C, T, TP, TS, CK>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   const int blocks = (a.ncells + C::CPB - 1) / C::CPB;
-  k_predictor<C, T, TP, TS><<<blocks, C::THREADS, smem, s>>>(a);
+  k_predictor<C, T, TP, TS, CK><<<blocks, C::THREADS, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -890,6 +939,18 @@ Entry make_entry() {
   e.init = launch_init<C>;
   e.l2 = launch_l2<C>;
   return e;
+}
+
+// Add the Cauchy-Kowalevskaya predictors (linear PDEs; FP64 / FP32 arithmetic, FP64 / FP32
+// traces) to an Entry.
+template <int PDE, int D, int N>
+void add_ck(Entry& e) {
+  using C = Cfg<PDE, D, N>;
+  static_assert(PDE == 0 || PDE == 1, "the Cauchy-Kowalevskaya predictor needs a linear PDE");
+  e.predictor_ck[P64][P64] = launch_predictor<C, double, double, double, true>;
+  e.predictor_ck[P64][P32] = launch_predictor<C, double, double, float, true>;
+  e.predictor_ck[P32][P64] = launch_predictor<C, float, float, double, true>;
+  e.predictor_ck[P32][P32] = launch_predictor<C, float, float, float, true>;
 }
 
 }  // namespace adg

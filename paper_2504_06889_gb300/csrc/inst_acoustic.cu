@@ -15,19 +15,26 @@ static void add_adjoint(Entry& e) {
 void register_acoustic() {
   {
     Entry e = make_entry<0, 2, 3, false>();  // 2D, N = 3 (planar-wave workload)
+    add_ck<0, 2, 3>(e);
     add_adjoint<2, 3>(e);
     register_entry(e);
   }
   {
     Entry e = make_entry<0, 3, 4, false>();
     add_tc<0, 3, 4>(e);
+    add_ck<0, 3, 4>(e);
     add_adjoint<3, 4>(e);
     register_entry(e);
   }  // 3D, N = 4 (pulse / adjoint workload)
-  register_entry(make_entry<0, 2, 2, false>());
+  {
+    Entry e = make_entry<0, 2, 2, false>();
+    add_ck<0, 2, 2>(e);
+    register_entry(e);
+  }
   {
     Entry e = make_entry<0, 3, 2, false>();
     add_tc<0, 3, 2>(e);
+    add_ck<0, 3, 2>(e);
     add_adjoint<3, 2>(e);
     register_entry(e);
   }
