@@ -9,6 +9,8 @@ Every function follows arXiv 2504.06889:
   * Sec. 2.1, eq. (Picard): the space-time predictor system solved by Picard
     iteration; the Cauchy-Kowalevskaya alternative for linear PDEs;
   * Sec. 2.2, eq. (weak_form_volume_surface), (CFL_condition), (rusanov_flux);
+  * Sec. 3.1 and Algorithm 1: the "storage" precision of the persistent solution,
+    rounded to its format after each of the step's two grid traversals;
   * Sec. 4: the acoustic, elastic, Euler and shallow-water fluxes;
   * Sec. 4.5, eq. (L2gauss): the error norm.
 """
@@ -29,6 +31,7 @@ _lock = threading.Lock()
 _lib = None
 
 ACOUSTIC, ELASTIC, EULER, SWE = 0, 1, 2, 3
+STORAGE = {"fp64": 0, "fp32": 1, "bf16": 2, "fp16": 3}
 SC_PLANAR, SC_EULER_WAVE, SC_SWE_MODES, SC_GAUSS_PULSE = 0, 1, 2, 3
 
 
@@ -60,6 +63,10 @@ def _load():
             lib.or_destroy.argtypes = [P]
             lib.or_set_ck.argtypes = [P, C.c_int]
             lib.or_set_picard_iters.argtypes = [P, C.c_int]
+            lib.or_set_storage.argtypes = [P, C.c_int]
+            lib.or_round_format.argtypes = [C.c_double, C.c_int]
+            lib.or_round_format.restype = C.c_double
+            lib.or_round_array.argtypes = [dp, C.c_longlong, C.c_int]
             lib.or_set_cell_c.argtypes = [P, dp]
             lib.or_tables.argtypes = [C.c_int] + [dp] * 7
             lib.or_flux.argtypes = [P, C.c_int, dp, C.c_int, dp]
@@ -97,6 +104,13 @@ def _dp(a: np.ndarray):
 
 def nvar(pde: int, dim: int) -> int:
     return {ACOUSTIC: 1 + dim, ELASTIC: 9 if dim == 3 else 5, EULER: 2 + dim, SWE: 3}[pde]
+
+
+def round_format(x, fmt):
+    """x (array) rounded to a storage format of Table precision_bits: nearest, ties to even."""
+    a = np.array(x, dtype=np.float64, copy=True, order="C")
+    _load().or_round_array(_dp(a), a.size, STORAGE[fmt] if isinstance(fmt, str) else int(fmt))
+    return a
 
 
 def tables(n: int):
@@ -144,6 +158,11 @@ class Mesh:
 
     def set_picard_iters(self, iters: int):
         _load().or_set_picard_iters(self._h, int(iters))
+
+    def set_storage(self, fmt):
+        """Persistent solution format between the two traversals of a step (Sec. 3.1):
+        'fp64', 'fp32', 'bf16' or 'fp16'."""
+        _load().or_set_storage(self._h, STORAGE[fmt] if isinstance(fmt, str) else int(fmt))
 
     def set_cell_c(self, c):
         if c is None:

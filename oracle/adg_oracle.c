@@ -171,6 +171,7 @@ int or_setup(or_mesh* M, int dim, int N, const int* m, const double* lo, const d
   M->cfl = cfl;
   M->picard_iters = picard_iters > 0 ? picard_iters : N + 1;
   M->use_ck = 0;
+  M->storage = OR_ST_FP64;
   M->cell_c = NULL;
   /* or_tables stores n x n matrices with row stride n; the mesh keeps stride OR_MAXN */
   {
@@ -719,6 +720,43 @@ static const double* all_trace(const void* ctx, int cell, int dir, int side, int
   return base + (((size_t)cell * A->d + dir) * 2 + side) * A->V * A->NF;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Storage precision (Sec. 3.1): rounding to a binary format of Table         */
+/* precision_bits from the definition of its values.  A format with p         */
+/* significand bits (hidden bit included) and exponents emin..emax holds      */
+/* m 2^(e-p+1) with integer |m| < 2^p and e in [emin, emax]; below 2^emin the */
+/* spacing stays 2^(emin-p+1) (subnormals).  Round to nearest, ties to even.  */
+/* ------------------------------------------------------------------------ */
+
+double or_round_format(double x, int fmt) {
+  int p, emin, emax;
+  switch (fmt) {
+    case OR_ST_FP32: p = 24; emin = -126; emax = 127; break;
+    case OR_ST_BF16: p = 8; emin = -126; emax = 127; break;
+    case OR_ST_FP16: p = 11; emin = -14; emax = 15; break;
+    default: return x;
+  }
+  if (x == 0.0 || !isfinite(x)) return x;
+  int e2;
+  frexp(x, &e2);             /* |x| in [2^(e2-1), 2^e2) */
+  int lead = e2 - 1;         /* exponent of the leading bit */
+  if (lead < emin) lead = emin;
+  const int q = lead - (p - 1); /* exponent of the spacing of representable values */
+  const double s = ldexp(x, -q);  /* x in units of the spacing; exact (power-of-two scaling) */
+  const double r = nearbyint(s);  /* nearest integer, ties to even (default rounding mode) */
+  const double y = ldexp(r, q);
+  const double maxv = ldexp(2.0 - ldexp(1.0, 1 - p), emax);
+  if (fabs(y) > maxv) return x > 0 ? INFINITY : -INFINITY;
+  return y;
+}
+
+void or_round_array(double* x, long long count, int fmt) {
+  if (fmt == OR_ST_FP64) return;
+  for (long long i = 0; i < count; ++i) x[i] = or_round_format(x[i], fmt);
+}
+
+void or_set_storage(or_mesh* M, int fmt) { M->storage = fmt; }
+
 double or_step(const or_mesh* M, double* Q, double dt) {
   const int n = M->n, V = M->nvar, d = M->dim, NS = ipow(n, d), NF = ipow(n, d - 1),
             C = ncells(M);
@@ -737,9 +775,12 @@ double or_step(const or_mesh* M, double* Q, double dt) {
     }
     free(Qc);
   }
+  /* the solution is stored in the storage format between the two traversals */
+  or_round_array(Q, (long long)C * V * NS, M->storage);
   all_traces A = {TQ, TF, d, V, NF};
 #pragma omp parallel for schedule(static)
   for (int c = 0; c < C; ++c) correct_cell(M, c, dt, all_trace, &A, Q + (size_t)c * V * NS);
+  or_round_array(Q, (long long)C * V * NS, M->storage);
   free(TQ);
   free(TF);
   (void)n;
@@ -785,8 +826,10 @@ void or_step_cells(const or_mesh* M, const double* Q, double dt, int nsample, co
                    TF + (size_t)t * d * 2 * V * NF);
       if (t == 0) memcpy(out + (size_t)s * V * NS, Qv, sizeof(double) * (size_t)V * NS);
     }
+    or_round_array(out + (size_t)s * V * NS, (long long)V * NS, M->storage);
     local_traces L = {d, V, NF, nloc, ids, TQ, TF};
     correct_cell(M, cells[s], dt, local_trace, &L, out + (size_t)s * V * NS);
+    or_round_array(out + (size_t)s * V * NS, (long long)V * NS, M->storage);
     free(TQ);
     free(TF);
     free(Qv);

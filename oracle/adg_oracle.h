@@ -33,6 +33,9 @@ extern "C" {
 #define OR_MAXV 9
 
 enum { OR_ACOUSTIC = 0, OR_ELASTIC = 1, OR_EULER = 2, OR_SWE = 3 };
+/* storage formats of Table precision_bits: significand bits p (with the hidden bit),
+ * smallest normal exponent, largest exponent */
+enum { OR_ST_FP64 = 0, OR_ST_FP32 = 1, OR_ST_BF16 = 2, OR_ST_FP16 = 3 };
 enum { OR_SC_PLANAR = 0, OR_SC_EULER_WAVE = 1, OR_SC_SWE_MODES = 2, OR_SC_GAUSS_PULSE = 3 };
 
 typedef struct {
@@ -43,6 +46,7 @@ typedef struct {
   double cfl;         /* C_CFL of eq. (CFL_condition) */
   int picard_iters;   /* fixed number of Picard sweeps */
   int use_ck;         /* 1: Cauchy-Kowalevskaya predictor instead of Picard (linear PDEs) */
+  int storage;        /* persistent-solution format (Sec. 3.1 "storage"): OR_ST_* */
   const double* cell_c; /* optional per-cell wave speed for acoustics (rho fixed); NULL = none */
   /* 1D tables on [0,1] */
   double xi[OR_MAXN], w[OR_MAXN];
@@ -107,6 +111,14 @@ or_mesh* or_create(int dim, int N, const int* m, const double* lo, const double*
 void or_destroy(or_mesh* M);
 void or_set_ck(or_mesh* M, int use_ck);
 void or_set_picard_iters(or_mesh* M, int iters);
+/* Persistent solution stored in format fmt (OR_ST_*) between the two grid traversals of a
+ * step (Sec. 3.1, Algorithm 1): the step rounds Q after the predictor/volume pass and after
+ * the corrector pass. */
+void or_set_storage(or_mesh* M, int fmt);
+/* x rounded to format fmt: nearest value, ties to even, overflow to +-inf. */
+double or_round_format(double x, int fmt);
+/* Round count values in place to format fmt. */
+void or_round_array(double* x, long long count, int fmt);
 
 #ifdef __cplusplus
 }
