@@ -61,6 +61,11 @@ MIXES = {
 MIXES["fp64ck"] = dict(MIXES["fp64"])
 MIXES["fp32ck"] = dict(MIXES["fp32"])
 MIX_SCHEME = {"fp64ck": "ck", "fp32ck": "ck"}
+# persistent solution stored below FP64 (rounded after each of the step's two traversals),
+# all kernels FP64 or all FP32
+for _k in ("fp64", "fp32"):
+    for _s, _n in (("fp32", "32"), ("fp16", "16"), ("bf16", "bf16")):
+        MIXES[f"{_k}s{_n}"] = dict(MIXES[_k], storage=_s)
 MIX_FLAGS = {"bf16tc": 1 | 2, "fp16tc": 1 | 2, "fp8tc": 1 | 2}
 
 # default mixes per workload (the tensor-core predictor is built for the 3D meshes)
@@ -84,7 +89,9 @@ def sweep_mixes():
                                                     "corrector": c}
     return out
 DTYPE = {"fp64": "f64", "fp32pred": "f32+f64", "fp32": "f32+f64", "bf16tc": "bf16+f32+f64",
-         "fp16tc": "f16+f32+f64", "fp8tc": "e4m3+f32+f64", "fp64ck": "f64", "fp32ck": "f32+f64"}
+         "fp16tc": "f16+f32+f64", "fp8tc": "e4m3+f32+f64", "fp64ck": "f64", "fp32ck": "f32+f64",
+         "fp64s32": "f64", "fp64s16": "f64", "fp64sbf16": "f64",
+         "fp32s32": "f32+f64", "fp32s16": "f32+f64", "fp32sbf16": "f32+f64"}
 
 
 def predictor_flops_per_cell(pde, dim, N, iters=None, scheme="picard"):
@@ -110,12 +117,13 @@ def predictor_flops_per_cell(pde, dim, N, iters=None, scheme="picard"):
     return (first + (it - 1) * sweep if it > 0 else 0) + final + vol + traces
 
 
-def predictor_bytes_per_cell(pde, dim, N, trace_bytes):
-    """Algorithmic HBM bytes of the predictor for one cell: read and write the FP64 state,
-    write the face traces (Qbar and Fbar.n, both sides of every direction)."""
+def predictor_bytes_per_cell(pde, dim, N, trace_bytes, state_bytes=8):
+    """Algorithmic HBM bytes of the predictor for one cell: read and write the state (FP64, or
+    the storage format), write the face traces (Qbar and Fbar.n, both sides of every
+    direction)."""
     n = N + 1
     V = I.nvar(pde, dim)
-    return 16 * n ** dim * V + 2 * dim * 2 * V * n ** (dim - 1) * trace_bytes
+    return 2 * state_bytes * n ** dim * V + 2 * dim * 2 * V * n ** (dim - 1) * trace_bytes
 
 
 def load_peaks():
@@ -393,7 +401,8 @@ def main():
                          "frac": ach / pk, "traffic": None,
                          "kernel": "k_predictor", "peak_source": f"{kind} ALU derived at {sm_mhz:.0f} MHz"}
         tb = {"fp64": 8, "fp32": 4, "bf16": 2}[prec["corrector"]]
-        bts = predictor_bytes_per_cell(wl.pde, wl.dim, wl.N, tb) * cells
+        sb = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}[prec.get("storage", "fp64")]
+        bts = predictor_bytes_per_cell(wl.pde, wl.dim, wl.N, tb, sb) * cells
         r["predictor_gbs"] = bts / (ms_pred / args.steps * 1e-3) / 1e9
         results[mix] = r
         if mix == headline and not args.no_e2e:

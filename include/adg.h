@@ -125,9 +125,20 @@ ADG_API int adg_set_pde(adg_ctx* c, int pde, const double* params, int nparams);
  *   PREDICTOR  FP64, FP32, BF16 (see PICARD)
  *   RIEMANN    FP64, FP32, BF16 (bf16 built for shallow water)
  *   CORRECTOR  FP64, FP32, BF16 (bf16 built for shallow water)
- *   STORAGE    FP64
+ *   STORAGE    FP64; FP32, BF16, FP16 (the persistent solution, Sec. 3.1 "storage") with all
+ *              four other kernels FP64 or all four FP32, the Picard predictor, and the orders
+ *              of the workloads (acoustic 2D N=3, 3D N=4; elastic 3D N=2, 6; Euler 3D N=2, 5;
+ *              shallow water N=2, 4).  The stored solution is rounded (to nearest, ties to
+ *              even) after each of the two grid traversals of a step (Algorithm 1): after the
+ *              predictor's volume update and after the corrector's surface update; dt follows
+ *              the stored values.  The context keeps it in its workspace.  The caller's FP64
+ *              state buffer holds the same values widened: every state-setting call and every
+ *              step call first rounds the FP64 buffer into the storage format (writing the
+ *              rounded values back), and every step call ends by widening the stored state
+ *              into it.  adg_misfit and adg_adjoint need FP64 storage.
  * Others return ADG_EUNSUPPORTED (at the call, or at the first step for mixes that depend on
- * the mesh and PDE). */
+ * the mesh and PDE).  Changing CORRECTOR or STORAGE changes the workspace size: bind the
+ * buffers again. */
 ADG_API int adg_set_kernel_precision(adg_ctx* c, int kernel, int prec, int flags);
 
 /* C_CFL of eq. (CFL_condition) (dt = cfl h / (d (2N+1) lambda_max)) and the

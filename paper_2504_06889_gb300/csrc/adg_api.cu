@@ -12,6 +12,7 @@
 #include "../../include/adg.h"
 #include "adg_adjoint.cuh"
 #include "adg_internal.h"
+#include "adg_kernels.cuh"
 
 namespace adg {
 
@@ -21,11 +22,18 @@ static std::vector<Entry>& registry() {
   return r;
 }
 void register_entry(const Entry& e) { registry().push_back(e); }
+static std::vector<StorageEntry>& storage_registry() {
+  static std::vector<StorageEntry> r;
+  return r;
+}
+void register_storage(const StorageEntry& e) { storage_registry().push_back(e); }
 
 void register_acoustic();
 void register_euler();
 void register_elastic();
 void register_swe();
+void register_storage_linear();
+void register_storage_nonlinear();
 
 static void ensure_registry() {
   static std::once_flag once;
@@ -34,7 +42,32 @@ static void ensure_registry() {
     register_euler();
     register_elastic();
     register_swe();
+    register_storage_linear();
+    register_storage_nonlinear();
   });
+}
+
+const StorageEntry* find_storage(int pde, int dim, int N) {
+  ensure_registry();
+  for (const StorageEntry& e : storage_registry())
+    if (e.pde == pde && e.dim == dim && e.N == N) return &e;
+  return nullptr;
+}
+
+// ---- the persistent solution below FP64: round the FP64 state into the storage format (and
+// back, so that the FP64 copy holds exactly the stored values), or widen the stored state -----
+template <class TQ>
+__global__ void k_store_in(double* Q, TQ* Qs, size_t count) {
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < count; k += (size_t)gridDim.x * blockDim.x) {
+    const TQ r = store_round<TQ>(Q[k]);
+    Qs[k] = r;
+    Q[k] = store_widen(r);
+  }
+}
+template <class TQ>
+__global__ void k_store_out(const TQ* Qs, double* Q, size_t count) {
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < count; k += (size_t)gridDim.x * blockDim.x)
+    Q[k] = store_widen(Qs[k]);
 }
 
 const Entry* find_entry(int pde, int dim, int N) {
@@ -225,9 +258,41 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 static size_t l2_partial_bytes(const adg_ctx* c) { return (size_t)152 * 4 * c->V * sizeof(double); }
 
+// the state in the storage format, when that is not FP64 (after traces and L2 partials)
+static size_t storage_elem_bytes(int p) { return p == P64 ? 0 : p == P32 ? 4 : 2; }
+static size_t storage_bytes(const adg_ctx* c) {
+  return (size_t)c->ncells * c->V * c->NS * storage_elem_bytes(c->prec[ADG_K_STORAGE]);
+}
+static void* storage_ptr(const adg_ctx* c) {
+  if (c->prec[ADG_K_STORAGE] == P64 || !c->ws) return nullptr;
+  return (char*)c->ws + align256(traces_bytes(c)) + align256(l2_partial_bytes(c));
+}
+
+// FP64 state -> storage format (and the FP64 copy rounded), or storage -> FP64 copy
+static cudaError_t storage_sync(const adg_ctx* c, bool in) {
+  const int sp = c->prec[ADG_K_STORAGE];
+  if (sp == P64) return cudaSuccess;
+  const size_t count = (size_t)c->ncells * c->V * c->NS;
+  int blocks = (int)std::min<size_t>((count + 255) / 256, (size_t)152 * 8);
+  if (blocks < 1) blocks = 1;
+  void* qs = storage_ptr(c);
+  if (sp == P32) {
+    if (in) k_store_in<float><<<blocks, 256, 0, c->stream>>>(c->Q, (float*)qs, count);
+    else k_store_out<float><<<blocks, 256, 0, c->stream>>>((const float*)qs, c->Q, count);
+  } else if (sp == PBF16) {
+    if (in) k_store_in<__nv_bfloat16><<<blocks, 256, 0, c->stream>>>(c->Q, (__nv_bfloat16*)qs, count);
+    else k_store_out<__nv_bfloat16><<<blocks, 256, 0, c->stream>>>((const __nv_bfloat16*)qs, c->Q, count);
+  } else {
+    if (in) k_store_in<__half><<<blocks, 256, 0, c->stream>>>(c->Q, (__half*)qs, count);
+    else k_store_out<__half><<<blocks, 256, 0, c->stream>>>((const __half*)qs, c->Q, count);
+  }
+  return cudaGetLastError();
+}
+
 static void fill_step_args(const adg_ctx* c, StepArgs* a) {
   std::memset(a, 0, sizeof(*a));
   a->Q = c->Q;
+  a->Qs = storage_ptr(c);
   a->traces = c->ws;
   a->sc = c->sc;
   for (int d = 0; d < 3; ++d) {
@@ -379,15 +444,16 @@ int adg_set_kernel_precision(adg_ctx* c, int kernel, int prec, int flags) {
   if (!c) return ADG_EINVAL;
   if (kernel < 0 || kernel > ADG_K_STORAGE) return fail(c, ADG_EINVAL, "unknown kernel");
   if (prec < 0 || prec > ADG_FP8E4M3) return fail(c, ADG_EINVAL, "unknown precision");
-  if (kernel == ADG_K_STORAGE && prec != ADG_FP64)
-    return fail(c, ADG_EUNSUPPORTED, "storage precision other than FP64 is not built");
+  if (kernel == ADG_K_STORAGE && prec == ADG_FP8E4M3)
+    return fail(c, ADG_EUNSUPPORTED, "storage is built in FP64, FP32, bf16 and fp16");
   if (prec == ADG_FP8E4M3 && kernel != ADG_K_PICARD)
     return fail(c, ADG_EUNSUPPORTED, "fp8 is built for the Picard contractions only");
   if (kernel == ADG_K_PREDICTOR && prec == ADG_FP16)
     return fail(c, ADG_EUNSUPPORTED, "the predictor's final stage runs in FP64, FP32 or bf16");
   if ((kernel == ADG_K_RIEMANN || kernel == ADG_K_CORRECTOR) && prec == ADG_FP16)
     return fail(c, ADG_EUNSUPPORTED, "fp16 Riemann/corrector not built");
-  if (kernel == ADG_K_CORRECTOR && prec != c->prec[ADG_K_CORRECTOR]) c->have_bufs = false;
+  if ((kernel == ADG_K_CORRECTOR || kernel == ADG_K_STORAGE) && prec != c->prec[kernel])
+    c->have_bufs = false;  // the workspace size changes
   c->prec[kernel] = prec;
   if (kernel == ADG_K_PICARD) c->flags = flags;
   return ADG_OK;
@@ -420,7 +486,7 @@ int adg_state_size(const adg_ctx* c, size_t* ndouble, int* nvar) {
 int adg_workspace_bytes(const adg_ctx* c, size_t* bytes) {
   if (!c || !bytes) return ADG_EINVAL;
   if (!c->have_mesh || !c->have_pde) return ADG_ENOTINIT;
-  *bytes = align256(traces_bytes(c)) + align256(l2_partial_bytes(c));
+  *bytes = align256(traces_bytes(c)) + align256(l2_partial_bytes(c)) + align256(storage_bytes(c));
   return ADG_OK;
 }
 
@@ -444,6 +510,7 @@ static int reset_scalars_and_lambda(adg_ctx* c, double t) {
   DevScalars s{};
   s.t = t;
   ADG_CUDA(c, cudaMemcpyAsync(c->sc, &s, sizeof(s), cudaMemcpyHostToDevice, c->stream));
+  ADG_CUDA(c, storage_sync(c, true));  // the state is stored (and its dt taken) in that format
   StepArgs a;
   fill_step_args(c, &a);
   ADG_CUDA(c, c->entry->lambda(a, c->stream));
@@ -531,6 +598,19 @@ static int select_kernels(adg_ctx* c, StepFn* pred, StepFn* corr) {
   const int pic = c->prec[ADG_K_PICARD], prd = c->prec[ADG_K_PREDICTOR];
   const int rie = c->prec[ADG_K_RIEMANN], cor = c->prec[ADG_K_CORRECTOR];
   if (rie > PBF16 || cor > PBF16) return fail(c, ADG_EUNSUPPORTED, "precision mix not built");
+  const int stp = c->prec[ADG_K_STORAGE];
+  if (stp != P64) {
+    const StorageEntry* se = find_storage(c->pde, c->dim, c->N);
+    if (!se) return fail(c, ADG_EUNSUPPORTED, "storage below FP64 is not built for this (PDE, d, N)");
+    if (c->scheme != ADG_PRED_PICARD) return fail(c, ADG_EUNSUPPORTED, "storage below FP64 runs the Picard predictor");
+    if (!(pic == prd && prd == rie && rie == cor && pic <= P32))
+      return fail(c, ADG_EUNSUPPORTED, "storage below FP64: all kernels FP64 or all kernels FP32");
+    const int si = stp == P32 ? 0 : stp == PBF16 ? 1 : 2;
+    *pred = se->predictor[si][pic];
+    *corr = se->corrector[si][pic];
+    if (!*pred || !*corr) return fail(c, ADG_EUNSUPPORTED, "storage mix not built");
+    return ADG_OK;
+  }
   if (c->scheme == ADG_PRED_CK) {
     if (c->pde != ADG_ACOUSTIC && c->pde != ADG_ELASTIC)
       return fail(c, ADG_EUNSUPPORTED, "the Cauchy-Kowalevskaya predictor needs a linear PDE");
@@ -565,10 +645,12 @@ int adg_step_async(adg_ctx* c, int nsteps) {
   if (st != ADG_OK) return st;
   StepArgs a;
   fill_step_args(c, &a);
+  ADG_CUDA(c, storage_sync(c, true));
   for (int s = 0; s < nsteps; ++s) {
     ADG_CUDA(c, pred(a, c->stream));
     ADG_CUDA(c, corr(a, c->stream));
   }
+  ADG_CUDA(c, storage_sync(c, false));
   return ADG_OK;
 }
 
@@ -589,6 +671,9 @@ int adg_step_timed(adg_ctx* c, int nsteps, double* t_out, double* ms_kernels) {
   if (!c) return ADG_EINVAL;
   if (!c->have_state) return fail(c, ADG_ENOTINIT, "set an initial state first");
   if (nsteps < 1) return fail(c, ADG_EINVAL, "nsteps < 1");
+  size_t need = 0;
+  adg_workspace_bytes(c, &need);
+  if (c->ws_bytes < need) return fail(c, ADG_ENOMEM, "workspace too small for this precision");
   StepFn pred = nullptr, corr = nullptr;
   int st = select_kernels(c, &pred, &corr);
   if (st != ADG_OK) return st;
@@ -604,13 +689,15 @@ int adg_step_timed(adg_ctx* c, int nsteps, double* t_out, double* ms_kernels) {
     }
   }
   int rc = ADG_OK;
-  cudaError_t ce = cudaEventRecord(ev[0], c->stream);
+  cudaError_t ce = storage_sync(c, true);
+  if (ce == cudaSuccess) ce = cudaEventRecord(ev[0], c->stream);
   for (int s = 0; s < nsteps && ce == cudaSuccess; ++s) {
     ce = pred(a, c->stream);
     if (ce == cudaSuccess) ce = cudaEventRecord(ev[2 * s + 1], c->stream);
     if (ce == cudaSuccess) ce = corr(a, c->stream);
     if (ce == cudaSuccess) ce = cudaEventRecord(ev[2 * s + 2], c->stream);
   }
+  if (ce == cudaSuccess) ce = storage_sync(c, false);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
   double sp = 0.0, sc = 0.0;
   for (int s = 0; s < nsteps && ce == cudaSuccess; ++s) {
@@ -877,6 +964,7 @@ static int forward_steps(adg_ctx* c, int nsteps, char* b, const AdjLayout& L, in
 int adg_misfit(adg_ctx* c, int nsteps, const double* xyz, int nrecv, const double* observed, double* J_out,
                double* record, void* d_workspace, size_t ws_bytes) {
   if (!c) return ADG_EINVAL;
+  if (c->prec[ADG_K_STORAGE] != P64) return fail(c, ADG_EUNSUPPORTED, "the misfit needs FP64 storage");
   AdjLayout L;
   int st = adj_setup(c, nsteps, 0, xyz, nrecv, d_workspace, ws_bytes, &L);
   if (st != ADG_OK) return st;
@@ -914,6 +1002,7 @@ int adg_adjoint(adg_ctx* c, int nsteps, int nsnap, const double* xyz, int nrecv,
     return fail(c, ADG_EUNSUPPORTED, "the adjoint is built for the FP64 and FP32 predictors");
   if (c->scheme != ADG_PRED_PICARD)
     return fail(c, ADG_EUNSUPPORTED, "the adjoint transposes the Picard predictor");
+  if (c->prec[ADG_K_STORAGE] != P64) return fail(c, ADG_EUNSUPPORTED, "the adjoint needs FP64 storage");
   if (!observed || !d_grad_p0 || !d_grad_c) return fail(c, ADG_EINVAL, "null output/observation");
   AdjLayout L;
   int st = adj_setup(c, nsteps, nsnap, xyz, nrecv, d_workspace, ws_bytes, &L);

@@ -51,6 +51,7 @@ struct DevScalars {
 
 struct StepArgs {
   double* Q;          // state [cells][V][NS]
+  void* Qs;           // the state in the storage precision when it is not FP64 (else null)
   void* traces;       // [cells][D][2 sides][2 (Qbar, Fbar.n)][V][NF] in the corrector precision
   DevScalars* sc;
   int m[3];
@@ -120,7 +121,17 @@ struct Entry {
   int l2_blocks_per_cell_group;  // cells per block of the L2 kernel
 };
 
+// Kernels with the persistent solution stored below FP64 (Sec. 3.1 "storage") for one
+// (PDE, d, N): [storage FP32 / BF16 / FP16][all kernels FP64 / all kernels FP32]
+struct StorageEntry {
+  int pde, dim, N;
+  StepFn predictor[3][2];
+  StepFn corrector[3][2];
+};
+
 void register_entry(const Entry& e);
+void register_storage(const StorageEntry& e);
+const StorageEntry* find_storage(int pde, int dim, int N);
 bool build_tables(int n, Tables* T);
 const Entry* find_entry(int pde, int dim, int N);
 

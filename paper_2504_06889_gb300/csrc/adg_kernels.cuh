@@ -17,6 +17,8 @@
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "adg_internal.h"
 #include "adg_physics.cuh"
 
@@ -138,6 +140,33 @@ template <int S> struct VecLoad<__nv_bfloat16, S> {
   }
 };
 
+// ---- storage precision of the persistent solution (Sec. 3.1 "storage") ----------------------
+// FP64 -> storage format, round to nearest with ties to even.  bf16 and fp16 go through FP32
+// rounded to odd (truncate, then set the last bit if anything was cut off): with at least two
+// more bits than the target, rounding to odd and then to nearest even equals direct rounding
+// to nearest even (S. Boldo, G. Melquiond, "Emulation of FMA and correctly rounded sums:
+// proved algorithms using rounding to odd", IEEE Trans. Computers 57(4), 2008).
+__device__ __forceinline__ float round_to_odd_f32(double x) {
+  float f = __double2float_rz(x);
+  if ((double)f != x && isfinite(x)) f = __uint_as_float(__float_as_uint(f) | 1u);
+  return f;
+}
+template <class TQ> __device__ __forceinline__ TQ store_round(double x);
+template <> __device__ __forceinline__ float store_round<float>(double x) { return __double2float_rn(x); }
+template <> __device__ __forceinline__ __nv_bfloat16 store_round<__nv_bfloat16>(double x) {
+  return __float2bfloat16_rn(round_to_odd_f32(x));
+}
+template <> __device__ __forceinline__ __half store_round<__half>(double x) {
+  return __float2half_rn(round_to_odd_f32(x));
+}
+__device__ __forceinline__ double store_widen(float x) { return (double)x; }
+__device__ __forceinline__ double store_widen(__nv_bfloat16 x) { return (double)__bfloat162float(x); }
+__device__ __forceinline__ double store_widen(__half x) { return (double)__half2float(x); }
+__device__ __forceinline__ double store_widen(double x) { return x; }
+__device__ __forceinline__ float store_to_float(float x) { return x; }
+__device__ __forceinline__ float store_to_float(__nv_bfloat16 x) { return __bfloat162float(x); }
+__device__ __forceinline__ float store_to_float(__half x) { return __half2float(x); }
+
 template <class C, class T, class TP> struct PredSmem {
   // two flux-slice buffers (double buffering) during the sweeps
   static constexpr size_t sweep = sizeof(T) * 2 * C::CPB * C::D * C::V * Pencil<C>::PER_DIR;
@@ -152,7 +181,7 @@ template <class C, class T, class TP> struct PredSmem {
 // last iterate, time averages Qbar = sum_k w_k q_k and Fbar = sum_k w_k F(q_k), the volume
 // integral added to Q in FP64 and the face traces of Qbar and Fbar.n written in TS.
 // smem_fin: CPB * (D V PD + V NS) values of TP; must not alias the tables.
-template <class C, class T, class TP, class TS>
+template <class C, class T, class TP, class TS, class TQ = double>
 __device__ __forceinline__ void predictor_final(const StepArgs& a, const T (*q)[C::V], TP* smem_fin,
                                                 const TP* sVm, const TP* sw, const TP* sp0, const TP* sp1,
                                                 double dt, int lc, int i, int cell, bool valid, int cl,
@@ -199,6 +228,8 @@ __device__ __forceinline__ void predictor_final(const StepArgs& a, const T (*q)[
   __syncthreads();
 
   // ---- volume integral: Q_i += dt sum_dir (1/h_dir) sum_m Vm[i_dir][m] Fbar(i[dir<-m]) --------
+  // (in FP64; with a storage format below FP64 the sum is rounded to it: the solution is
+  // stored between the two traversals of the step)
   if (valid && owner) {
     const TP ihp[3] = {conv<TP>(a.invh[0]), conv<TP>(a.invh[1]), conv<TP>(a.invh[2])};
     double* Qw = a.Q + (size_t)cell * V * NS;
@@ -215,7 +246,12 @@ __device__ __forceinline__ void predictor_final(const StepArgs& a, const T (*q)[
         for (int m = 0; m < n; ++m) s += Vr[m] * Fp[m];
         vol += s * ihp[dir];
       }
-      Qw[v * NS + i] += dt * conv<double>(vol);
+      if constexpr (std::is_same<TQ, double>::value) {
+        Qw[v * NS + i] += dt * conv<double>(vol);
+      } else {
+        TQ* Qsw = static_cast<TQ*>(a.Qs) + (size_t)cell * V * NS;
+        Qsw[v * NS + i] = store_round<TQ>(store_widen(Qsw[v * NS + i]) + dt * conv<double>(vol));
+      }
     }
   }
 
@@ -257,7 +293,7 @@ __device__ __forceinline__ void predictor_final(const StepArgs& a, const T (*q)[
 // m < N, q_k = sum_m (xi_k dt)^m / m! d_t^m Q at the time nodes; N derivative evaluations per
 // cell instead of about (N+1)^2 flux slices.  Both end in the same final stage.
 // ------------------------------------------------------------------------------------------------
-template <class C, class T, class TP, class TS, bool CK = false>
+template <class C, class T, class TP, class TS, bool CK = false, class TQ = double>
 __global__ void __launch_bounds__(C::THREADS) k_predictor(const __grid_constant__ StepArgs a) {
   using Ph = Phys<C::PDE, C::D>;
   constexpr int n = C::n, V = C::V, D = C::D, NS = C::NS, NF = C::NF, CPB = C::CPB;
@@ -324,9 +360,20 @@ __global__ void __launch_bounds__(C::THREADS) k_predictor(const __grid_constant_
   const PP<T> pp = make_pp<T>(a.pp, cl);
 
   T Qh[V];
-  const double* Qc = a.Q + (size_t)cl * V * NS;
+  if constexpr (std::is_same<TQ, double>::value) {
+    const double* Qc = a.Q + (size_t)cl * V * NS;
 #pragma unroll
-  for (int v = 0; v < V; ++v) Qh[v] = conv<T>(Qc[v * NS + i]);
+    for (int v = 0; v < V; ++v) Qh[v] = conv<T>(Qc[v * NS + i]);
+  } else {
+    const TQ* Qc = static_cast<const TQ*>(a.Qs) + (size_t)cl * V * NS;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      if constexpr (std::is_same<T, float>::value)
+        Qh[v] = store_to_float(Qc[v * NS + i]);  // exact
+      else
+        Qh[v] = conv<T>(store_widen(Qc[v * NS + i]));
+    }
+  }
 
   T* sFbuf = reinterpret_cast<T*>(smem_raw);
   constexpr size_t bufsz = (size_t)CPB * D * V * PD;
@@ -452,8 +499,8 @@ __global__ void __launch_bounds__(C::THREADS) k_predictor(const __grid_constant_
   }
   __syncthreads();
 
-  predictor_final<C, T, TP, TS>(a, q, reinterpret_cast<TP*>(smem_raw), sVm, sw, sp0, sp1, dt, lc, i, cell,
-                                valid, cl, idx, pb);
+  predictor_final<C, T, TP, TS, TQ>(a, q, reinterpret_cast<TP*>(smem_raw), sVm, sw, sp0, sp1, dt, lc, i,
+                                    cell, valid, cl, idx, pb);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -469,7 +516,7 @@ template <class C, class TR, class TC> struct CorrSmem {
   static constexpr size_t total = tr + g + sp + coef + 64;
 };
 
-template <class C, class TR, class TC, class TS>
+template <class C, class TR, class TC, class TS, class TQ = double>
 __global__ void __launch_bounds__(C::THREADS) k_corrector(const __grid_constant__ StepArgs a) {
   using Ph = Phys<C::PDE, C::D>;
   constexpr int n = C::n, V = C::V, D = C::D, NS = C::NS, NF = C::NF, CPB = C::CPB;
@@ -576,6 +623,7 @@ __global__ void __launch_bounds__(C::THREADS) k_corrector(const __grid_constant_
   float lam32 = 0.0f;
   bool bad = false, risky = false;
   double qnew_keep[V];
+  TQ qs_keep[V];
   if (valid) {
     const int idx[3] = {i % n, (i / n) % n, i / (n * n)};
     int jf[3];
@@ -588,7 +636,7 @@ __global__ void __launch_bounds__(C::THREADS) k_corrector(const __grid_constant_
       jf[2] = idx[0] + n * idx[1];
     }
     double* Qw = a.Q + (size_t)cell * V * NS;
-    double qnew[V];
+    float qf[V];  // FP32 copy of the new state for the lambda estimate
 #pragma unroll
     for (int v = 0; v < V; ++v) {
       TC surf = tcast<TC>(0.0);
@@ -599,17 +647,25 @@ __global__ void __launch_bounds__(C::THREADS) k_corrector(const __grid_constant_
         const TC gm = sG[((2 * dir + 0) * V + v) * NF + jf[dir]];
         surf += sCoef[(D + dir) * n + id] * gp - sCoef[dir * n + id] * gm;
       }
-      const double qv = Qw[v * NS + i] - dt * todouble(surf);
-      Qw[v * NS + i] = qv;
-      qnew[v] = qv;
-      qnew_keep[v] = qv;
-      bad |= !isfinite(qv);
+      if constexpr (std::is_same<TQ, double>::value) {
+        const double qv = Qw[v * NS + i] - dt * todouble(surf);
+        Qw[v * NS + i] = qv;
+        qnew_keep[v] = qv;
+        qf[v] = (float)qv;
+        bad |= !isfinite(qv);
+      } else {
+        // stored in the storage format; the next dt follows the stored values (their FP32
+        // copy is exact, the FP64 one is made only for the lambda candidates below)
+        TQ* Qsw = static_cast<TQ*>(a.Qs) + (size_t)cell * V * NS;
+        const TQ r = store_round<TQ>(store_widen(Qsw[v * NS + i]) - dt * todouble(surf));
+        Qsw[v * NS + i] = r;
+        qs_keep[v] = r;
+        qf[v] = store_to_float(r);
+        bad |= !isfinite(qf[v]);
+      }
     }
     // FP32 estimate of this node's spectral radius; the exact FP64 value is computed below
     // only for nodes that can hold the block maximum
-    float qf[V];
-#pragma unroll
-    for (int v = 0; v < V; ++v) qf[v] = (float)qnew[v];
     const float l32 = Ph::maxspeed(make_pp<float>(a.pp, cell), qf);
     risky = !(l32 < 3.0e38f) || Ph::speed_is_ill_conditioned(qf);
     if (!risky) atomicMax(&s_l32, __float_as_uint(l32));
@@ -621,6 +677,10 @@ __global__ void __launch_bounds__(C::THREADS) k_corrector(const __grid_constant_
   // far below 1e-4 for well-conditioned states, so the FP64 maximum is among the candidates.
   if (valid && !bad && (risky || lam32 >= __uint_as_float(s_l32) * (1.0f - 1.0e-4f))) {
     const PP<double> pd = make_pp<double>(a.pp, cell);
+    if constexpr (!std::is_same<TQ, double>::value) {
+#pragma unroll
+      for (int v = 0; v < V; ++v) qnew_keep[v] = store_widen(qs_keep[v]);
+    }
     lam = Ph::maxspeed(pd, qnew_keep);
     bad |= !isfinite(lam);
   }
@@ -839,33 +899,33 @@ __global__ void k_l2_final(const double* partial, int nblocks, double* out) {
 // ------------------------------------------------------------------------------------------------
 // launchers
 // ------------------------------------------------------------------------------------------------
-template <class C, class T, class TP, class TS, bool CK = false>
+template <class C, class T, class TP, class TS, bool CK = false, class TQ = double>
 cudaError_t launch_predictor(const StepArgs& a, cudaStream_t s) {
   const size_t smem = PredSmem<C, T, TP>::total;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_predictor<C, T, TP, TS, CK>,
+    cudaError_t e = cudaFuncSetAttribute(k_predictor<C, T, TP, TS, CK, TQ>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   const int blocks = (a.ncells + C::CPB - 1) / C::CPB;
-  k_predictor<C, T, TP, TS, CK><<<blocks, C::THREADS, smem, s>>>(a);
+  k_predictor<C, T, TP, TS, CK, TQ><<<blocks, C::THREADS, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <class C, class TR, class TC, class TS>
+template <class C, class TR, class TC, class TS, class TQ = double>
 cudaError_t launch_corrector(const StepArgs& a, cudaStream_t s) {
   const size_t smem = CorrSmem<C, TR, TC>::total;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_corrector<C, TR, TC, TS>,
+    cudaError_t e = cudaFuncSetAttribute(k_corrector<C, TR, TC, TS, TQ>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   const int blocks = (a.ncells + C::CPB - 1) / C::CPB;
-  k_corrector<C, TR, TC, TS><<<blocks, C::THREADS, smem, s>>>(a);
+  k_corrector<C, TR, TC, TS, TQ><<<blocks, C::THREADS, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -938,6 +998,30 @@ Entry make_entry() {
   e.lambda = launch_lambda<C>;
   e.init = launch_init<C>;
   e.l2 = launch_l2<C>;
+  return e;
+}
+
+// Kernels with the persistent solution in FP32, bf16 or fp16 for one (PDE, d, N): every
+// kernel in FP64 (traces FP64) or every kernel in FP32 (traces FP32).
+template <int PDE, int D, int N>
+StorageEntry make_storage_entry() {
+  using C = Cfg<PDE, D, N>;
+  StorageEntry e{};
+  e.pde = PDE;
+  e.dim = D;
+  e.N = N;
+  e.predictor[0][0] = launch_predictor<C, double, double, double, false, float>;
+  e.predictor[1][0] = launch_predictor<C, double, double, double, false, __nv_bfloat16>;
+  e.predictor[2][0] = launch_predictor<C, double, double, double, false, __half>;
+  e.predictor[0][1] = launch_predictor<C, float, float, float, false, float>;
+  e.predictor[1][1] = launch_predictor<C, float, float, float, false, __nv_bfloat16>;
+  e.predictor[2][1] = launch_predictor<C, float, float, float, false, __half>;
+  e.corrector[0][0] = launch_corrector<C, double, double, double, float>;
+  e.corrector[1][0] = launch_corrector<C, double, double, double, __nv_bfloat16>;
+  e.corrector[2][0] = launch_corrector<C, double, double, double, __half>;
+  e.corrector[0][1] = launch_corrector<C, float, float, float, float>;
+  e.corrector[1][1] = launch_corrector<C, float, float, float, __nv_bfloat16>;
+  e.corrector[2][1] = launch_corrector<C, float, float, float, __half>;
   return e;
 }
 

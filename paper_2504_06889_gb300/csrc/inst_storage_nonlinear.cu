@@ -1,0 +1,12 @@
+// Kernel instantiations with the persistent solution stored in FP32, bf16 or fp16 (Sec. 3.1
+// "storage"): compressible Euler and shallow water.
+#include "adg_kernels.cuh"
+
+namespace adg {
+void register_storage_nonlinear() {
+  register_storage(make_storage_entry<2, 3, 5>());  // Euler 3D, N = 5 (density wave)
+  register_storage(make_storage_entry<2, 3, 2>());
+  register_storage(make_storage_entry<3, 2, 4>());  // shallow water 2D, N = 4 (modes)
+  register_storage(make_storage_entry<3, 2, 2>());
+}
+}  // namespace adg

@@ -211,7 +211,7 @@ def test_errors_before_prerequisites(adg):
     assert lib.adg_init_mesh(h, 2, 3, cells, lo, lo) == adg.EINVAL
     assert lib.adg_init_mesh(h, 2, 3, cells, lo, hi) == adg.OK
     assert lib.adg_set_pde(h, adg.SWE, p, 0) == adg.EINVAL
-    assert lib.adg_set_kernel_precision(h, adg.K_STORAGE, adg.FP32, 0) == adg.EUNSUPPORTED
+    assert lib.adg_set_kernel_precision(h, adg.K_STORAGE, adg.FP8E4M3, 0) == adg.EUNSUPPORTED
     assert lib.adg_set_pde(h, adg.ACOUSTIC, p, 2) == adg.OK
     ws = C.c_size_t()
     assert lib.adg_workspace_bytes(h, C.byref(ws)) == adg.OK
