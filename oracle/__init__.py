@@ -30,9 +30,9 @@ _SRC = os.path.join(_HERE, "adg_oracle.c")
 _lock = threading.Lock()
 _lib = None
 
-ACOUSTIC, ELASTIC, EULER, SWE = 0, 1, 2, 3
+ACOUSTIC, ELASTIC, EULER, SWE, SWE_B = 0, 1, 2, 3, 4
 STORAGE = {"fp64": 0, "fp32": 1, "bf16": 2, "fp16": 3}
-SC_PLANAR, SC_EULER_WAVE, SC_SWE_MODES, SC_GAUSS_PULSE = 0, 1, 2, 3
+SC_PLANAR, SC_EULER_WAVE, SC_SWE_MODES, SC_GAUSS_PULSE, SC_LAKE = 0, 1, 2, 3, 4
 
 
 def build(force: bool = False) -> str:
@@ -93,6 +93,8 @@ def _load():
             lib.or_adjoint.argtypes = [P, dp, C.c_int, C.c_int, dp, dp, dp, dp]
             lib.or_adjoint.restype = C.c_double
             lib.or_rusanov.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int, dp, dp, dp, dp, dp]
+            lib.or_ncp.argtypes = [P, dp, C.c_int, dp, dp]
+            lib.or_ncp_fluctuation.argtypes = [P, C.c_int, C.c_int, dp, dp, dp]
             _lib = lib
     return _lib
 
@@ -103,7 +105,7 @@ def _dp(a: np.ndarray):
 
 
 def nvar(pde: int, dim: int) -> int:
-    return {ACOUSTIC: 1 + dim, ELASTIC: 9 if dim == 3 else 5, EULER: 2 + dim, SWE: 3}[pde]
+    return {ACOUSTIC: 1 + dim, ELASTIC: 9 if dim == 3 else 5, EULER: 2 + dim, SWE: 3, SWE_B: 4}[pde]
 
 
 def round_format(x, fmt):
@@ -179,6 +181,21 @@ class Mesh:
         F = np.zeros(self.V)
         _load().or_flux(self._h, cell, _dp(q), dir, _dp(F))
         return F
+
+    def ncp(self, q, dir, dq):
+        """B_dir(q) dq, the non-conservative product of eq. (swe_canonical)."""
+        q = np.ascontiguousarray(q, dtype=np.float64)
+        dq = np.ascontiguousarray(dq, dtype=np.float64)
+        out = np.zeros(self.V)
+        _load().or_ncp(self._h, _dp(q), dir, _dp(dq), _dp(out))
+        return out
+
+    def ncp_fluctuation(self, qm, qp, dir):
+        """Half the path integral of B across a face ([V][nface] traces of both sides)."""
+        qm, qp = (np.ascontiguousarray(a, dtype=np.float64) for a in (qm, qp))
+        out = np.zeros_like(qm)
+        _load().or_ncp_fluctuation(self._h, dir, qm.shape[-1], _dp(qm), _dp(qp), _dp(out))
+        return out
 
     def speed(self, q, dir, cell=0):
         q = np.ascontiguousarray(q, dtype=np.float64)

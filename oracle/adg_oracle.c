@@ -148,6 +148,7 @@ int or_nvar(int pde, int dim) {
     case OR_ELASTIC: return dim == 3 ? 9 : 5;  /* stresses (Voigt), velocities */
     case OR_EULER: return 2 + dim;             /* rho, rho v_1..v_d, E */
     case OR_SWE: return 3;                     /* h, hu, hv (flat bathymetry) */
+    case OR_SWE_B: return 4;                   /* h, hu, hv, b (Sec. 4.4) */
   }
   return -1;
 }
@@ -156,7 +157,7 @@ int or_setup(or_mesh* M, int dim, int N, const int* m, const double* lo, const d
              const double* params, int nparams, double cfl, int picard_iters) {
   memset(M, 0, sizeof(*M));
   if (dim < 2 || dim > 3 || N < 0 || N + 1 > OR_MAXN) return -1;
-  if (pde == OR_SWE && dim != 2) return -1;
+  if ((pde == OR_SWE || pde == OR_SWE_B) && dim != 2) return -1;
   M->dim = dim;
   M->N = N;
   M->n = N + 1;
@@ -274,7 +275,24 @@ void or_flux(const or_mesh* M, int cell, const double* q, int dir, double* F) {
     double vel[2] = {q[1] / h, q[2] / h};
     F[0] = q[1 + dir];
     for (int a = 0; a < 2; ++a) F[1 + a] = q[1 + a] * vel[dir] + (a == dir ? 0.5 * g * h * h : 0.0);
+  } else if (M->pde == OR_SWE_B) {
+    /* eq. (swe_cons): G = (h v_x, h v_x^2, h v_x v_y, 0), H likewise; the hydrostatic
+     * pressure is in the non-conservative product (or_ncp) */
+    double h = q[0];
+    double vel[2] = {q[1] / h, q[2] / h};
+    F[0] = q[1 + dir];
+    for (int a = 0; a < 2; ++a) F[1 + a] = q[1 + a] * vel[dir];
+    F[3] = 0.0;
   }
+}
+
+/* eq. (swe_noncons): C(Q) (along x) and D(Q) (along y) have the single nonzero row of the
+ * momentum along that direction, (g h, 0, 0, g h): B_dir(q) dq = g h (dh + db) e_{1+dir} */
+void or_ncp(const or_mesh* M, const double* q, int dir, const double* dq, double* out) {
+  for (int v = 0; v < M->nvar; ++v) out[v] = 0.0;
+  if (M->pde != OR_SWE_B) return;
+  double g = M->pp[0];
+  out[1 + dir] = g * q[0] * dq[0] + g * q[0] * dq[3];
 }
 
 double or_speed(const or_mesh* M, int cell, const double* q, int dir) {
@@ -294,7 +312,7 @@ double or_speed(const or_mesh* M, int cell, const double* q, int dir) {
     double p = (gamma - 1.0) * (E - 0.5 * rho * v2);
     return fabs(q[1 + dir] / rho) + sqrt(gamma * p / rho);
   }
-  if (M->pde == OR_SWE) {
+  if (M->pde == OR_SWE || M->pde == OR_SWE_B) {
     double g = M->pp[0];
     return fabs(q[1 + dir] / q[0]) + sqrt(g * q[0]);
   }
@@ -342,6 +360,17 @@ void or_exact(const or_mesh* M, int scen, const double* sp, int nsp, const doubl
     const double* p = sp + 5;
     for (int j = 0; j < nm; ++j, p += 4) h += p[0] * sin(p[1] * x[0] + p[2] * x[1] + p[3]);
     Q[0] = h;
+  } else if (scen == OR_SC_LAKE) {
+    /* eq. (lake_initial) with an optional disturbed surface: sp = [eta0, b0, ab, kbx, kby,
+     * nm, {a, kx, ky, phi} x nm]; b = b0 + ab sin(kbx x + kby y), eta = eta0 + sum a
+     * sin(k.x + phi), h = eta - b, v = 0.  With nm = 0 the lake is at rest for all t. */
+    double b = sp[1] + sp[2] * sin(sp[3] * x[0] + sp[4] * x[1]);
+    double eta = sp[0];
+    int nm = (int)sp[5];
+    const double* p = sp + 6;
+    for (int j = 0; j < nm; ++j, p += 4) eta += p[0] * sin(p[1] * x[0] + p[2] * x[1] + p[3]);
+    Q[0] = eta - b;
+    Q[3] = b;
   } else if (scen == OR_SC_GAUSS_PULSE) {
     /* sp = [x0[3], sigma, amp]: p = amp exp(-|x - x0|^2 / (2 sigma^2)), periodic
      * distance on the mesh box, v = 0 (t ignored) */
@@ -468,6 +497,18 @@ static int node_with(const or_mesh* M, int i, int dir, int a) {
   return i - node_dir_index(M, i, dir) * s + a * s;
 }
 
+/* derivative along dir of every variable of the state polynomial qs[v*NS+i] at node i,
+ * including 1/h_dir */
+static void ncp_state_derivative(const or_mesh* M, const double* qs, int i, int dir, double* dq) {
+  const int V = M->nvar, NS = ipow(M->n, M->dim);
+  int idir = node_dir_index(M, i, dir);
+  for (int v = 0; v < V; ++v) {
+    double s = 0.0;
+    for (int a = 0; a < M->n; ++a) s += M->D[idir][a] * qs[v * NS + node_with(M, i, dir, a)];
+    dq[v] = s / M->h[dir];
+  }
+}
+
 /* R[(k*V+v)*NS+i] for the space-time field q[(k*V+v)*NS+i] */
 static void space_derivative_of_flux(const or_mesh* M, int cell, const double* q, int nt,
                                      double* R) {
@@ -495,6 +536,20 @@ static void space_derivative_of_flux(const or_mesh* M, int cell, const double* q
           r += s / M->h[dir];
         }
         R[(k * V + v) * NS + i] = r;
+      }
+  /* non-conservative product, eq. (swe_canonical): R += sum_dir B_dir(q) dq/dx_dir, the
+   * derivative of the state polynomial taken at the node */
+  if (M->pde == OR_SWE_B)
+    for (int k = 0; k < nt; ++k)
+      for (int i = 0; i < NS; ++i) {
+        double qv[OR_MAXV];
+        for (int v = 0; v < V; ++v) qv[v] = q[(k * V + v) * NS + i];
+        for (int dir = 0; dir < d; ++dir) {
+          double dq[OR_MAXV], b[OR_MAXV];
+          ncp_state_derivative(M, q + (size_t)k * V * NS, i, dir, dq);
+          or_ncp(M, qv, dir, dq, b);
+          for (int v = 0; v < V; ++v) R[(k * V + v) * NS + i] += b[v];
+        }
       }
   free(F);
 }
@@ -589,8 +644,29 @@ void or_rusanov(const or_mesh* M, int cellL, int cellR, int dir, int nface, cons
   for (int v = 0; v < V; ++v)
     for (int j = 0; j < nface; ++j) {
       int o = v * nface + j;
-      G[o] = 0.5 * (Fm[o] + Fp[o]) + 0.5 * s * (qm[o] - qp[o]);
+      double jump = qm[o] - qp[o];
+      if (M->pde == OR_SWE_B) {
+        /* eq. (swe_custom_riemann): the dissipation acts on the surface elevation h + b
+         * instead of h, and not on b */
+        if (v == 0) jump = (qm[j] + qm[3 * nface + j]) - (qp[j] + qp[3 * nface + j]);
+        if (v == 3) jump = 0.0;
+      }
+      G[o] = 0.5 * (Fm[o] + Fp[o]) + 0.5 * s * jump;
     }
+}
+
+void or_ncp_fluctuation(const or_mesh* M, int dir, int nface, const double* qm, const double* qp,
+                        double* Dh) {
+  const int V = M->nvar;
+  for (int o = 0; o < V * nface; ++o) Dh[o] = 0.0;
+  if (M->pde != OR_SWE_B) return;
+  double g = M->pp[0];
+  for (int j = 0; j < nface; ++j) {
+    /* B_dir is linear in h along the straight path: int_0^1 g h(s) ds = g (h- + h+) / 2 */
+    double hbar = 0.5 * (qm[j] + qp[j]);
+    double deta = (qp[j] + qp[3 * nface + j]) - (qm[j] + qm[3 * nface + j]);
+    Dh[(1 + dir) * nface + j] = 0.5 * g * hbar * deta;
+  }
 }
 
 static int neighbour(const or_mesh* M, int c, int dir, int side) {
@@ -673,6 +749,24 @@ static void predict_cell(const or_mesh* M, int c, const double* Qc, double dt, d
       }
       Qout[v * NS + i] = Qc[v * NS + i] + dt * vol;
     }
+  /* non-conservative volume term, eq. (swe_canonical): Q_i -= dt sum_k w_k sum_dir
+   * B_dir(q_{k,i}) dq_k/dx_dir (i) (mass-inverted; the nodal quadrature of the cell integral
+   * of the test function times B grad q) */
+  if (M->pde == OR_SWE_B)
+    for (int i = 0; i < NS; ++i) {
+      double acc[OR_MAXV] = {0};
+      for (int k = 0; k < n; ++k) {
+        double qv[OR_MAXV];
+        for (int v = 0; v < V; ++v) qv[v] = q[(k * V + v) * NS + i];
+        for (int dir = 0; dir < d; ++dir) {
+          double dq[OR_MAXV], b[OR_MAXV];
+          ncp_state_derivative(M, q + (size_t)k * V * NS, i, dir, dq);
+          or_ncp(M, qv, dir, dq, b);
+          for (int v = 0; v < V; ++v) acc[v] += M->w[k] * b[v];
+        }
+      }
+      for (int v = 0; v < V; ++v) Qout[v * NS + i] -= dt * acc[v];
+    }
   free(q);
   free(Fbar);
   free(Qbar);
@@ -694,6 +788,16 @@ static void correct_cell(const or_mesh* M, int c, double dt, trace_fn tr, const 
                tr(ctx, cl, dir, 1, 1), tr(ctx, c, dir, 0, 1), G0);
     or_rusanov(M, c, cr, dir, NF, tr(ctx, c, dir, 1, 0), tr(ctx, cr, dir, 0, 0),
                tr(ctx, c, dir, 1, 1), tr(ctx, cr, dir, 0, 1), G1);
+    if (M->pde == OR_SWE_B) {
+      /* path-conservative jump term: c is the plus cell of its left face and the minus cell of
+       * its right face */
+      double* Dh = (double*)malloc(sizeof(double) * (size_t)V * NF);
+      or_ncp_fluctuation(M, dir, NF, tr(ctx, cl, dir, 1, 0), tr(ctx, c, dir, 0, 0), Dh);
+      for (int o = 0; o < V * NF; ++o) G0[o] -= Dh[o];
+      or_ncp_fluctuation(M, dir, NF, tr(ctx, c, dir, 1, 0), tr(ctx, cr, dir, 0, 0), Dh);
+      for (int o = 0; o < V * NF; ++o) G1[o] += Dh[o];
+      free(Dh);
+    }
     /* surface integral: int phi_k G.n dS on the right (n = +e_dir) and
      * left (n = -e_dir) faces, mass-matrix inverted */
     for (int v = 0; v < V; ++v)

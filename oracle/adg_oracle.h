@@ -32,11 +32,14 @@ extern "C" {
 #define OR_MAXN 10 /* n = N+1 <= 10 */
 #define OR_MAXV 9
 
-enum { OR_ACOUSTIC = 0, OR_ELASTIC = 1, OR_EULER = 2, OR_SWE = 3 };
+/* OR_SWE: shallow water with flat bathymetry in conservative form (h, hu, hv).
+ * OR_SWE_B: the paper's form of Sec. 4.4 with bathymetry, Q = (h, hu, hv, b), conservative
+ * fluxes without the hydrostatic pressure and the non-conservative product B(Q) grad Q. */
+enum { OR_ACOUSTIC = 0, OR_ELASTIC = 1, OR_EULER = 2, OR_SWE = 3, OR_SWE_B = 4 };
 /* storage formats of Table precision_bits: significand bits p (with the hidden bit),
  * smallest normal exponent, largest exponent */
 enum { OR_ST_FP64 = 0, OR_ST_FP32 = 1, OR_ST_BF16 = 2, OR_ST_FP16 = 3 };
-enum { OR_SC_PLANAR = 0, OR_SC_EULER_WAVE = 1, OR_SC_SWE_MODES = 2, OR_SC_GAUSS_PULSE = 3 };
+enum { OR_SC_PLANAR = 0, OR_SC_EULER_WAVE = 1, OR_SC_SWE_MODES = 2, OR_SC_GAUSS_PULSE = 3, OR_SC_LAKE = 4 };
 
 typedef struct {
   int dim, N, n, nvar, pde;
@@ -68,6 +71,9 @@ double or_lagrange(int n, const double* xi, int j, double x);
 /* pointwise physics */
 void or_flux(const or_mesh* M, int cell, const double* q, int dir, double* F);
 double or_speed(const or_mesh* M, int cell, const double* q, int dir);
+/* non-conservative product B_dir(q) dq of eq. (swe_canonical) for OR_SWE_B, given the
+ * derivative dq of the state along dir (zero for every other PDE) */
+void or_ncp(const or_mesh* M, const double* q, int dir, const double* dq, double* out);
 
 /* exact / initial data and error */
 void or_exact(const or_mesh* M, int scen, const double* sp, int nsp, const double* x, double t,
@@ -101,9 +107,15 @@ void or_adjoint_step(const or_mesh* M, const double* Qn, double dt, double* lam,
 double or_adjoint(const or_mesh* M, const double* Q0, int nsteps, int nrecv, const double* xyz,
                   const double* observed, double* gq0, double* gc);
 
-/* Rusanov flux on one face node set, exposed for unit tests */
+/* Rusanov flux on one face node set, exposed for unit tests (eq. rusanov_flux; for OR_SWE_B
+ * the well-balanced form of eq. swe_custom_riemann without its non-conservative part) */
 void or_rusanov(const or_mesh* M, int cellL, int cellR, int dir, int nface, const double* qm,
                 const double* qp, const double* Fm, const double* Fp, double* G);
+/* half the path integral of the non-conservative product across a face, 1/2 int_0^1
+ * B_dir(q- + s (q+ - q-)) ds (q+ - q-), on the straight path (OR_SWE_B; zero otherwise):
+ * the face's minus cell adds it to the flux G, the plus cell subtracts it */
+void or_ncp_fluctuation(const or_mesh* M, int dir, int nface, const double* qm, const double* qp,
+                        double* Dh);
 
 /* heap handles (used by the Python wrapper) */
 or_mesh* or_create(int dim, int N, const int* m, const double* lo, const double* hi, int pde,

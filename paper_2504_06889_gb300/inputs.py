@@ -25,13 +25,14 @@ from dataclasses import dataclass, field, replace
 
 import numpy as np
 
-ACOUSTIC, ELASTIC, EULER, SWE = 0, 1, 2, 3
-SC_PLANAR, SC_EULER_WAVE, SC_SWE_MODES, SC_GAUSS_PULSE = 0, 1, 2, 3
-PDE_NAMES = {ACOUSTIC: "acoustic", ELASTIC: "elastic", EULER: "euler", SWE: "swe"}
+ACOUSTIC, ELASTIC, EULER, SWE, SWE_B = 0, 1, 2, 3, 4
+SC_PLANAR, SC_EULER_WAVE, SC_SWE_MODES, SC_GAUSS_PULSE, SC_LAKE = 0, 1, 2, 3, 4
+PDE_NAMES = {ACOUSTIC: "acoustic", ELASTIC: "elastic", EULER: "euler", SWE: "swe",
+             SWE_B: "swe_bathymetry"}
 
 
 def nvar(pde: int, dim: int) -> int:
-    return {ACOUSTIC: 1 + dim, ELASTIC: 9 if dim == 3 else 5, EULER: 2 + dim, SWE: 3}[pde]
+    return {ACOUSTIC: 1 + dim, ELASTIC: 9 if dim == 3 else 5, EULER: 2 + dim, SWE: 3, SWE_B: 4}[pde]
 
 
 # ---------------------------------------------------------------------------
@@ -99,6 +100,17 @@ def swe_modes(seed=4, h0=1.0, a0=0.01, nmodes=8, amp=1e-3):
         m = rng.integers(1, 5, size=2)
         phi = rng.uniform(0.0, 2 * np.pi)
         out += [amp, 2 * np.pi * m[0], 2 * np.pi * m[1], phi]
+    return np.asarray(out, dtype=np.float64)
+
+
+def lake(eta0=2.0, b0=0.0, ab=1.0, kb=(2 * np.pi, 2 * np.pi), nmodes=0, amp=1e-2, seed=6):
+    """Lake over the sinusoidal bathymetry b = b0 + ab sin(kb.x) with surface eta = eta0 plus
+    nmodes seeded periodic modes of amplitude amp (none: the lake at rest), h = eta - b, v = 0."""
+    rng = np.random.default_rng(seed)
+    out = [eta0, b0, ab, kb[0], kb[1], float(nmodes)]
+    for _ in range(nmodes):
+        m = rng.integers(1, 4, size=2)
+        out += [amp, 2 * np.pi * m[0], 2 * np.pi * m[1], rng.uniform(0.0, 2 * np.pi)]
     return np.asarray(out, dtype=np.float64)
 
 
@@ -205,6 +217,14 @@ def swe2d_modes(m=512, N=4, steps=200, seed=4):
                     swe_modes(seed), steps, has_exact=False)
 
 
+def swe2d_lake(m=27, N=5, steps=200, eta0=2.0, b0=0.0):
+    """Shallow water with bathymetry (non-conservative form), g = 9.81: the lake at rest over
+    b = b0 + sin(2 pi (x + y)) with surface eta0 (the paper's setup: 27^2 cells, order 5,
+    eta0 = 2); the exact solution is the initial state."""
+    return Workload("swelake_N%d_%dx%d" % (N, m, m), 2, N, (m, m), SWE_B, (9.81,), SC_LAKE,
+                    lake(eta0, b0), steps)
+
+
 def acoustic3d_pulse(m=32, N=4, steps=100, seed=5):
     """3D acoustics, rho = 1, c = 1, Gaussian pressure pulse (sigma = 0.05) at a seeded spot."""
     return Workload("acoustic3d_N%d_%d^3" % (N, m), 3, N, (m, m, m), ACOUSTIC, (1.0, 1.0),
@@ -232,5 +252,6 @@ WORKLOADS = {
     "euler3d": euler3d_wave,
     "elastic3d": elastic3d_planar,
     "swe2d": swe2d_modes,
+    "swelake": swe2d_lake,
     "acoustic3d": acoustic3d_pulse,
 }
