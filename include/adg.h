@@ -59,8 +59,14 @@ enum adg_status {
   ADG_ENOMEM = -7        /* workspace smaller than adg_workspace_bytes() */
 };
 
-/* PDE systems of Sec. 4 (eq. acoustic, lin_elastic, euler_eq, swe with b = const) */
-enum adg_pde { ADG_ACOUSTIC = 0, ADG_ELASTIC = 1, ADG_EULER = 2, ADG_SWE = 3 };
+/* PDE systems of Sec. 4 (eq. acoustic, lin_elastic, euler_eq, swe with b = const).
+ * ADG_SWE_B: the shallow-water form of eq. (swe_canonical) with bathymetry, 2D, variables
+ * (h, hu, hv, b): conservative fluxes of eq. (swe_cons) without the hydrostatic pressure, the
+ * non-conservative product of eq. (swe_noncons) in the predictor and the volume integral, and
+ * the well-balanced Rusanov flux of eq. (swe_custom_riemann) (dissipation on h + b) with the
+ * path-conservative jump term 1/2 int B dq on the straight path, added by a face's minus cell
+ * and subtracted by its plus cell.  Parameter: g.  Built for N = 2, 4, 5. */
+enum adg_pde { ADG_ACOUSTIC = 0, ADG_ELASTIC = 1, ADG_EULER = 2, ADG_SWE = 3, ADG_SWE_B = 4 };
 
 /* The per-kernel precision knobs of Sec. 3.1 ("predictor", "Picard", "corrector",
  * "storage"), with the Riemann solve split from the face integral. */
@@ -92,12 +98,17 @@ enum adg_flags {
  *  ADG_SC_SWE_MODES   [h0, a0, kx0, ky0, nm, {a, kx, ky, phi} x nm], at rest;
  *                     closed form at t = 0 only
  *  ADG_SC_GAUSS_PULSE [x0, y0, z0, sigma, amp]: p = amp exp(-|x-x0|^2/(2 sigma^2)),
- *                     periodic distance, v = 0; closed form at t = 0 only */
+ *                     periodic distance, v = 0; closed form at t = 0 only
+ *  ADG_SC_LAKE        [eta0, b0, ab, kbx, kby, nm, {a, kx, ky, phi} x nm] (ADG_SWE_B):
+ *                     b = b0 + ab sin(kbx x + kby y), eta = eta0 + sum a sin(kx x + ky y + phi),
+ *                     h = eta - b, v = 0 (eq. lake_initial); nm = 0 is the lake at rest, whose
+ *                     closed form is the initial state at every t; otherwise t = 0 only */
 enum adg_scenario {
   ADG_SC_PLANAR = 0,
   ADG_SC_EULER_WAVE = 1,
   ADG_SC_SWE_MODES = 2,
-  ADG_SC_GAUSS_PULSE = 3
+  ADG_SC_GAUSS_PULSE = 3,
+  ADG_SC_LAKE = 4
 };
 
 /* Create / destroy a context bound to the current CUDA device. */

@@ -14,12 +14,12 @@ import numpy as np
 from . import build as _build
 
 OK, EINVAL, ENOTINIT, ECUDA, ENONFINITE, ETIMEOUT, EUNSUPPORTED, ENOMEM = 0, -1, -2, -3, -4, -5, -6, -7
-ACOUSTIC, ELASTIC, EULER, SWE = 0, 1, 2, 3
+ACOUSTIC, ELASTIC, EULER, SWE, SWE_B = 0, 1, 2, 3, 4
 K_PICARD, K_PREDICTOR, K_RIEMANN, K_CORRECTOR, K_STORAGE = 0, 1, 2, 3, 4
 FP64, FP32, BF16, FP16, FP8E4M3 = 0, 1, 2, 3, 4
 F_COMPENSATED_LAST, F_PER_CELL_SCALE, F_COMPENSATED_TWO = 1, 2, 4
 PRED_PICARD, PRED_CK = 0, 1
-SC_PLANAR, SC_EULER_WAVE, SC_SWE_MODES, SC_GAUSS_PULSE = 0, 1, 2, 3
+SC_PLANAR, SC_EULER_WAVE, SC_SWE_MODES, SC_GAUSS_PULSE, SC_LAKE = 0, 1, 2, 3, 4
 PREC_NAMES = {"fp64": FP64, "fp32": FP32, "bf16": BF16, "fp16": FP16, "fp8": FP8E4M3, "fp8e4m3": FP8E4M3}
 
 _lib = None

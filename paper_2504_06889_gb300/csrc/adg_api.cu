@@ -32,6 +32,7 @@ void register_acoustic();
 void register_euler();
 void register_elastic();
 void register_swe();
+void register_swe_bathymetry();
 void register_storage_linear();
 void register_storage_nonlinear();
 
@@ -42,6 +43,7 @@ static void ensure_registry() {
     register_euler();
     register_elastic();
     register_swe();
+    register_swe_bathymetry();
     register_storage_linear();
     register_storage_nonlinear();
   });
@@ -320,6 +322,7 @@ int adg_nvar(int pde, int dim) {
     case ADG_ELASTIC: return dim == 3 ? 9 : 5;
     case ADG_EULER: return 2 + dim;
     case ADG_SWE: return dim == 2 ? 3 : -1;
+    case ADG_SWE_B: return dim == 2 ? 4 : -1;
   }
   return -1;
 }
@@ -521,7 +524,7 @@ static int reset_scalars_and_lambda(adg_ctx* c, double t) {
 int adg_set_initial(adg_ctx* c, int scenario, const double* params, int nparams) {
   if (!c) return ADG_EINVAL;
   if (!c->have_bufs || !c->entry) return fail(c, ADG_ENOTINIT, "bind buffers first");
-  if (scenario < ADG_SC_PLANAR || scenario > ADG_SC_GAUSS_PULSE) return fail(c, ADG_EINVAL, "unknown scenario");
+  if (scenario < ADG_SC_PLANAR || scenario > ADG_SC_LAKE) return fail(c, ADG_EINVAL, "unknown scenario");
   if (!params || nparams < 1) return fail(c, ADG_EINVAL, "missing scenario parameters");
   // validate the encodings' lengths
   int need = 0;
@@ -535,6 +538,10 @@ int adg_set_initial(adg_ctx* c, int scenario, const double* params, int nparams)
     if (c->pde != ADG_SWE) return fail(c, ADG_EINVAL, "swe modes need the SWE PDE");
     if (nparams < 5) return fail(c, ADG_EINVAL, "swe modes: too few parameters");
     need = 5 + 4 * (int)params[4];
+  } else if (scenario == ADG_SC_LAKE) {
+    if (c->pde != ADG_SWE_B) return fail(c, ADG_EINVAL, "the lake needs the SWE form with bathymetry");
+    if (nparams < 6) return fail(c, ADG_EINVAL, "lake: too few parameters");
+    need = 6 + 4 * (int)params[5];
   } else {
     if (c->pde != ADG_ACOUSTIC) return fail(c, ADG_EINVAL, "gauss pulse needs acoustics");
     need = 5;
@@ -778,7 +785,8 @@ static int run_l2(adg_ctx* c, const double* Qref, double* per, double* tot) {
 int adg_error_vs_exact(adg_ctx* c, double* per, double* tot) {
   if (!c) return ADG_EINVAL;
   if (c->scenario < 0) return fail(c, ADG_ENOTINIT, "no scenario set");
-  if ((c->scenario == ADG_SC_SWE_MODES || c->scenario == ADG_SC_GAUSS_PULSE)) {
+  const bool moving_lake = c->scenario == ADG_SC_LAKE && c->sp.size() > 5 && c->sp[5] > 0.0;
+  if (c->scenario == ADG_SC_SWE_MODES || c->scenario == ADG_SC_GAUSS_PULSE || moving_lake) {
     DevScalars s;
     ADG_CUDA(c, cudaMemcpyAsync(&s, c->sc, sizeof(s), cudaMemcpyDeviceToHost, c->stream));
     ADG_CUDA(c, cudaStreamSynchronize(c->stream));

@@ -27,6 +27,8 @@ namespace adg {
 template <int PDE_, int D_, int N_> struct Cfg {
   static constexpr int PDE = PDE_, D = D_, N = N_, n = N_ + 1;
   static constexpr int NS = ipow_c(n, D), NF = ipow_c(n, D - 1), V = nvar_c(PDE_, D_);
+  static constexpr int NG = ncp_grads_c(PDE_);  // state pencils for a non-conservative product
+  static constexpr int VX = V + NG;             // pencil components per direction
   static constexpr int CPB = NS >= 96 ? 1 : (128 / NS);  // cells per block
   static constexpr int THREADS = CPB * NS;
 };
@@ -169,9 +171,11 @@ __device__ __forceinline__ float store_to_float(__half x) { return __half2float(
 
 template <class C, class T, class TP> struct PredSmem {
   // two flux-slice buffers (double buffering) during the sweeps
-  static constexpr size_t sweep = sizeof(T) * 2 * C::CPB * C::D * C::V * Pencil<C>::PER_DIR;
-  // final stage: Fbar in pencil layout + Qbar
-  static constexpr size_t fin = sizeof(TP) * C::CPB * (C::D * C::V * Pencil<C>::PER_DIR + C::V * C::NS);
+  static constexpr size_t sweep = sizeof(T) * 2 * C::CPB * C::D * C::VX * Pencil<C>::PER_DIR;
+  // final stage: Fbar in pencil layout + Qbar (+ the state pencils of every time node for a
+  // non-conservative product)
+  static constexpr size_t fin =
+      sizeof(TP) * C::CPB * (C::D * C::V * Pencil<C>::PER_DIR + C::V * C::NS + C::n * C::D * C::NG * Pencil<C>::PER_DIR);
   static constexpr size_t big = ((sweep > fin ? sweep : fin) + 15) / 16 * 16;
   static constexpr size_t tables = sizeof(T) * (C::n * C::n + C::n + 1) + sizeof(TP) * (C::n * C::n + 3 * C::n);
   static constexpr size_t total = big + tables;
@@ -213,9 +217,12 @@ __device__ __forceinline__ void predictor_final(const StepArgs& a, const T (*q)[
       for (int dir = 0; dir < D; ++dir) Fb[dir][v] += wk * F[dir][v];
     }
   }
-  // shared: Fbar [dir][v][pencil layout], Qbar [v][node]
-  TP* sFb = smem_fin + (size_t)lc * (D * V * PD + V * NS);
+  // shared: Fbar [dir][v][pencil layout], Qbar [v][node], and for a non-conservative product
+  // the differentiated state variables of every time node [k][dir][g][pencil layout]
+  constexpr int NG = C::NG;
+  TP* sFb = smem_fin + (size_t)lc * (D * V * PD + V * NS + n * D * NG * PD);
   TP* sQb = sFb + D * V * PD;
+  TP* sNc = sQb + V * NS;
   if (owner) {
 #pragma unroll
     for (int v = 0; v < V; ++v) {
@@ -223,6 +230,15 @@ __device__ __forceinline__ void predictor_final(const StepArgs& a, const T (*q)[
 #pragma unroll
       for (int dir = 0; dir < D; ++dir)
         if (Ph::nz(dir, v)) sFb[(dir * V + v) * PD + pb[dir] + idx[dir]] = Fb[dir][v];
+    }
+    if constexpr (NG > 0) {
+#pragma unroll
+      for (int k = 0; k < n; ++k)
+#pragma unroll
+        for (int dir = 0; dir < D; ++dir)
+#pragma unroll
+          for (int g = 0; g < NG; ++g)
+            sNc[((k * D + dir) * NG + g) * PD + pb[dir] + idx[dir]] = conv<TP>(q[k][Ph::gvar(g)]);
     }
   }
   __syncthreads();
@@ -233,6 +249,32 @@ __device__ __forceinline__ void predictor_final(const StepArgs& a, const T (*q)[
   if (valid && owner) {
     const TP ihp[3] = {conv<TP>(a.invh[0]), conv<TP>(a.invh[1]), conv<TP>(a.invh[2])};
     double* Qw = a.Q + (size_t)cell * V * NS;
+    // non-conservative volume term: nc = sum_k w_k sum_dir B_dir(q_k) dq_k/dx_dir at the node
+    TP nc[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) nc[v] = TP(0);
+    if constexpr (NG > 0) {
+#pragma unroll
+      for (int k = 0; k < n; ++k) {
+        TP grad[D][NG > 0 ? NG : 1];
+#pragma unroll
+        for (int dir = 0; dir < D; ++dir)
+#pragma unroll
+          for (int g = 0; g < NG; ++g) {
+            const TP* Np = sNc + ((k * D + dir) * NG + g) * PD + pb[dir];
+            TP s = TP(0);
+#pragma unroll
+            for (int m = 0; m < n; ++m) s += Tab<TP>::D(a.tab, idx[dir], m) * ihp[dir] * Np[m];
+            grad[dir][g] = s;
+          }
+        TP qk[V], out[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) qk[v] = conv<TP>(q[k][v]);
+        Ph::ncp(ppP, qk, grad, out);
+#pragma unroll
+        for (int v = 0; v < V; ++v) nc[v] += sw[k] * out[v];
+      }
+    }
 #pragma unroll
     for (int v = 0; v < V; ++v) {
       TP vol = TP(0);
@@ -247,10 +289,15 @@ __device__ __forceinline__ void predictor_final(const StepArgs& a, const T (*q)[
         vol += s * ihp[dir];
       }
       if constexpr (std::is_same<TQ, double>::value) {
-        Qw[v * NS + i] += dt * conv<double>(vol);
+        if constexpr (NG > 0)
+          Qw[v * NS + i] = (Qw[v * NS + i] + dt * conv<double>(vol)) - dt * conv<double>(nc[v]);
+        else
+          Qw[v * NS + i] += dt * conv<double>(vol);
       } else {
         TQ* Qsw = static_cast<TQ*>(a.Qs) + (size_t)cell * V * NS;
-        Qsw[v * NS + i] = store_round<TQ>(store_widen(Qsw[v * NS + i]) + dt * conv<double>(vol));
+        double qv = store_widen(Qsw[v * NS + i]) + dt * conv<double>(vol);
+        if constexpr (NG > 0) qv -= dt * conv<double>(nc[v]);
+        Qsw[v * NS + i] = store_round<TQ>(qv);
       }
     }
   }
@@ -286,6 +333,45 @@ __device__ __forceinline__ void predictor_final(const StepArgs& a, const T (*q)[
   }
 }
 
+// Non-conservative product inside the predictor (eq. swe_canonical): the state variables it
+// differentiates go to the pencil slots V.. V+NG-1 of every direction next to the fluxes, and a
+// node's product B_dir(q) dq/dx_dir comes from the same contraction as the flux derivative.
+// No-ops for PDEs without a product.
+template <class C, class T>
+__device__ __forceinline__ void write_ncp_pencils(T* sF, const T* q, const int* pb, const int* idx) {
+  using Ph = Phys<C::PDE, C::D>;
+  if constexpr (C::NG > 0) {
+    constexpr int PD = Pencil<C>::PER_DIR;
+#pragma unroll
+    for (int dir = 0; dir < C::D; ++dir)
+#pragma unroll
+      for (int g = 0; g < C::NG; ++g) sF[(dir * C::VX + C::V + g) * PD + pb[dir] + idx[dir]] = q[Ph::gvar(g)];
+  }
+}
+template <class C, class T, int S>
+__device__ __forceinline__ void ncp_at_node(const PP<T>& pp, const T* sF, const T* q, const int* pb,
+                                            const T (*Dr)[S], T* out) {
+  using Ph = Phys<C::PDE, C::D>;
+#pragma unroll
+  for (int v = 0; v < C::V; ++v) out[v] = T(0);
+  if constexpr (C::NG > 0) {
+    constexpr int PD = Pencil<C>::PER_DIR;
+    T grad[C::D][C::NG];
+#pragma unroll
+    for (int dir = 0; dir < C::D; ++dir)
+#pragma unroll
+      for (int g = 0; g < C::NG; ++g) {
+        T f[S];
+        VecLoad<T, S>::load(sF + (dir * C::VX + C::V + g) * PD + pb[dir], f);
+        T s = T(0);
+#pragma unroll
+        for (int m = 0; m < C::n; ++m) s += Dr[dir][m] * f[m];
+        grad[dir][g] = s;
+      }
+    Ph::ncp(pp, q, grad, out);
+  }
+}
+
 // ------------------------------------------------------------------------------------------------
 // predictor + volume integral + face traces
 // CK = false: Picard sweeps (Sec. 2.1, eq. Picard).  CK = true: Cauchy-Kowalevskaya for the
@@ -296,7 +382,7 @@ __device__ __forceinline__ void predictor_final(const StepArgs& a, const T (*q)[
 template <class C, class T, class TP, class TS, bool CK = false, class TQ = double>
 __global__ void __launch_bounds__(C::THREADS) k_predictor(const __grid_constant__ StepArgs a) {
   using Ph = Phys<C::PDE, C::D>;
-  constexpr int n = C::n, V = C::V, D = C::D, NS = C::NS, NF = C::NF, CPB = C::CPB;
+  constexpr int n = C::n, V = C::V, D = C::D, NS = C::NS, CPB = C::CPB, VX = C::VX;
   constexpr int S = Pencil<C>::S, PD = Pencil<C>::PER_DIR;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double s_dt;
@@ -376,7 +462,7 @@ __global__ void __launch_bounds__(C::THREADS) k_predictor(const __grid_constant_
   }
 
   T* sFbuf = reinterpret_cast<T*>(smem_raw);
-  constexpr size_t bufsz = (size_t)CPB * D * V * PD;
+  constexpr size_t bufsz = (size_t)CPB * D * VX * PD;
   // zero the pencil pads once (they are read as part of the vector loads and multiplied by 0)
   if (S != n)
     for (size_t t = threadIdx.x; t < 2 * bufsz; t += blockDim.x) sFbuf[t] = T(0);
@@ -396,7 +482,7 @@ __global__ void __launch_bounds__(C::THREADS) k_predictor(const __grid_constant_
     for (int v = 0; v < V; ++v) dq[v] = Qh[v];
 #pragma unroll 1
     for (int m = 1; m <= C::N; ++m) {
-      T* sF = sFbuf + buf * bufsz + (size_t)lc * D * V * PD;
+      T* sF = sFbuf + buf * bufsz + (size_t)lc * D * VX * PD;
       {
         T F[D][V];
         Ph::flux(pp, dq, F);
@@ -404,7 +490,7 @@ __global__ void __launch_bounds__(C::THREADS) k_predictor(const __grid_constant_
         for (int dir = 0; dir < D; ++dir)
 #pragma unroll
           for (int v = 0; v < V; ++v)
-            if (Ph::nz(dir, v)) sF[(dir * V + v) * PD + pb[dir] + idx[dir]] = F[dir][v];
+            if (Ph::nz(dir, v)) sF[(dir * VX + v) * PD + pb[dir] + idx[dir]] = F[dir][v];
       }
       __syncthreads();
       const T* fac = sdtP + m * n;
@@ -415,7 +501,7 @@ __global__ void __launch_bounds__(C::THREADS) k_predictor(const __grid_constant_
         for (int dir = 0; dir < D; ++dir) {
           if (!Ph::nz(dir, v)) continue;
           T f[S];
-          VecLoad<T, S>::load(sF + (dir * V + v) * PD + pb[dir], f);
+          VecLoad<T, S>::load(sF + (dir * VX + v) * PD + pb[dir], f);
 #pragma unroll
           for (int mm = 0; mm < n; ++mm) rv += Dr[dir][mm] * f[mm];
         }
@@ -429,7 +515,7 @@ __global__ void __launch_bounds__(C::THREADS) k_predictor(const __grid_constant_
   // Sweep 1 starts from q = Q at every time node, so all time slices share one flux and one
   // derivative R: q^1[kk] = Q - dt (sum_l P[kk][l]) R.
   if (!CK && a.picard_iters > 0) {
-    T* sF = sFbuf + (size_t)lc * D * V * PD;
+    T* sF = sFbuf + (size_t)lc * D * VX * PD;
     {
       T F[D][V];
       Ph::flux(pp, Qh, F);
@@ -437,17 +523,20 @@ __global__ void __launch_bounds__(C::THREADS) k_predictor(const __grid_constant_
       for (int dir = 0; dir < D; ++dir)
 #pragma unroll
         for (int v = 0; v < V; ++v)
-          if (Ph::nz(dir, v)) sF[(dir * V + v) * PD + pb[dir] + idx[dir]] = F[dir][v];
+          if (Ph::nz(dir, v)) sF[(dir * VX + v) * PD + pb[dir] + idx[dir]] = F[dir][v];
+      write_ncp_pencils<C>(sF, Qh, pb, idx);
     }
     __syncthreads();
+    T ncpv[V];
+    ncp_at_node<C>(pp, sF, Qh, pb, Dr, ncpv);
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-      T rv = T(0);
+      T rv = ncpv[v];
 #pragma unroll
       for (int dir = 0; dir < D; ++dir) {
         if (!Ph::nz(dir, v)) continue;
         T f[S];
-        VecLoad<T, S>::load(sF + (dir * V + v) * PD + pb[dir], f);
+        VecLoad<T, S>::load(sF + (dir * VX + v) * PD + pb[dir], f);
 #pragma unroll
         for (int m = 0; m < n; ++m) rv += Dr[dir][m] * f[m];
       }
@@ -464,7 +553,7 @@ __global__ void __launch_bounds__(C::THREADS) k_predictor(const __grid_constant_
       for (int v = 0; v < V; ++v) qn[k][v] = Qh[v];
 #pragma unroll
     for (int k = 0; k < n; ++k) {
-      T* sF = sFbuf + buf * bufsz + (size_t)lc * D * V * PD;
+      T* sF = sFbuf + buf * bufsz + (size_t)lc * D * VX * PD;
       {
         T F[D][V];
         Ph::flux(pp, q[k], F);
@@ -472,17 +561,20 @@ __global__ void __launch_bounds__(C::THREADS) k_predictor(const __grid_constant_
         for (int dir = 0; dir < D; ++dir)
 #pragma unroll
           for (int v = 0; v < V; ++v)
-            if (Ph::nz(dir, v)) sF[(dir * V + v) * PD + pb[dir] + idx[dir]] = F[dir][v];
+            if (Ph::nz(dir, v)) sF[(dir * VX + v) * PD + pb[dir] + idx[dir]] = F[dir][v];
+        write_ncp_pencils<C>(sF, q[k], pb, idx);
       }
       __syncthreads();
+      T ncpv[V];
+      ncp_at_node<C>(pp, sF, q[k], pb, Dr, ncpv);
 #pragma unroll
       for (int v = 0; v < V; ++v) {
-        T rv = T(0);
+        T rv = ncpv[v];
 #pragma unroll
         for (int dir = 0; dir < D; ++dir) {
           if (!Ph::nz(dir, v)) continue;
           T f[S];
-          VecLoad<T, S>::load(sF + (dir * V + v) * PD + pb[dir], f);
+          VecLoad<T, S>::load(sF + (dir * VX + v) * PD + pb[dir], f);
 #pragma unroll
           for (int m = 0; m < n; ++m) rv += Dr[dir][m] * f[m];
         }
@@ -611,7 +703,12 @@ __global__ void __launch_bounds__(C::THREADS) k_corrector(const __grid_constant_
         const TR qp = sT[((f * 2 + 1) * 2 + 0) * V * NF + e];
         const TR Fm = sT[((f * 2 + 0) * 2 + 1) * V * NF + e];
         const TR Fp = sT[((f * 2 + 1) * 2 + 1) * V * NF + e];
-        const TR G = half * (Fm + Fp) + half * s * (qm - qp);
+        TR G;
+        if constexpr (C::NG > 0)  // well-balanced flux with the non-conservative jump term
+          G = Ph::face_flux(ppL, sT + ((f * 2 + 0) * 2 + 0) * V * NF, sT + ((f * 2 + 1) * 2 + 0) * V * NF, NF,
+                            e % NF, e / NF, f / 2, (f % 2) == 1, s, Fm, Fp);
+        else
+          G = half * (Fm + Fp) + half * s * (qm - qp);
         sG[f * V * NF + e] = conv<TC>(G);
       }
     }
@@ -719,7 +816,7 @@ __global__ void __launch_bounds__(C::THREADS) k_corrector(const __grid_constant_
 template <class C>
 __global__ void k_lambda(const __grid_constant__ StepArgs a) {
   using Ph = Phys<C::PDE, C::D>;
-  constexpr int V = C::V, NS = C::NS, D = C::D;
+  constexpr int V = C::V, NS = C::NS;
   __shared__ unsigned long long s_lam;
   __shared__ unsigned int s_bad;
   if (threadIdx.x == 0) {
@@ -790,6 +887,13 @@ __device__ void exact_solution(int scen, const double* sp, const PdeParams& pp, 
     const int nm = (int)sp[4];
     for (int j = 0; j < nm; ++j) h += sp[5 + 4 * j] * sin(sp[6 + 4 * j] * x[0] + sp[7 + 4 * j] * x[1] + sp[8 + 4 * j]);
     Q[0] = h;
+  } else if (scen == 4) {  // lake over sinusoidal bathymetry, eq. (lake_initial), optional modes
+    const double b = sp[1] + sp[2] * sin(sp[3] * x[0] + sp[4] * x[1]);
+    double eta = sp[0];
+    const int nm = (int)sp[5];
+    for (int j = 0; j < nm; ++j) eta += sp[6 + 4 * j] * sin(sp[7 + 4 * j] * x[0] + sp[8 + 4 * j] * x[1] + sp[9 + 4 * j]);
+    Q[0] = eta - b;
+    if constexpr (V == 4) Q[3] = b;
   } else if (scen == 3) {  // Gaussian pressure pulse, periodic distance
     double r2 = 0.0;
 #pragma unroll

@@ -11,8 +11,10 @@ namespace adg {
 
 constexpr int ipow_c(int b, int e) { return e == 0 ? 1 : b * ipow_c(b, e - 1); }
 constexpr int nvar_c(int pde, int d) {
-  return pde == 0 ? 1 + d : pde == 1 ? (d == 3 ? 9 : 5) : pde == 2 ? 2 + d : 3;
+  return pde == 0 ? 1 + d : pde == 1 ? (d == 3 ? 9 : 5) : pde == 2 ? 2 + d : pde == 3 ? 3 : 4;
 }
+// state variables whose derivatives enter a non-conservative product B(Q) grad Q
+constexpr int ncp_grads_c(int pde) { return pde == 4 ? 2 : 0; }
 
 // Arithmetic helpers that also work for bf16 (computed with bf16 rounding per op).
 template <class T> __device__ __forceinline__ T tcast(double x) { return (T)x; }
@@ -113,6 +115,7 @@ template <int PDE, int D> struct Phys;
 template <int D> struct Phys<0, D> {
   static constexpr int V = 1 + D;
   static constexpr bool linear = true;
+  static constexpr int NG = 0;  // no non-conservative product
   __host__ __device__ static constexpr bool nz(int dir, int v) { return v == 0 || v == 1 + dir; }
   template <class T> __device__ static __forceinline__ void flux(const PP<T>& p, const T* q, T (*F)[V]) {
 #pragma unroll
@@ -132,6 +135,7 @@ template <int D> struct Phys<0, D> {
 template <> struct Phys<1, 3> {
   static constexpr int V = 9;  // sxx syy szz sxy syz sxz vx vy vz
   static constexpr bool linear = true;
+  static constexpr int NG = 0;  // no non-conservative product
   __host__ __device__ static constexpr bool nz(int dir, int v) {
     return !((dir == 0 && v == 4) || (dir == 1 && v == 5) || (dir == 2 && v == 3));
   }
@@ -176,6 +180,7 @@ template <> struct Phys<1, 3> {
 template <> struct Phys<1, 2> {
   static constexpr int V = 5;  // sxx syy sxy vx vy
   static constexpr bool linear = true;
+  static constexpr int NG = 0;  // no non-conservative product
   __host__ __device__ static constexpr bool nz(int, int) { return true; }
   template <class T> __device__ static __forceinline__ void flux(const PP<T>& p, const T* q, T (*F)[V]) {
     const T vx = q[3], vy = q[4];
@@ -199,6 +204,7 @@ template <> struct Phys<1, 2> {
 template <int D> struct Phys<2, D> {
   static constexpr int V = 2 + D;
   static constexpr bool linear = false;
+  static constexpr int NG = 0;  // no non-conservative product
   __host__ __device__ static constexpr bool nz(int, int) { return true; }
   template <class T> __device__ static __forceinline__ T pressure(const PP<T>& p, const T* q, T* u) {
     const T ir = T(1) / q[0];
@@ -264,6 +270,7 @@ template <int D> struct Phys<2, D> {
 template <> struct Phys<3, 2> {
   static constexpr int V = 3;
   static constexpr bool linear = false;
+  static constexpr int NG = 0;  // no non-conservative product
   __host__ __device__ static constexpr bool nz(int, int) { return true; }
   template <class T> __device__ static __forceinline__ void flux(const PP<T>& p, const T* q, T (*F)[V]) {
     const T ih = T(1) / q[0];
@@ -275,6 +282,64 @@ template <> struct Phys<3, 2> {
     F[1][0] = q[2];
     F[1][1] = q[1] * v;
     F[1][2] = q[2] * v + ph;
+  }
+  template <class T> __device__ static __forceinline__ T speed(const PP<T>& p, const T* q, int dir) {
+    return tabs(q[1 + dir] / q[0]) + tsqrt(p.g * q[0]);
+  }
+  template <class T> __device__ static __forceinline__ T maxspeed(const PP<T>& p, const T* q) {
+    return tmax(tabs(q[1]), tabs(q[2])) / q[0] + tsqrt(p.g * q[0]);
+  }
+  __device__ static __forceinline__ bool speed_is_ill_conditioned(const float* q) { return !(q[0] > 0.0f); }
+};
+
+// ---- shallow water with bathymetry, eq. (swe_canonical): Q = (h, hu, hv, b) -----------------
+// Conservative fluxes of eq. (swe_cons) without the hydrostatic pressure, which enters through
+// the non-conservative product of eq. (swe_noncons): B_dir(Q) grad Q = g h d(h + b)/dx_dir in
+// the momentum along dir.  b has neither flux nor product (it never changes).
+template <> struct Phys<4, 2> {
+  static constexpr int V = 4;
+  static constexpr bool linear = false;
+  static constexpr int NG = 2;                    // the product needs grad h and grad b
+  __host__ __device__ static constexpr int gvar(int g) { return g == 0 ? 0 : 3; }
+  __host__ __device__ static constexpr bool nz(int, int v) { return v < 3; }
+  template <class T> __device__ static __forceinline__ void flux(const PP<T>& p, const T* q, T (*F)[V]) {
+    const T ih = T(1) / q[0];
+    const T u = q[1] * ih, v = q[2] * ih;
+    F[0][0] = q[1];
+    F[0][1] = q[1] * u;
+    F[0][2] = q[2] * u;
+    F[0][3] = T(0);
+    F[1][0] = q[2];
+    F[1][1] = q[1] * v;
+    F[1][2] = q[2] * v;
+    F[1][3] = T(0);
+  }
+  // out[v] = (B_dir(q) dq)_v for every dir, from grad[dir][g] = d(q[gvar(g)])/dx_dir
+  template <class T> __device__ static __forceinline__ void ncp(const PP<T>& p, const T* q, const T (*grad)[NG],
+                                                                T* out) {
+    out[0] = T(0);
+    out[3] = T(0);
+    out[1] = p.g * q[0] * grad[0][0] + p.g * q[0] * grad[0][1];
+    out[2] = p.g * q[0] * grad[1][0] + p.g * q[0] * grad[1][1];
+  }
+  // Face flux of eq. (swe_custom_riemann) for one side: Rusanov with the dissipation acting on
+  // the surface elevation h + b (none on b), plus half the path integral of B across the face
+  // (straight path: g (h- + h+)/2 (eta+ - eta-) in the normal momentum), added by the face's
+  // minus cell and subtracted by its plus cell.  Tm, Tp: [V][NF] time-averaged traces.
+  template <class T>
+  __device__ static __forceinline__ T face_flux(const PP<T>& p, const T* Tm, const T* Tp, int NF, int j, int v,
+                                                int dir, bool minus_cell, T s, T Fm, T Fp) {
+    const T half = tcast<T>(0.5);
+    const T hm = Tm[j], hp = Tp[j], bm = Tm[3 * NF + j], bp = Tp[3 * NF + j];
+    T jump = Tm[v * NF + j] - Tp[v * NF + j];
+    if (v == 0) jump = (hm + bm) - (hp + bp);
+    if (v == 3) jump = T(0);
+    T G = half * (Fm + Fp) + half * s * jump;
+    if (v == 1 + dir) {
+      const T dh = half * p.g * (half * (hm + hp)) * ((hp + bp) - (hm + bm));
+      G = minus_cell ? G + dh : G - dh;
+    }
+    return G;
   }
   template <class T> __device__ static __forceinline__ T speed(const PP<T>& p, const T* q, int dir) {
     return tabs(q[1 + dir] / q[0]) + tsqrt(p.g * q[0]);

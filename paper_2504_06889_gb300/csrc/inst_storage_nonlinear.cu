@@ -8,5 +8,7 @@ void register_storage_nonlinear() {
   register_storage(make_storage_entry<2, 3, 2>());
   register_storage(make_storage_entry<3, 2, 4>());  // shallow water 2D, N = 4 (modes)
   register_storage(make_storage_entry<3, 2, 2>());
+  register_storage(make_storage_entry<4, 2, 5>());  // shallow water with bathymetry (lake)
+  register_storage(make_storage_entry<4, 2, 2>());
 }
 }  // namespace adg

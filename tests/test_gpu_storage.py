@@ -4,8 +4,9 @@ oracle with the same storage format.
 Both sides round the same FP64 sums to the format after each traversal.  The sums agree to
 FP64 rounding order (about 1e-16 relative), so a stored value can land one unit of the
 format's last place (ulp) apart where the exact sum sits next to a rounding boundary.  So:
-  * one step from the same stored state: every element equal, or one ulp apart, and at least
-    99% of them equal;
+  * one step from the same stored state: every element equal, or one ulp apart (or, for
+    values at the FP64 rounding-noise level, within 1e-12 max|Q|), and at least 99% of the
+    values above that level equal;
   * several steps with FP64 kernels: relative eq.-(L2gauss) distance <= steps * 2^-p;
   * FP32 kernels: relative distance <= 1e-5 + steps * 2^-p (p the format's significand bits).
 """
@@ -42,6 +43,9 @@ CASES = [
     I.euler3d_wave(N=5).with_cells((2, 2, 2), 2),
     I.swe2d_modes(N=4).with_cells((7, 3), 3),          # 21 cells, 5 per block: ragged tail
     I.swe2d_modes(N=2).with_cells((5, 4), 3),
+    I.Workload("lake", 2, 5, (4, 3), I.SWE_B, (9.81,), I.SC_LAKE, I.lake(nmodes=3, amp=0.05), 3,
+               has_exact=False),
+    I.swe2d_lake(m=4, N=2, steps=3),
 ]
 IDS = [f"{w.name.split('_')[0]}_N{w.N}_{'x'.join(map(str, w.cells))}" for w in CASES]
 
@@ -75,9 +79,12 @@ def test_one_step_equal_or_one_ulp(adg, oracle_mod, wl, fmt):
     assert dtg == dt or abs(dtg - dt) <= 1e-15 * dt
     Qg = s.state()
     np.testing.assert_array_equal(oracle_mod.round_format(Qg, fmt), Qg)  # representable
+    # values that are FP64 rounding noise (a lake at rest has zero velocity) differ by that
+    # noise, which a format with a wide exponent range can hold
     diff = np.abs(Qg - Qo)
-    assert np.all(diff <= ulp(Qo, fmt)), diff.max()
-    assert np.mean(diff == 0) >= 0.99
+    assert np.all(diff <= np.maximum(ulp(Qo, fmt), 1e-12 * np.abs(Qo).max())), diff.max()
+    real = np.abs(Qo) > 1e-10 * np.abs(Qo).max()
+    assert np.mean(diff[real] == 0) >= 0.99
 
 
 @pytest.mark.parametrize("fmt", ["fp32", "bf16", "fp16"])
