@@ -6,7 +6,7 @@ FP64 rounding order (about 1e-16 relative), so a stored value can land one unit 
 format's last place (ulp) apart where the exact sum sits next to a rounding boundary.  So:
   * one step from the same stored state: every element equal, or one ulp apart (or, for
     values at the FP64 rounding-noise level, within 1e-12 max|Q|), and at least 99% of the
-    values above that level equal;
+    values above 1e-6 max|Q| equal;
   * several steps with FP64 kernels: relative eq.-(L2gauss) distance <= steps * 2^-p;
   * FP32 kernels: relative distance <= 1e-5 + steps * 2^-p (p the format's significand bits).
 """
@@ -83,7 +83,9 @@ def test_one_step_equal_or_one_ulp(adg, oracle_mod, wl, fmt):
     # noise, which a format with a wide exponent range can hold
     diff = np.abs(Qg - Qo)
     assert np.all(diff <= np.maximum(ulp(Qo, fmt), 1e-12 * np.abs(Qo).max())), diff.max()
-    real = np.abs(Qo) > 1e-10 * np.abs(Qo).max()
+    # values far below the state's scale come from cancellation (the velocities of a lake at
+    # rest): FP64 rounding-order differences are a larger part of them, so they are left out
+    real = np.abs(Qo) > 1e-6 * np.abs(Qo).max()
     assert np.mean(diff[real] == 0) >= 0.99
 
 
