@@ -33,6 +33,7 @@ _lib = None
 ACOUSTIC, ELASTIC, EULER, SWE, SWE_B = 0, 1, 2, 3, 4
 STORAGE = {"fp64": 0, "fp32": 1, "bf16": 2, "fp16": 3}
 SC_PLANAR, SC_EULER_WAVE, SC_SWE_MODES, SC_GAUSS_PULSE, SC_LAKE = 0, 1, 2, 3, 4
+SC_EULER_BELL, SC_EULER_VORTEX = 5, 6
 
 
 def build(force: bool = False) -> str:

@@ -360,6 +360,47 @@ void or_exact(const or_mesh* M, int scen, const double* sp, int nsp, const doubl
     const double* p = sp + 5;
     for (int j = 0; j < nm; ++j, p += 4) h += p[0] * sin(p[1] * x[0] + p[2] * x[1] + p[3]);
     Q[0] = h;
+  } else if (scen == OR_SC_EULER_BELL) {
+    /* Sec. 4.3.1: sp = [rho0, amp, width, x0, y0, ux, uy, p0]; rho = rho0 (1 + amp
+     * exp(-width |x - x0 - u t|^2)) (the squared exponent of the figure; nearest periodic
+     * image), velocity u, pressure p0: an exact solution of the Euler equations */
+    double gamma = M->pp[0], r2 = 0.0, u2 = 0.0;
+    for (int a = 0; a < 2; ++a) {
+      double L = M->h[a] * M->m[a];
+      double dx = x[a] - sp[3 + a] - sp[5 + a] * t;
+      dx -= L * floor(dx / L + 0.5);
+      r2 += dx * dx;
+      u2 += sp[5 + a] * sp[5 + a];
+    }
+    double rho = sp[0] * (1.0 + sp[1] * exp(-sp[2] * r2));
+    Q[0] = rho;
+    Q[1] = rho * sp[5];
+    Q[2] = rho * sp[6];
+    Q[3] = sp[7] / (gamma - 1.0) + 0.5 * rho * u2;
+  } else if (scen == OR_SC_EULER_VORTEX) {
+    /* Sec. 4.3.2 (Hu and Shu's isentropic vortex): sp = [rho_inf, p_inf, beta, x0, y0, u_inf,
+     * v_inf]; with r the distance to the centre x0 + u_inf t (nearest periodic image):
+     * dT = (1 - gamma) beta^2 / (8 gamma pi^2) e^(1 - r^2), rho = rho_inf + (1 + dT)^(1/(gamma-1))
+     * - 1, p = p_inf + (1 + dT)^(gamma/(gamma-1)) - 1 (the printed dp repeats drho; this is the
+     * isentropic form, p / rho^gamma = 1 for rho_inf = p_inf = 1), (du, dv) = beta / (2 pi)
+     * e^((1 - r^2)/2) (-y, x) */
+    double gamma = M->pp[0], d[2], r2 = 0.0;
+    for (int a = 0; a < 2; ++a) {
+      double L = M->h[a] * M->m[a];
+      d[a] = x[a] - sp[3 + a] - sp[5 + a] * t;
+      d[a] -= L * floor(d[a] / L + 0.5);
+      r2 += d[a] * d[a];
+    }
+    const double pi = 3.14159265358979323846;
+    double dT = (1.0 - gamma) * sp[2] * sp[2] / (8.0 * gamma * pi * pi) * exp(1.0 - r2);
+    double rho = sp[0] + (pow(1.0 + dT, 1.0 / (gamma - 1.0)) - 1.0);
+    double p = sp[1] + (pow(1.0 + dT, gamma / (gamma - 1.0)) - 1.0);
+    double f = sp[2] / (2.0 * pi) * exp(0.5 * (1.0 - r2));
+    double u = sp[5] - d[1] * f, v = sp[6] + d[0] * f;
+    Q[0] = rho;
+    Q[1] = rho * u;
+    Q[2] = rho * v;
+    Q[3] = p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v);
   } else if (scen == OR_SC_LAKE) {
     /* eq. (lake_initial) with an optional disturbed surface: sp = [eta0, b0, ab, kbx, kby,
      * nm, {a, kx, ky, phi} x nm]; b = b0 + ab sin(kbx x + kby y), eta = eta0 + sum a

@@ -39,7 +39,15 @@ enum { OR_ACOUSTIC = 0, OR_ELASTIC = 1, OR_EULER = 2, OR_SWE = 3, OR_SWE_B = 4 }
 /* storage formats of Table precision_bits: significand bits p (with the hidden bit),
  * smallest normal exponent, largest exponent */
 enum { OR_ST_FP64 = 0, OR_ST_FP32 = 1, OR_ST_BF16 = 2, OR_ST_FP16 = 3 };
-enum { OR_SC_PLANAR = 0, OR_SC_EULER_WAVE = 1, OR_SC_SWE_MODES = 2, OR_SC_GAUSS_PULSE = 3, OR_SC_LAKE = 4 };
+enum {
+  OR_SC_PLANAR = 0,
+  OR_SC_EULER_WAVE = 1,
+  OR_SC_SWE_MODES = 2,
+  OR_SC_GAUSS_PULSE = 3,
+  OR_SC_LAKE = 4,
+  OR_SC_EULER_BELL = 5,  /* Sec. 4.3.1: advected Gaussian density bell */
+  OR_SC_EULER_VORTEX = 6 /* Sec. 4.3.2: isentropic vortex */
+};
 
 typedef struct {
   int dim, N, n, nvar, pde;

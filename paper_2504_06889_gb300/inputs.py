@@ -27,6 +27,7 @@ import numpy as np
 
 ACOUSTIC, ELASTIC, EULER, SWE, SWE_B = 0, 1, 2, 3, 4
 SC_PLANAR, SC_EULER_WAVE, SC_SWE_MODES, SC_GAUSS_PULSE, SC_LAKE = 0, 1, 2, 3, 4
+SC_EULER_BELL, SC_EULER_VORTEX = 5, 6
 PDE_NAMES = {ACOUSTIC: "acoustic", ELASTIC: "elastic", EULER: "euler", SWE: "swe",
              SWE_B: "swe_bathymetry"}
 
@@ -114,6 +115,17 @@ def lake(eta0=2.0, b0=0.0, ab=1.0, kb=(2 * np.pi, 2 * np.pi), nmodes=0, amp=1e-2
     return np.asarray(out, dtype=np.float64)
 
 
+def euler_bell(rho0=0.02, amp=1.0, width=50.0, x0=(0.0, 0.0), u=(1.0, 1.0), p0=1.0):
+    """Advected Gaussian density bell (Sec. 4.3.1): rho = rho0 (1 + amp exp(-width |x - x0 -
+    u t|^2)), velocity u, pressure p0."""
+    return np.asarray([rho0, amp, width, x0[0], x0[1], u[0], u[1], p0], dtype=np.float64)
+
+
+def euler_vortex(rho_inf=1.0, p_inf=1.0, beta=5.0, x0=(0.0, 0.0), u=(0.0, 0.0)):
+    """Isentropic vortex (Sec. 4.3.2) centred at x0, carried with the velocity u."""
+    return np.asarray([rho_inf, p_inf, beta, x0[0], x0[1], u[0], u[1]], dtype=np.float64)
+
+
 def gauss_pulse(seed=5, sigma=0.05, amp=1.0, dim=3):
     rng = np.random.default_rng(seed)
     x0 = list(rng.uniform(0.25, 0.75, size=dim)) + [0.0] * (3 - dim)
@@ -166,6 +178,8 @@ class Workload:
     steps: int
     cfl: float = -1.0  # < 0: 0.9 times the stability limit for N
     has_exact: bool = True
+    lo: tuple = None   # domain box (None: the unit box)
+    hi: tuple = None
 
     def __post_init__(self):
         if self.cfl < 0:
@@ -225,6 +239,19 @@ def swe2d_lake(m=27, N=5, steps=200, eta0=2.0, b0=0.0):
                     lake(eta0, b0), steps)
 
 
+def euler2d_bell(m=27, N=5, steps=100):
+    """2D Euler, gamma = 1.4, the density bell of Sec. 4.3.1 on [-1, 1]^2 (one traversal of
+    the domain per unit time)."""
+    return Workload("eulerbell_N%d_%dx%d" % (N, m, m), 2, N, (m, m), EULER, (1.4,), SC_EULER_BELL,
+                    euler_bell(), steps, lo=(-1.0, -1.0), hi=(1.0, 1.0))
+
+
+def euler2d_vortex(m=27, N=5, steps=100):
+    """2D Euler, gamma = 1.4, the static isentropic vortex of Sec. 4.3.2 on [-5, 5]^2."""
+    return Workload("eulervortex_N%d_%dx%d" % (N, m, m), 2, N, (m, m), EULER, (1.4,), SC_EULER_VORTEX,
+                    euler_vortex(), steps, lo=(-5.0, -5.0), hi=(5.0, 5.0))
+
+
 def acoustic3d_pulse(m=32, N=4, steps=100, seed=5):
     """3D acoustics, rho = 1, c = 1, Gaussian pressure pulse (sigma = 0.05) at a seeded spot."""
     return Workload("acoustic3d_N%d_%d^3" % (N, m), 3, N, (m, m, m), ACOUSTIC, (1.0, 1.0),
@@ -253,5 +280,7 @@ WORKLOADS = {
     "elastic3d": elastic3d_planar,
     "swe2d": swe2d_modes,
     "swelake": swe2d_lake,
+    "eulerbell": euler2d_bell,
+    "eulervortex": euler2d_vortex,
     "acoustic3d": acoustic3d_pulse,
 }
