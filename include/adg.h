@@ -102,13 +102,24 @@ enum adg_flags {
  *  ADG_SC_LAKE        [eta0, b0, ab, kbx, kby, nm, {a, kx, ky, phi} x nm] (ADG_SWE_B):
  *                     b = b0 + ab sin(kbx x + kby y), eta = eta0 + sum a sin(kx x + ky y + phi),
  *                     h = eta - b, v = 0 (eq. lake_initial); nm = 0 is the lake at rest, whose
- *                     closed form is the initial state at every t; otherwise t = 0 only */
+ *                     closed form is the initial state at every t; otherwise t = 0 only
+ *  ADG_SC_EULER_BELL  [rho0, amp, width, x0, y0, ux, uy, p0] (2D Euler, Sec. 4.3.1):
+ *                     rho = rho0 (1 + amp exp(-width |x - x0 - u t|^2)), velocity u,
+ *                     pressure p0; nearest periodic image of the bell
+ *  ADG_SC_EULER_VORTEX [rho_inf, p_inf, beta, x0, y0, u_inf, v_inf] (2D Euler, Sec. 4.3.2):
+ *                     isentropic vortex of strength beta centred at x0 + u t:
+ *                     dT = (1 - gamma) beta^2 / (8 gamma pi^2) e^(1 - r^2),
+ *                     rho = rho_inf + (1 + dT)^(1/(gamma-1)) - 1,
+ *                     p = p_inf + (1 + dT)^(gamma/(gamma-1)) - 1,
+ *                     v = u + beta / (2 pi) e^((1 - r^2)/2) (-y, x) */
 enum adg_scenario {
   ADG_SC_PLANAR = 0,
   ADG_SC_EULER_WAVE = 1,
   ADG_SC_SWE_MODES = 2,
   ADG_SC_GAUSS_PULSE = 3,
-  ADG_SC_LAKE = 4
+  ADG_SC_LAKE = 4,
+  ADG_SC_EULER_BELL = 5,
+  ADG_SC_EULER_VORTEX = 6
 };
 
 /* Create / destroy a context bound to the current CUDA device. */

@@ -20,6 +20,7 @@ FP64, FP32, BF16, FP16, FP8E4M3 = 0, 1, 2, 3, 4
 F_COMPENSATED_LAST, F_PER_CELL_SCALE, F_COMPENSATED_TWO = 1, 2, 4
 PRED_PICARD, PRED_CK = 0, 1
 SC_PLANAR, SC_EULER_WAVE, SC_SWE_MODES, SC_GAUSS_PULSE, SC_LAKE = 0, 1, 2, 3, 4
+SC_EULER_BELL, SC_EULER_VORTEX = 5, 6
 PREC_NAMES = {"fp64": FP64, "fp32": FP32, "bf16": BF16, "fp16": FP16, "fp8": FP8E4M3, "fp8e4m3": FP8E4M3}
 
 _lib = None

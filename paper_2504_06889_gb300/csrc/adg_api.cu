@@ -33,6 +33,7 @@ void register_euler();
 void register_elastic();
 void register_swe();
 void register_swe_bathymetry();
+void register_euler2d();
 void register_storage_linear();
 void register_storage_nonlinear();
 
@@ -44,6 +45,7 @@ static void ensure_registry() {
     register_elastic();
     register_swe();
     register_swe_bathymetry();
+    register_euler2d();
     register_storage_linear();
     register_storage_nonlinear();
   });
@@ -524,7 +526,7 @@ static int reset_scalars_and_lambda(adg_ctx* c, double t) {
 int adg_set_initial(adg_ctx* c, int scenario, const double* params, int nparams) {
   if (!c) return ADG_EINVAL;
   if (!c->have_bufs || !c->entry) return fail(c, ADG_ENOTINIT, "bind buffers first");
-  if (scenario < ADG_SC_PLANAR || scenario > ADG_SC_LAKE) return fail(c, ADG_EINVAL, "unknown scenario");
+  if (scenario < ADG_SC_PLANAR || scenario > ADG_SC_EULER_VORTEX) return fail(c, ADG_EINVAL, "unknown scenario");
   if (!params || nparams < 1) return fail(c, ADG_EINVAL, "missing scenario parameters");
   // validate the encodings' lengths
   int need = 0;
@@ -538,6 +540,9 @@ int adg_set_initial(adg_ctx* c, int scenario, const double* params, int nparams)
     if (c->pde != ADG_SWE) return fail(c, ADG_EINVAL, "swe modes need the SWE PDE");
     if (nparams < 5) return fail(c, ADG_EINVAL, "swe modes: too few parameters");
     need = 5 + 4 * (int)params[4];
+  } else if (scenario == ADG_SC_EULER_BELL || scenario == ADG_SC_EULER_VORTEX) {
+    if (c->pde != ADG_EULER || c->dim != 2) return fail(c, ADG_EINVAL, "bell and vortex need 2D Euler");
+    need = scenario == ADG_SC_EULER_BELL ? 8 : 7;
   } else if (scenario == ADG_SC_LAKE) {
     if (c->pde != ADG_SWE_B) return fail(c, ADG_EINVAL, "the lake needs the SWE form with bathymetry");
     if (nparams < 6) return fail(c, ADG_EINVAL, "lake: too few parameters");

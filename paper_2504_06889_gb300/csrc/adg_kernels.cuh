@@ -887,6 +887,42 @@ __device__ void exact_solution(int scen, const double* sp, const PdeParams& pp, 
     const int nm = (int)sp[4];
     for (int j = 0; j < nm; ++j) h += sp[5 + 4 * j] * sin(sp[6 + 4 * j] * x[0] + sp[7 + 4 * j] * x[1] + sp[8 + 4 * j]);
     Q[0] = h;
+  } else if (scen == 5) {  // advected density bell (Sec. 4.3.1), nearest periodic image
+    if constexpr (D == 2 && V == 4) {
+      double r2 = 0.0, u2 = 0.0;
+#pragma unroll
+      for (int d = 0; d < 2; ++d) {
+        double dx = x[d] - sp[3 + d] - sp[5 + d] * t;
+        dx -= L[d] * floor(dx / L[d] + 0.5);
+        r2 += dx * dx;
+        u2 += sp[5 + d] * sp[5 + d];
+      }
+      const double rho = sp[0] * (1.0 + sp[1] * exp(-sp[2] * r2));
+      Q[0] = rho;
+      Q[1] = rho * sp[5];
+      Q[2] = rho * sp[6];
+      Q[3] = sp[7] / (pp.gamma - 1.0) + 0.5 * rho * u2;
+    }
+  } else if (scen == 6) {  // isentropic vortex (Sec. 4.3.2), isentropic pressure
+    if constexpr (D == 2 && V == 4) {
+      double dd[2], r2 = 0.0;
+#pragma unroll
+      for (int d = 0; d < 2; ++d) {
+        dd[d] = x[d] - sp[3 + d] - sp[5 + d] * t;
+        dd[d] -= L[d] * floor(dd[d] / L[d] + 0.5);
+        r2 += dd[d] * dd[d];
+      }
+      const double g = pp.gamma, pi = 3.14159265358979323846;
+      const double dT = (1.0 - g) * sp[2] * sp[2] / (8.0 * g * pi * pi) * exp(1.0 - r2);
+      const double rho = sp[0] + (pow(1.0 + dT, 1.0 / (g - 1.0)) - 1.0);
+      const double pr = sp[1] + (pow(1.0 + dT, g / (g - 1.0)) - 1.0);
+      const double f = sp[2] / (2.0 * pi) * exp(0.5 * (1.0 - r2));
+      const double u = sp[5] - dd[1] * f, v = sp[6] + dd[0] * f;
+      Q[0] = rho;
+      Q[1] = rho * u;
+      Q[2] = rho * v;
+      Q[3] = pr / (g - 1.0) + 0.5 * rho * (u * u + v * v);
+    }
   } else if (scen == 4) {  // lake over sinusoidal bathymetry, eq. (lake_initial), optional modes
     const double b = sp[1] + sp[2] * sin(sp[3] * x[0] + sp[4] * x[1]);
     double eta = sp[0];

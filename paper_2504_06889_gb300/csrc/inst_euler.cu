@@ -9,7 +9,6 @@ void register_euler() {
     add_tc<2, 3, 5>(e);
     register_entry(e);
   }  // 3D, N = 5 (density-wave workload)
-  register_entry(make_entry<2, 2, 3, false>());
   {
     Entry e = make_entry<2, 3, 2, false>();
     add_tc<2, 3, 2>(e);

@@ -6,6 +6,7 @@ namespace adg {
 void register_storage_nonlinear() {
   register_storage(make_storage_entry<2, 3, 5>());  // Euler 3D, N = 5 (density wave)
   register_storage(make_storage_entry<2, 3, 2>());
+  register_storage(make_storage_entry<2, 2, 5>());  // Euler 2D, N = 5 (bell, vortex)
   register_storage(make_storage_entry<3, 2, 4>());  // shallow water 2D, N = 4 (modes)
   register_storage(make_storage_entry<3, 2, 2>());
   register_storage(make_storage_entry<4, 2, 5>());  // shallow water with bathymetry (lake)

@@ -1,10 +1,12 @@
 """Precision studies in the manner of Sec. 5: run one workload to a final time in several
 precision mixes through the C ABI and report the eq. (L2gauss) error against the closed form.
 
-``python -m paper_2504_06889_gb300.study lake`` prints the lake-at-rest table (shallow water
-with bathymetry, Sec. 4.4: 27^2 cells, order 5, eta0 = 2, t = 1), the scenario the paper finds
-most sensitive to precision: per-kernel precisions with FP64 storage, and storage precisions
-with FP64 or FP32 kernels.
+``python -m paper_2504_06889_gb300.study lake|bell|vortex [t_end]`` prints the table of one
+scenario on the paper's mesh (27^2 cells, order 5): per-kernel precisions with FP64 storage,
+and storage precisions with FP64 or FP32 kernels.  lake: the lake at rest (shallow water with
+bathymetry, Sec. 4.4, eta0 = 2, t = 1), the scenario the paper finds most sensitive to
+precision; bell: the advected density bell (2D Euler, Sec. 4.3.1, t = 2); vortex: the static
+isentropic vortex (Sec. 4.3.2, t = 10).
 """
 from __future__ import annotations
 
@@ -48,8 +50,8 @@ def run_to_time(wl, t_end, precision=None, flags=0, scheme="picard", chunk=256):
     finite."""
     from . import adg
 
-    s = adg.Solver(wl.dim, wl.N, wl.cells, wl.pde, wl.params, cfl=wl.cfl, precision=precision,
-                   flags=flags, scheme=scheme)
+    s = adg.Solver(wl.dim, wl.N, wl.cells, wl.pde, wl.params, lo=wl.lo, hi=wl.hi, cfl=wl.cfl,
+                   precision=precision, flags=flags, scheme=scheme)
     try:
         s.set_initial(wl.scenario, wl.sp)
         t, dt = s.time()
@@ -74,22 +76,36 @@ def run_to_time(wl, t_end, precision=None, flags=0, scheme="picard", chunk=256):
         s.close()
 
 
-def lake_table(t_end=1.0, m=27, N=5, eta0=2.0, b0=0.0, mixes=LAKE_MIXES):
-    wl = I.swe2d_lake(m=m, N=N, eta0=eta0, b0=b0)
+def table(wl, t_end, mixes=LAKE_MIXES):
     rows = []
     for label, prec in mixes:
         r = run_to_time(wl, t_end, precision=prec)
         r["mix"] = label
         rows.append(r)
-    return {"workload": wl.name, "t_end": t_end, "eta0": eta0, "rows": rows}
+    return {"workload": wl.name, "t_end": t_end, "rows": rows}
+
+
+def lake_table(t_end=1.0, m=27, N=5, eta0=2.0, b0=0.0, mixes=LAKE_MIXES):
+    out = table(I.swe2d_lake(m=m, N=N, eta0=eta0, b0=b0), t_end, mixes)
+    out["eta0"] = eta0
+    return out
+
+
+# the 2D Euler scenarios of Sec. 4.3 on the paper's mesh and end times
+SCENARIOS = {
+    "lake": (lambda: I.swe2d_lake(), 1.0),
+    "bell": (lambda: I.euler2d_bell(), 2.0),
+    "vortex": (lambda: I.euler2d_vortex(), 10.0),
+}
 
 
 def main(argv):
-    if not argv or argv[0] != "lake":
+    if not argv or argv[0] not in SCENARIOS:
         print(__doc__)
         return 2
-    t_end = float(argv[1]) if len(argv) > 1 else 1.0
-    out = lake_table(t_end)
+    make, t_default = SCENARIOS[argv[0]]
+    t_end = float(argv[1]) if len(argv) > 1 else t_default
+    out = table(make(), t_end)
     for r in out["rows"]:
         l2 = "NaN" if not r["finite"] else ("%.3e" % r["l2"])
         print("%-26s steps %6d  t %.4f  L2 %s" % (r["mix"], r["steps"], r["t"], l2))
