@@ -1,10 +1,13 @@
-// Tensor-core (tcgen05) predictor for the 16-bit Picard mixes: the derivative contractions of
+// Tensor-core (tcgen05) predictor, one MMA round per time slice: the derivative contractions of
 // every Picard sweep (eq. Picard, R = sum_dir D_dir F_dir(q)) run as small GEMMs on the 5th
-// generation tensor cores with bf16 or fp16 inputs and FP32 accumulation in tensor memory; the
-// pointwise fluxes, the time operator and the final stage stay on the FP32 pipes.
+// generation tensor cores with bf16, fp16 or E4M3 inputs and FP32 accumulation in tensor memory;
+// the pointwise fluxes, the time operator and the final stage stay on the FP32 pipes.  It serves
+// the E4M3 mixes and the PDEs with more than five variables (3D elasticity); the 16-bit mixes of
+// the other 3D PDEs use the sweep-batched kernel of adg_tc_sweep.cuh.
 //
 // Data flow per time slice k of a sweep (one CTA per cell, one thread per spatial node):
-//  1. each node computes F_dir(q_k) (FP32), scales it by the cell's power of two and writes it as
+//  1. each node computes F_dir(q_k) - F_c (FP32; F_c is the flux at the cell's first node, whose
+//     derivative is zero), scales it by the cell's power of two and writes it as
 //     a 16-bit value into the A operand of direction dir: row = (v, pencil p mod NPP), column =
 //     (p / NPP) * 8 + position along the pencil (K-major, 8x8 core matrices, no swizzle);
 //  2. one thread issues, per direction and 128-row tile, tcgen05.mma with B = diag(D, D)
@@ -182,6 +185,7 @@ __global__ void __launch_bounds__(TcCfg<C, TIN>::THREADS)
   __shared__ __align__(8) uint64_t s_mbar;
   __shared__ uint32_t s_tmem;
   __shared__ uint32_t s_fmax[2], s_timeout;
+  __shared__ float s_fc[C::D][C::V];  // flux offset of the cell: F(Q) at its node 0
   __shared__ double s_dt;
   if (a.sc->bad) return;
   const double dt = block_dt(a, D, C::N, &s_dt);
@@ -271,9 +275,25 @@ __global__ void __launch_bounds__(TcCfg<C, TIN>::THREADS)
       for (int v = 0; v < V; ++v) m = fmaxf(m, fabsf(F[dir][v]));
     return m;
   };
+  // The derivative of a constant is zero, so the operands hold F - F_c with F_c the flux at the
+  // cell's first node: the low-precision rounding applies to the flux's variation over the cell,
+  // not to its much larger mean, which would cancel in the contraction.
+  if (tid == 0) {
+    T F[D][V];
+    Ph::flux(pp, Qh, F);
+#pragma unroll
+    for (int dir = 0; dir < D; ++dir)
+#pragma unroll
+      for (int v = 0; v < V; ++v) s_fc[dir][v] = F[dir][v];
+  }
+  __syncthreads();
   if (owner) {
     T F[D][V];
     Ph::flux(pp, Qh, F);
+#pragma unroll
+    for (int dir = 0; dir < D; ++dir)
+#pragma unroll
+      for (int v = 0; v < V; ++v) F[dir][v] -= s_fc[dir][v];
     atomicMax(&s_fmax[1], __float_as_uint(fmax_of(F)));
   }
   tc::fence_async_smem();
@@ -321,6 +341,10 @@ __global__ void __launch_bounds__(TcCfg<C, TIN>::THREADS)
       if (owner) {
         T F[D][V];
         Ph::flux(pp, q[k], F);
+#pragma unroll
+        for (int dir = 0; dir < D; ++dir)
+#pragma unroll
+          for (int v = 0; v < V; ++v) F[dir][v] -= s_fc[dir][v];
         atomicMax(&s_fmax[r & 1], __float_as_uint(fmax_of(F)));
 #pragma unroll
         for (int dir = 0; dir < D; ++dir)

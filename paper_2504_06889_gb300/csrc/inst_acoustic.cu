@@ -2,6 +2,7 @@
 #include "adg_kernels.cuh"
 #include "adg_tc.cuh"
 #include "adg_adjoint.cuh"
+#include "adg_tc_sweep.cuh"
 
 namespace adg {
 template <int D, int N>
@@ -22,6 +23,7 @@ void register_acoustic() {
   {
     Entry e = make_entry<0, 3, 4, false>();
     add_tc<0, 3, 4>(e);
+    add_tcs<0, 4>(e);
     add_ck<0, 3, 4>(e);
     add_adjoint<3, 4>(e);
     register_entry(e);
@@ -34,6 +36,7 @@ void register_acoustic() {
   {
     Entry e = make_entry<0, 3, 2, false>();
     add_tc<0, 3, 2>(e);
+    add_tcs<0, 2>(e);
     add_ck<0, 3, 2>(e);
     add_adjoint<3, 2>(e);
     register_entry(e);
