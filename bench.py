@@ -126,6 +126,16 @@ def predictor_bytes_per_cell(pde, dim, N, trace_bytes, state_bytes=8):
     return 2 * state_bytes * n ** dim * V + 2 * dim * 2 * V * n ** (dim - 1) * trace_bytes
 
 
+# DRAM bytes per cell of one predictor launch, from one ncu capture of the same kernel on a
+# 32^3 case of the workload (dram__bytes_read.sum + dram__bytes_write.sum divided by the cells);
+# the traffic of a launch is proportional to its cells.  Only valid while the kernel is
+# unchanged since the capture (the profile named beside it).
+MEASURED_TRAFFIC = {
+    ("euler3d_N5_64^3", "fp32"): (791.747e6 / 32768, "profiles/k_predictor_fp32_euler3d_N5_32cubed.md"),
+    ("euler3d_N5_64^3", "bf16tc"): (797.131e6 / 32768, "profiles/k_predictor_tcs_bf16_euler3d_N5_32cubed.md"),
+}
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -397,9 +407,14 @@ def main():
         sm_mhz = peaks.get("sm_max_mhz", 2070.0)
         pk = alu_peak_tflops(kind, sm_mhz)
         ach = fl / (ms_pred / args.steps * 1e-3) / 1e12
+        tr = MEASURED_TRAFFIC.get((wl.name, mix)) if wl.name.endswith(f"{wl.cells[0]}^{wl.dim}") else None
         r["roofline"] = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
-                         "frac": ach / pk, "traffic": None,
-                         "kernel": "k_predictor", "peak_source": f"{kind} ALU derived at {sm_mhz:.0f} MHz"}
+                         "frac": ach / pk, "traffic": tr[0] * cells if tr else None,
+                         "kernel": "k_predictor_tcs" if mix in ("bf16tc", "fp16tc") and wl.pde != I.ELASTIC
+                         else "k_predictor_tc" if "tc" in mix else "k_predictor",
+                         "peak_source": f"{kind} ALU derived at {sm_mhz:.0f} MHz"}
+        if tr:
+            r["roofline"]["traffic_source"] = f"ncu capture on 32^3 cells scaled by the cells ({tr[1]})"
         tb = {"fp64": 8, "fp32": 4, "bf16": 2}[prec["corrector"]]
         sb = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}[prec.get("storage", "fp64")]
         bts = predictor_bytes_per_cell(wl.pde, wl.dim, wl.N, tb, sb) * cells

@@ -183,6 +183,16 @@ bool build_tables(int n, Tables* T) {
   return true;
 }
 
+void finalize_step_args(StepArgs* a) {
+  for (int side = 0; side < 2; ++side)
+    for (int d = 0; d < 3; ++d)
+      for (int i = 0; i < a->tab.n && i < kMaxN1; ++i) {
+        const double c = (side ? a->tab.psi1[i] : a->tab.psi0[i]) * a->invh[d] / a->tab.w[i];
+        a->surf[side][d][i] = c;
+        a->fsurf[side][d][i] = (float)c;
+      }
+}
+
 void finalize_pde_params(PdeParams* p) {
   p->irho = p->rho > 0 ? 1.0 / p->rho : 0.0;
   p->lam2mu = p->lam + 2.0 * p->mu;
@@ -313,6 +323,7 @@ static void fill_step_args(const adg_ctx* c, StepArgs* a) {
   a->per_cell_scale = (c->flags & ADG_F_PER_CELL_SCALE) ? 1 : 0;
   a->tab = c->tab;
   a->pp = c->pp;
+  finalize_step_args(a);
 }
 
 extern "C" {

@@ -47,6 +47,8 @@ struct DevScalars {
   unsigned int steps;           // good steps taken since the state was set
   unsigned int timeout;         // a bounded device wait ran out (tensor-core predictor)
   unsigned int pad_;
+  double dt_cur;                // dt of the next step from lam_cur (set by the corrector's last
+                                // block); 0 until known, then every block derives it from lam_cur
 };
 
 struct StepArgs {
@@ -63,9 +65,14 @@ struct StepArgs {
   int comp_sweeps;     // tensor-core Picard: number of final sweeps with hi/lo compensation
   int per_cell_scale;  // tensor-core Picard: power-of-two scaling of the flux per cell
   int pad;
+  // surface-integral coefficients psi_side(xi_i) / (h_dir w_i) [side][dir][i], FP64 and rounded
+  // to FP32 (set by finalize_step_args)
+  double surf[2][3][kMaxN1];
+  float fsurf[2][3][kMaxN1];
   Tables tab;
   PdeParams pp;
 };
+void finalize_step_args(StepArgs* a);
 
 struct InitArgs {
   double* Q;

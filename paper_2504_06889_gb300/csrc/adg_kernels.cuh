@@ -41,15 +41,21 @@ template <int D, int n> __device__ __forceinline__ int node_of_face(int dir, int
   return j + n * n * a;
 }
 
-__device__ __forceinline__ double dt_from(const StepArgs& a, int D, int N) {
-  const double lam = __longlong_as_double((long long)a.sc->lam_cur);
+__device__ __forceinline__ double dt_of_lambda(const StepArgs& a, int D, int N, double lam) {
   return a.cfl * a.hmin / ((double)D * (2.0 * N + 1.0) * lam);
 }
+__device__ __forceinline__ double dt_from(const StepArgs& a, int D, int N) {
+  return dt_of_lambda(a, D, N, __longlong_as_double((long long)a.sc->lam_cur));
+}
 
-// dt of this step, computed by one thread and shared through shared memory (the FP64 division
-// is expensive on this part; every block computes the same value)
+// dt of this step, read by one thread and shared through shared memory.  The corrector's last
+// block stores it with lambda_max (one FP64 division per step); until then (the first step after
+// the state was set) every block divides, with the same result.
 __device__ __forceinline__ double block_dt(const StepArgs& a, int D, int N, double* s_dt) {
-  if (threadIdx.x == 0) *s_dt = dt_from(a, D, N);
+  if (threadIdx.x == 0) {
+    const double d = *(volatile const double*)&a.sc->dt_cur;
+    *s_dt = d > 0.0 ? d : dt_from(a, D, N);
+  }
   __syncthreads();
   return *s_dt;
 }
@@ -639,7 +645,10 @@ __global__ void __launch_bounds__(C::THREADS) k_corrector(const __grid_constant_
                                     CorrSmem<C, TR, TC>::sp);
   for (int t = threadIdx.x; t < 2 * D * n; t += blockDim.x) {
     const int id = t % n, dir = (t / n) % D, side = t / (n * D);
-    sCoef[t] = tcast<TC>((side ? a.tab.psi1[id] : a.tab.psi0[id]) * a.invh[dir] / a.tab.w[id]);
+    if constexpr (std::is_same<TC, float>::value)
+      sCoef[t] = a.fsurf[side][dir][id];
+    else
+      sCoef[t] = tcast<TC>(a.surf[side][dir][id]);
   }
 
   const TS* trc = reinterpret_cast<const TS*>(a.traces);
@@ -801,7 +810,9 @@ __global__ void __launch_bounds__(C::THREADS) k_corrector(const __grid_constant_
     } else {
       sc->t = sc->t + dt;
       sc->dt_last = dt;
-      sc->lam_cur = sc->lam_next;
+      const unsigned long long lam_bits = sc->lam_next;
+      sc->lam_cur = lam_bits;
+      sc->dt_cur = dt_of_lambda(a, D, C::N, __longlong_as_double((long long)lam_bits));  // next step's dt
       sc->steps = sc->steps + 1u;
     }
     sc->lam_next = 0ull;

@@ -56,6 +56,7 @@ __global__ void k_noalloc_reset(DevScalars* sc, double t) {
     sc->bad = 0u;
     sc->steps = 0u;
     sc->timeout = 0u;
+    sc->dt_cur = 0.0;
   }
 }
 
@@ -136,6 +137,7 @@ extern "C" int adg_step_noalloc(int pde, int dim, int order_N, const int* cells,
   a.hmin = hmin;
   a.cfl = cfl;
   a.picard_iters = picard_iters > 0 ? picard_iters : order_N + 1;
+  finalize_step_args(&a);
 
   k_noalloc_reset<<<1, 32, 0, s>>>(a.sc, *t_inout);
   if (cudaGetLastError() != cudaSuccess) return ADG_ECUDA;
