@@ -3,11 +3,11 @@
  *
  * The library advances a hyperbolic PDE system  Q_t + div F(Q) = 0  on a uniform
  * periodic Cartesian mesh with the one-step ADER-DG scheme of Marot-Lassauzaie &
- * Bader, arXiv 2504.06889 (Sec. 2, Algorithm 1): per cell a space-time predictor
+ * Bader, arXiv 2504.06889 (Sec. 3, Algorithm 1): per cell a space-time predictor
  * (eq. Picard, solved by Picard iteration), face extrapolation and the volume
  * integral; per face a Rusanov Riemann solve (eq. rusanov_flux); the surface
  * integral and the update of eq. (weak_form_volume_surface); the time step of
- * eq. (CFL_condition).  Precision is chosen per kernel, as in Sec. 3.1.
+ * eq. (CFL_condition).  Precision is chosen per kernel, as in Sec. 4.1.
  *
  * Conventions
  *  - Every call returns an adg_status.  On failure adg_last_error() describes it.
@@ -59,7 +59,7 @@ enum adg_status {
   ADG_ENOMEM = -7        /* workspace smaller than adg_workspace_bytes() */
 };
 
-/* PDE systems of Sec. 4 (eq. acoustic, lin_elastic, euler_eq, swe with b = const).
+/* PDE systems of Sec. 5 (eq. acoustic, lin_elastic, euler_eq, swe with b = const).
  * ADG_SWE_B: the shallow-water form of eq. (swe_canonical) with bathymetry, 2D, variables
  * (h, hu, hv, b): conservative fluxes of eq. (swe_cons) without the hydrostatic pressure, the
  * non-conservative product of eq. (swe_noncons) in the predictor and the volume integral, and
@@ -68,7 +68,7 @@ enum adg_status {
  * and subtracted by its plus cell.  Parameter: g.  Built for N = 2, 4, 5. */
 enum adg_pde { ADG_ACOUSTIC = 0, ADG_ELASTIC = 1, ADG_EULER = 2, ADG_SWE = 3, ADG_SWE_B = 4 };
 
-/* The per-kernel precision knobs of Sec. 3.1 ("predictor", "Picard", "corrector",
+/* The per-kernel precision knobs of Sec. 4.1 ("predictor", "Picard", "corrector",
  * "storage"), with the Riemann solve split from the face integral. */
 enum adg_kernel {
   ADG_K_PICARD = 0,    /* arithmetic of the Picard sweeps (flux + contractions) */
@@ -80,7 +80,7 @@ enum adg_kernel {
 
 enum adg_prec { ADG_FP64 = 0, ADG_FP32 = 1, ADG_BF16 = 2, ADG_FP16 = 3, ADG_FP8E4M3 = 4 };
 
-/* Predictor schemes of Sec. 2.1 (adg_set_predictor) */
+/* Predictor schemes of Sec. 3.1 (adg_set_predictor) */
 enum adg_predictor { ADG_PRED_PICARD = 0, ADG_PRED_CK = 1 };
 
 enum adg_flags {
@@ -92,7 +92,7 @@ enum adg_flags {
 /* Scenario closed forms for adg_set_initial() / adg_error_vs_exact(); the
  * parameter encodings are:
  *  ADG_SC_PLANAR      [Q0[V], nw, {amp, kx, ky, kz, omega, r[V]} x nw]
- *                     Q = Q0 + sum amp sin(k.x - omega t) r   (Sec. 4.2.1 planar waves)
+ *                     Q = Q0 + sum amp sin(k.x - omega t) r   (Sec. 5.2.1 planar waves)
  *  ADG_SC_EULER_WAVE  [rho0, A, kx, ky, kz, ux, uy, uz, p0]
  *                     rho = rho0 + A sin(k.(x - u t)), velocity u, pressure p0
  *  ADG_SC_SWE_MODES   [h0, a0, kx0, ky0, nm, {a, kx, ky, phi} x nm], at rest;
@@ -103,10 +103,10 @@ enum adg_flags {
  *                     b = b0 + ab sin(kbx x + kby y), eta = eta0 + sum a sin(kx x + ky y + phi),
  *                     h = eta - b, v = 0 (eq. lake_initial); nm = 0 is the lake at rest, whose
  *                     closed form is the initial state at every t; otherwise t = 0 only
- *  ADG_SC_EULER_BELL  [rho0, amp, width, x0, y0, ux, uy, p0] (2D Euler, Sec. 4.3.1):
+ *  ADG_SC_EULER_BELL  [rho0, amp, width, x0, y0, ux, uy, p0] (2D Euler, Sec. 5.3.1):
  *                     rho = rho0 (1 + amp exp(-width |x - x0 - u t|^2)), velocity u,
  *                     pressure p0; nearest periodic image of the bell
- *  ADG_SC_EULER_VORTEX [rho_inf, p_inf, beta, x0, y0, u_inf, v_inf] (2D Euler, Sec. 4.3.2):
+ *  ADG_SC_EULER_VORTEX [rho_inf, p_inf, beta, x0, y0, u_inf, v_inf] (2D Euler, Sec. 5.3.2):
  *                     isentropic vortex of strength beta centred at x0 + u t:
  *                     dT = (1 - gamma) beta^2 / (8 gamma pi^2) e^(1 - r^2),
  *                     rho = rho_inf + (1 + dT)^(1/(gamma-1)) - 1,
@@ -130,7 +130,7 @@ ADG_API int adg_destroy(adg_ctx* c);
 ADG_API int adg_set_stream(adg_ctx* c, void* cuda_stream);
 
 /* Uniform periodic mesh of [lo,hi]^dim with cells[d] cells per direction and
- * order N (dim in {2,3}).  Sec. 2: tree-structured Cartesian grid, here uniform. */
+ * order N (dim in {2,3}).  Sec. 3: tree-structured Cartesian grid, here uniform. */
 ADG_API int adg_init_mesh(adg_ctx* c, int dim, int order_N, const int* cells, const double* lo,
                   const double* hi);
 
@@ -138,7 +138,7 @@ ADG_API int adg_init_mesh(adg_ctx* c, int dim, int order_N, const int* cells, co
  *   acoustic: rho, K        elastic: rho, c_p, c_s        euler: gamma        swe: g */
 ADG_API int adg_set_pde(adg_ctx* c, int pde, const double* params, int nparams);
 
-/* Precision of one kernel (Sec. 3.1).  Built combinations:
+/* Precision of one kernel (Sec. 4.1).  Built combinations:
  *   PICARD     FP64, FP32 (SIMT, must equal PREDICTOR); BF16, FP16, FP8E4M3 with PREDICTOR
  *              FP32 (tensor cores, FP32 accumulation, 3D meshes, CORRECTOR FP32 or FP64; flags
  *              (ADG_F_*) given with the PICARD call select compensation and per-cell scaling);
@@ -147,7 +147,7 @@ ADG_API int adg_set_pde(adg_ctx* c, int pde, const double* params, int nparams);
  *   PREDICTOR  FP64, FP32, BF16 (see PICARD)
  *   RIEMANN    FP64, FP32, BF16 (bf16 built for shallow water)
  *   CORRECTOR  FP64, FP32, BF16 (bf16 built for shallow water)
- *   STORAGE    FP64; FP32, BF16, FP16 (the persistent solution, Sec. 3.1 "storage") with all
+ *   STORAGE    FP64; FP32, BF16, FP16 (the persistent solution, Sec. 4.1 "storage") with all
  *              four other kernels FP64 or all four FP32, the Picard predictor, and the orders
  *              of the workloads (acoustic 2D N=3, 3D N=4; elastic 3D N=2, 6; Euler 3D N=2, 5;
  *              shallow water N=2, 4).  The stored solution is rounded (to nearest, ties to
@@ -167,8 +167,8 @@ ADG_API int adg_set_kernel_precision(adg_ctx* c, int kernel, int prec, int flags
  * number of Picard sweeps (<= 0: N+1). */
 ADG_API int adg_set_numerics(adg_ctx* c, double cfl, int picard_iters);
 
-/* Predictor scheme (Sec. 2.1).  ADG_PRED_PICARD (default): the Picard sweeps of eq. (Picard),
- * any PDE.  ADG_PRED_CK: the Cauchy-Kowalevskaya procedure of the last paragraph of Sec. 2.1,
+/* Predictor scheme (Sec. 3.1).  ADG_PRED_PICARD (default): the Picard sweeps of eq. (Picard),
+ * any PDE.  ADG_PRED_CK: the Cauchy-Kowalevskaya procedure of the last paragraph of Sec. 3.1,
  * for the linear PDEs only (acoustic, elastic): d_t^{m+1} Q = -sum_d d_d F_d(d_t^m Q) for
  * m = 0..N-1 and q(tau) = sum_m (tau dt)^m / m! d_t^m Q at the time nodes, followed by the
  * same time averages, volume integral and face traces.  CK runs with PICARD == PREDICTOR in
@@ -176,6 +176,17 @@ ADG_API int adg_set_numerics(adg_ctx* c, double cfl, int picard_iters);
  * returns ADG_EUNSUPPORTED at the first step; adg_adjoint needs the Picard scheme.  The
  * allocation-free adg_step_noalloc always runs the FP64 Picard kernels. */
 ADG_API int adg_set_predictor(adg_ctx* c, int scheme);
+
+/* Iterative-refinement predictor (NEXT-1 of the hot-path scope; the precision split of the
+ * mixed-precision iterative refinement discussed in Sec. 2, applied to the Picard iteration of
+ * eq. (Picard)).  fp64_sweeps = k > 0: of the I Picard sweeps (adg_set_numerics), the first I - k
+ * run in the PICARD precision, FP32 or BF16 (SIMT arithmetic), and the last k, started from that
+ * iterate, together with the final stage (time averages, volume integral, face traces) in FP64;
+ * PREDICTOR must be FP64.  Each FP64 sweep shrinks the low-precision sweeps' error by the
+ * Picard map's contraction factor; k >= I gives the FP64 predictor.  0 (default) turns it off.
+ * Built for 3D Euler (N = 2, 5) and 3D acoustics (N = 4), Picard scheme, FP64 storage; other
+ * cases return ADG_EUNSUPPORTED at the first step.  Values outside [0, 1000] return ADG_EINVAL. */
+ADG_API int adg_set_refinement(adg_ctx* c, int fp64_sweeps);
 
 /* Bytes the caller must provide as workspace for this mesh/PDE/precision. */
 ADG_API int adg_workspace_bytes(const adg_ctx* c, size_t* bytes);
@@ -186,7 +197,7 @@ ADG_API int adg_state_size(const adg_ctx* c, size_t* ndouble, int* nvar);
  * a workspace of at least adg_workspace_bytes(), 256-byte aligned. */
 ADG_API int adg_bind_buffers(adg_ctx* c, double* d_state, void* d_workspace, size_t workspace_bytes);
 
-/* Interpolate a scenario's closed form at the GL nodes at t = 0 (Sec. 4.5: the
+/* Interpolate a scenario's closed form at the GL nodes at t = 0 (Sec. 5.5: the
  * DG solution starts from Q_h^*) and set t = 0.  params: host array, kept by the
  * context for adg_error_vs_exact(). */
 ADG_API int adg_set_initial(adg_ctx* c, int scenario, const double* params, int nparams);
@@ -213,7 +224,7 @@ ADG_API int adg_step_timed(adg_ctx* c, int nsteps, double* t_out, double* ms_ker
 /* Current time and the dt the next step will use (waits). */
 ADG_API int adg_get_time(adg_ctx* c, double* t, double* dt_next);
 
-/* eq. (L2gauss) of Sec. 4.5 in FP64 between the state and the scenario's closed
+/* eq. (L2gauss) of Sec. 5.5 in FP64 between the state and the scenario's closed
  * form at the current time: l2_per_var[V] (may be NULL) and the total. */
 ADG_API int adg_error_vs_exact(adg_ctx* c, double* l2_per_var, double* l2_total);
 

@@ -5,14 +5,14 @@ baseline leg of ``bench.py`` are the only code that may import this package.
 The CUDA library does not import, link or call it, and shares no code with it.
 
 Every function follows arXiv 2504.06889:
-  * Sec. 2, eq. (piecewise_solution): tensor-product Lagrange basis on GL nodes;
-  * Sec. 2.1, eq. (Picard): the space-time predictor system solved by Picard
+  * Sec. 3, eq. (piecewise_solution): tensor-product Lagrange basis on GL nodes;
+  * Sec. 3.1, eq. (Picard): the space-time predictor system solved by Picard
     iteration; the Cauchy-Kowalevskaya alternative for linear PDEs;
-  * Sec. 2.2, eq. (weak_form_volume_surface), (CFL_condition), (rusanov_flux);
-  * Sec. 3.1 and Algorithm 1: the "storage" precision of the persistent solution,
+  * Sec. 3.2, eq. (weak_form_volume_surface), (CFL_condition), (rusanov_flux);
+  * Sec. 4.1 and Algorithm 1: the "storage" precision of the persistent solution,
     rounded to its format after each of the step's two grid traversals;
-  * Sec. 4: the acoustic, elastic, Euler and shallow-water fluxes;
-  * Sec. 4.5, eq. (L2gauss): the error norm.
+  * Sec. 5: the acoustic, elastic, Euler and shallow-water fluxes;
+  * Sec. 5.5, eq. (L2gauss): the error norm.
 """
 from __future__ import annotations
 
@@ -163,7 +163,7 @@ class Mesh:
         _load().or_set_picard_iters(self._h, int(iters))
 
     def set_storage(self, fmt):
-        """Persistent solution format between the two traversals of a step (Sec. 3.1):
+        """Persistent solution format between the two traversals of a step (Sec. 4.1):
         'fp64', 'fp32', 'bf16' or 'fp16'."""
         _load().or_set_storage(self._h, STORAGE[fmt] if isinstance(fmt, str) else int(fmt))
 

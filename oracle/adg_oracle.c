@@ -3,7 +3,7 @@
  * the smoke check and the benchmark's CPU-baseline leg are its only users; the
  * CUDA library never links, loads or calls it, and it shares no code with it.
  *
- * Everything is written in the order and notation of arXiv 2504.06889, Sec. 2:
+ * Everything is written in the order and notation of arXiv 2504.06889, Sec. 3:
  * no blocking, fusion or reordering beyond what the equations state.  Loops are
  * over (cell, time node k, variable v, spatial node i) in the obvious way.
  *
@@ -22,7 +22,7 @@
 #include <string.h>
 
 /* ------------------------------------------------------------------------ */
-/* 1D tables.  Sec. 2, eq. (piecewise_solution): Lagrange polynomials with    */
+/* 1D tables.  Sec. 3, eq. (piecewise_solution): Lagrange polynomials with    */
 /* Gauss-Legendre support points.  GL nodes by Newton on P_n (long double).   */
 /* ------------------------------------------------------------------------ */
 
@@ -148,7 +148,7 @@ int or_nvar(int pde, int dim) {
     case OR_ELASTIC: return dim == 3 ? 9 : 5;  /* stresses (Voigt), velocities */
     case OR_EULER: return 2 + dim;             /* rho, rho v_1..v_d, E */
     case OR_SWE: return 3;                     /* h, hu, hv (flat bathymetry) */
-    case OR_SWE_B: return 4;                   /* h, hu, hv, b (Sec. 4.4) */
+    case OR_SWE_B: return 4;                   /* h, hu, hv, b (Sec. 5.4) */
   }
   return -1;
 }
@@ -192,7 +192,7 @@ int or_setup(or_mesh* M, int dim, int N, const int* m, const double* lo, const d
 void or_set_cell_c(or_mesh* M, const double* cell_c) { M->cell_c = cell_c; }
 
 /* ------------------------------------------------------------------------ */
-/* PDE fluxes, Sec. 4.  F_dir(q) and the spectral radius of dF_dir/dq.        */
+/* PDE fluxes, Sec. 5.  F_dir(q) and the spectral radius of dF_dir/dq.        */
 /* ------------------------------------------------------------------------ */
 
 void or_flux(const or_mesh* M, int cell, const double* q, int dir, double* F) {
@@ -267,7 +267,7 @@ void or_flux(const or_mesh* M, int cell, const double* q, int dir, double* F) {
     for (int a = 0; a < d; ++a) F[1 + a] = q[1 + a] * vel[dir] + (a == dir ? p : 0.0);
     F[1 + d] = vel[dir] * (E + p);
   } else if (M->pde == OR_SWE) {
-    /* Sec. 4.4 with flat bathymetry: the hydrostatic non-conservative term
+    /* Sec. 5.4 with flat bathymetry: the hydrostatic non-conservative term
      * g h grad(b + h) reduces to grad(g h^2 / 2), so F_dir = (h v_dir,
      * h v v_dir + g h^2/2 e_dir) */
     double g = M->pp[0];
@@ -320,7 +320,7 @@ double or_speed(const or_mesh* M, int cell, const double* q, int dir) {
 }
 
 /* ------------------------------------------------------------------------ */
-/* Exact solutions / initial data (Sec. 4 scenarios and the synthetic ones)  */
+/* Exact solutions / initial data (Sec. 5 scenarios and the synthetic ones)  */
 /* ------------------------------------------------------------------------ */
 
 void or_exact(const or_mesh* M, int scen, const double* sp, int nsp, const double* x, double t,
@@ -330,7 +330,7 @@ void or_exact(const or_mesh* M, int scen, const double* sp, int nsp, const doubl
   for (int v = 0; v < V; ++v) Q[v] = 0.0;
   if (scen == OR_SC_PLANAR) {
     /* sp = [Q0[V], nw, {amp, kx, ky, kz, omega, r[V]} x nw];
-     * Q = Q0 + sum amp sin(k.x - omega t) r  (planar wave, Sec. 4.2.1) */
+     * Q = Q0 + sum amp sin(k.x - omega t) r  (planar wave, Sec. 5.2.1) */
     for (int v = 0; v < V; ++v) Q[v] = sp[v];
     int nw = (int)sp[V];
     const double* p = sp + V + 1;
@@ -361,7 +361,7 @@ void or_exact(const or_mesh* M, int scen, const double* sp, int nsp, const doubl
     for (int j = 0; j < nm; ++j, p += 4) h += p[0] * sin(p[1] * x[0] + p[2] * x[1] + p[3]);
     Q[0] = h;
   } else if (scen == OR_SC_EULER_BELL) {
-    /* Sec. 4.3.1: sp = [rho0, amp, width, x0, y0, ux, uy, p0]; rho = rho0 (1 + amp
+    /* Sec. 5.3.1: sp = [rho0, amp, width, x0, y0, ux, uy, p0]; rho = rho0 (1 + amp
      * exp(-width |x - x0 - u t|^2)) (the squared exponent of the figure; nearest periodic
      * image), velocity u, pressure p0: an exact solution of the Euler equations */
     double gamma = M->pp[0], r2 = 0.0, u2 = 0.0;
@@ -378,7 +378,7 @@ void or_exact(const or_mesh* M, int scen, const double* sp, int nsp, const doubl
     Q[2] = rho * sp[6];
     Q[3] = sp[7] / (gamma - 1.0) + 0.5 * rho * u2;
   } else if (scen == OR_SC_EULER_VORTEX) {
-    /* Sec. 4.3.2 (Hu and Shu's isentropic vortex): sp = [rho_inf, p_inf, beta, x0, y0, u_inf,
+    /* Sec. 5.3.2 (Hu and Shu's isentropic vortex): sp = [rho_inf, p_inf, beta, x0, y0, u_inf,
      * v_inf]; with r the distance to the centre x0 + u_inf t (nearest periodic image):
      * dT = (1 - gamma) beta^2 / (8 gamma pi^2) e^(1 - r^2), rho = rho_inf + (1 + dT)^(1/(gamma-1))
      * - 1, p = p_inf + (1 + dT)^(gamma/(gamma-1)) - 1 (the printed dp repeats drho; this is the
@@ -440,7 +440,7 @@ static int ipow(int b, int e) {
 
 static int ncells(const or_mesh* M) { return M->m[0] * M->m[1] * M->m[2]; }
 
-/* Sec. 4.5: Q_h^* interpolates the exact solution at the GL nodes */
+/* Sec. 5.5: Q_h^* interpolates the exact solution at the GL nodes */
 void or_interpolate(const or_mesh* M, int scen, const double* sp, int nsp, double t, double* Q) {
   const int V = M->nvar, NS = ipow(M->n, M->dim), C = ncells(M);
 #pragma omp parallel for schedule(static)
@@ -525,7 +525,7 @@ void or_totals(const or_mesh* M, const double* Q, double* tot) {
 }
 
 /* ------------------------------------------------------------------------ */
-/* Predictor, Sec. 2.1.  Eq. (Picard) divided by the spatial mass h^d prod w: */
+/* Predictor, Sec. 3.1.  Eq. (Picard) divided by the spatial mass h^d prod w: */
 /*   sum_l K1[k][l] q_{l,i} + dt w_k R_{k,i} = psi_k(0) Q_i,                  */
 /*   R_{k,i} = sum_dir (1/h_dir) sum_a D[i_dir][a] F_dir(q_{k, i[dir<-a]}).    */
 /* Picard: q^(r) = K1^{-1} (psi(0) Q - dt w o R(q^(r-1))), q^(0) = Q.          */
@@ -618,7 +618,7 @@ void or_predictor_cell(const or_mesh* M, int cell, const double* Qc, double dt, 
   free(R);
 }
 
-/* Cauchy-Kowalevskaya predictor for linear PDEs (Sec. 2.1, last paragraph):
+/* Cauchy-Kowalevskaya predictor for linear PDEs (Sec. 3.1, last paragraph):
  * q(tau) = sum_{m=0}^{N} (tau dt)^m / m! d_t^m Q, d_t^{m+1} Q = -sum_dir d_dir F_dir(d_t^m Q). */
 void or_ck_cell(const or_mesh* M, int cell, const double* Qc, double dt, double* q) {
   const int n = M->n, V = M->nvar, NS = ipow(n, M->dim), N = M->N;
@@ -731,7 +731,7 @@ static int face_index(const or_mesh* M, int i, int dir) {
 }
 
 /* ------------------------------------------------------------------------ */
-/* One ADER-DG step, Sec. 2 and Algorithm 1:                                 */
+/* One ADER-DG step, Sec. 3 and Algorithm 1:                                 */
 /*  pass 1 per cell: predictor, time averages, face traces (expansion),      */
 /*         Q += dt vol   (eq. weak_form_volume_surface, volume term)          */
 /*  pass 2 per cell: Rusanov on each face, Q -= dt surf (surface term)       */
@@ -866,7 +866,7 @@ static const double* all_trace(const void* ctx, int cell, int dir, int side, int
 }
 
 /* ------------------------------------------------------------------------ */
-/* Storage precision (Sec. 3.1): rounding to a binary format of Table         */
+/* Storage precision (Sec. 4.1): rounding to a binary format of Table         */
 /* precision_bits from the definition of its values.  A format with p         */
 /* significand bits (hidden bit included) and exponents emin..emax holds      */
 /* m 2^(e-p+1) with integer |m| < 2^p and e in [emin, emax]; below 2^emin the */

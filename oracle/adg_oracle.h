@@ -10,13 +10,13 @@
  * Section / equation references are to Marot-Lassauzaie & Bader, "Mixed-Precision
  * in High-Order Methods: the Impact of Floating-Point Precision on the ADER-DG
  * Algorithm" (arXiv 2504.06889):
- *   Sec. 2 eq. (piecewise_solution)        nodal tensor-product GL basis
- *   Sec. 2.1 eq. (Picard)                  space-time predictor system
- *   Sec. 2.2 eq. (weak_form_volume_surface) corrector
- *   Sec. 2.2 eq. (CFL_condition)           time step
- *   Sec. 2.2 eq. (rusanov_flux)            Riemann solver
- *   Sec. 4 (acoustic, elastic, Euler, shallow water)  PDE fluxes
- *   Sec. 4.5 eq. (L2gauss)                 error norm
+ *   Sec. 3 eq. (piecewise_solution)        nodal tensor-product GL basis
+ *   Sec. 3.1 eq. (Picard)                  space-time predictor system
+ *   Sec. 3.2 eq. (weak_form_volume_surface) corrector
+ *   Sec. 3.2 eq. (CFL_condition)           time step
+ *   Sec. 3.2 eq. (rusanov_flux)            Riemann solver
+ *   Sec. 5 (acoustic, elastic, Euler, shallow water)  PDE fluxes
+ *   Sec. 5.5 eq. (L2gauss)                 error norm
  *
  * Data layout (same as the exported state of the library under test, but
  * written independently): Q[cell][var][node], cell = cx + m0*(cy + m1*cz),
@@ -33,7 +33,7 @@ extern "C" {
 #define OR_MAXV 9
 
 /* OR_SWE: shallow water with flat bathymetry in conservative form (h, hu, hv).
- * OR_SWE_B: the paper's form of Sec. 4.4 with bathymetry, Q = (h, hu, hv, b), conservative
+ * OR_SWE_B: the paper's form of Sec. 5.4 with bathymetry, Q = (h, hu, hv, b), conservative
  * fluxes without the hydrostatic pressure and the non-conservative product B(Q) grad Q. */
 enum { OR_ACOUSTIC = 0, OR_ELASTIC = 1, OR_EULER = 2, OR_SWE = 3, OR_SWE_B = 4 };
 /* storage formats of Table precision_bits: significand bits p (with the hidden bit),
@@ -45,8 +45,8 @@ enum {
   OR_SC_SWE_MODES = 2,
   OR_SC_GAUSS_PULSE = 3,
   OR_SC_LAKE = 4,
-  OR_SC_EULER_BELL = 5,  /* Sec. 4.3.1: advected Gaussian density bell */
-  OR_SC_EULER_VORTEX = 6 /* Sec. 4.3.2: isentropic vortex */
+  OR_SC_EULER_BELL = 5,  /* Sec. 5.3.1: advected Gaussian density bell */
+  OR_SC_EULER_VORTEX = 6 /* Sec. 5.3.2: isentropic vortex */
 };
 
 typedef struct {
@@ -57,7 +57,7 @@ typedef struct {
   double cfl;         /* C_CFL of eq. (CFL_condition) */
   int picard_iters;   /* fixed number of Picard sweeps */
   int use_ck;         /* 1: Cauchy-Kowalevskaya predictor instead of Picard (linear PDEs) */
-  int storage;        /* persistent-solution format (Sec. 3.1 "storage"): OR_ST_* */
+  int storage;        /* persistent-solution format (Sec. 4.1 "storage"): OR_ST_* */
   const double* cell_c; /* optional per-cell wave speed for acoustics (rho fixed); NULL = none */
   /* 1D tables on [0,1] */
   double xi[OR_MAXN], w[OR_MAXN];
@@ -132,7 +132,7 @@ void or_destroy(or_mesh* M);
 void or_set_ck(or_mesh* M, int use_ck);
 void or_set_picard_iters(or_mesh* M, int iters);
 /* Persistent solution stored in format fmt (OR_ST_*) between the two grid traversals of a
- * step (Sec. 3.1, Algorithm 1): the step rounds Q after the predictor/volume pass and after
+ * step (Sec. 4.1, Algorithm 1): the step rounds Q after the predictor/volume pass and after
  * the corrector pass. */
 void or_set_storage(or_mesh* M, int fmt);
 /* x rounded to format fmt: nearest value, ties to even, overflow to +-inf. */

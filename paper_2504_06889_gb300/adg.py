@@ -43,6 +43,7 @@ _SIGS = {
     "adg_set_pde": [_P, C.c_int, _dp, C.c_int],
     "adg_set_kernel_precision": [_P, C.c_int, C.c_int, C.c_int],
     "adg_set_numerics": [_P, C.c_double, C.c_int],
+    "adg_set_refinement": [_P, C.c_int],
     "adg_set_predictor": [_P, C.c_int],
     "adg_workspace_bytes": [_P, C.POINTER(C.c_size_t)],
     "adg_state_size": [_P, C.POINTER(C.c_size_t), _ip],
@@ -96,7 +97,7 @@ class Solver:
     """One ADER-DG context with torch-allocated state and workspace on the current device."""
 
     def __init__(self, dim, N, cells, pde, params, lo=None, hi=None, cfl=0.9, picard_iters=0,
-                 precision=None, flags=0, stream=None, scheme=PRED_PICARD):
+                 precision=None, flags=0, stream=None, scheme=PRED_PICARD, refine=0):
         import torch
 
         self._torch = torch
@@ -120,6 +121,8 @@ class Solver:
         if isinstance(scheme, str):
             scheme = {"picard": PRED_PICARD, "ck": PRED_CK}[scheme]
         self._check(self.lib.adg_set_predictor(self.ctx, scheme))
+        if refine:
+            self._check(self.lib.adg_set_refinement(self.ctx, int(refine)))
         for k, p in (precision or {}).items():
             kk = {"picard": K_PICARD, "predictor": K_PREDICTOR, "riemann": K_RIEMANN,
                   "corrector": K_CORRECTOR, "storage": K_STORAGE}[k] if isinstance(k, str) else k

@@ -82,7 +82,7 @@ const Entry* find_entry(int pde, int dim, int N) {
 }
 
 // ---- 1D tables on [0,1]: Gauss-Legendre points by Newton on the shifted Legendre polynomial,
-// barycentric Lagrange weights for derivative and boundary values (Sec. 2). -------------------
+// barycentric Lagrange weights for derivative and boundary values (Sec. 3). -------------------
 static void legendre_shifted(int n, long double x, long double* P, long double* dP) {
   // P_n(2x-1) and d/dx via the three-term recurrence in t = 2x - 1
   const long double t = 2.0L * x - 1.0L;
@@ -231,6 +231,7 @@ struct adg_ctx {
   int flags = 0;
   double cfl = 0.9;
   int picard_iters = 0;
+  int refine = 0;  // FP64 refinement sweeps (0: off)
   int scheme = ADG_PRED_PICARD;
   double* Q = nullptr;
   void* ws = nullptr;
@@ -321,6 +322,7 @@ static void fill_step_args(const adg_ctx* c, StepArgs* a) {
   a->picard_iters = c->picard_iters > 0 ? c->picard_iters : c->N + 1;
   a->comp_sweeps = (c->flags & ADG_F_COMPENSATED_TWO) ? 2 : (c->flags & ADG_F_COMPENSATED_LAST) ? 1 : 0;
   a->per_cell_scale = (c->flags & ADG_F_PER_CELL_SCALE) ? 1 : 0;
+  a->refine_sweeps = c->refine;
   a->tab = c->tab;
   a->pp = c->pp;
   finalize_step_args(a);
@@ -484,6 +486,13 @@ int adg_set_numerics(adg_ctx* c, double cfl, int picard_iters) {
   return ADG_OK;
 }
 
+int adg_set_refinement(adg_ctx* c, int fp64_sweeps) {
+  if (!c) return ADG_EINVAL;
+  if (fp64_sweeps < 0 || fp64_sweeps > 1000) return fail(c, ADG_EINVAL, "fp64_sweeps must be in [0, 1000]");
+  c->refine = fp64_sweeps;
+  return ADG_OK;
+}
+
 int adg_set_predictor(adg_ctx* c, int scheme) {
   if (!c) return ADG_EINVAL;
   if (scheme != ADG_PRED_PICARD && scheme != ADG_PRED_CK) return fail(c, ADG_EINVAL, "unknown predictor scheme");
@@ -634,7 +643,12 @@ static int select_kernels(adg_ctx* c, StepFn* pred, StepFn* corr) {
     if (!*pred || !*corr) return fail(c, ADG_EUNSUPPORTED, "storage mix not built");
     return ADG_OK;
   }
-  if (c->scheme == ADG_PRED_CK) {
+  if (c->refine > 0) {
+    if (c->scheme != ADG_PRED_PICARD) return fail(c, ADG_EUNSUPPORTED, "refinement refines the Picard sweeps");
+    if (prd != P64 || (pic != P32 && pic != PBF16))
+      return fail(c, ADG_EUNSUPPORTED, "refinement: PICARD in {FP32, BF16} and PREDICTOR FP64");
+    *pred = c->entry->predictor_refine[pic == P32 ? 0 : 1][cor];
+  } else if (c->scheme == ADG_PRED_CK) {
     if (c->pde != ADG_ACOUSTIC && c->pde != ADG_ELASTIC)
       return fail(c, ADG_EUNSUPPORTED, "the Cauchy-Kowalevskaya predictor needs a linear PDE");
     if (pic != prd || pic > P32)

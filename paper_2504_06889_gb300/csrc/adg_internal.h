@@ -12,7 +12,7 @@ constexpr int kMaxV = 9;
 
 enum Prec { P64 = 0, P32 = 1, PBF16 = 2, PF16 = 3, PF8 = 4 };
 
-// 1D operators on the reference interval [0,1] (Sec. 2), in FP64.
+// 1D operators on the reference interval [0,1] (Sec. 3), in FP64.
 struct Tables {
   int n;
   double xi[kMaxN1], w[kMaxN1], psi0[kMaxN1], psi1[kMaxN1];
@@ -64,7 +64,7 @@ struct StepArgs {
   int picard_iters;
   int comp_sweeps;     // tensor-core Picard: number of final sweeps with hi/lo compensation
   int per_cell_scale;  // tensor-core Picard: power-of-two scaling of the flux per cell
-  int pad;
+  int refine_sweeps;   // refinement predictor: the last sweeps run in FP64
   // surface-integral coefficients psi_side(xi_i) / (h_dir w_i) [side][dir][i], FP64 and rounded
   // to FP32 (set by finalize_step_args)
   double surf[2][3][kMaxN1];
@@ -119,6 +119,9 @@ struct Entry {
   StepFn predictor_tc[3][3];
   // Cauchy-Kowalevskaya predictor (linear PDEs): [P64 / P32 arithmetic][trace prec]
   StepFn predictor_ck[2][3];
+  // refinement predictor (low-precision sweeps, then FP64 sweeps and final stage):
+  // [low sweeps 0 = FP32, 1 = bf16][trace prec]
+  StepFn predictor_refine[2][3];
   // discrete adjoint (linear acoustics): face projections, per-cell adjoint [0 = FP64, 1 = FP32]
   void* adj_trace;
   void* adj_cell[2];
@@ -128,7 +131,7 @@ struct Entry {
   int l2_blocks_per_cell_group;  // cells per block of the L2 kernel
 };
 
-// Kernels with the persistent solution stored below FP64 (Sec. 3.1 "storage") for one
+// Kernels with the persistent solution stored below FP64 (Sec. 4.1 "storage") for one
 // (PDE, d, N): [storage FP32 / BF16 / FP16][all kernels FP64 / all kernels FP32]
 struct StorageEntry {
   int pde, dim, N;

@@ -1,4 +1,4 @@
-// SIMT kernels of the ADER-DG step (arXiv 2504.06889, Sec. 2 and Algorithm 1), templated on
+// SIMT kernels of the ADER-DG step (arXiv 2504.06889, Sec. 3 and Algorithm 1), templated on
 // the PDE, the dimension d, the order N and the per-kernel precisions.
 //
 //  k_predictor   one thread per spatial node of a cell; the thread keeps its node's space-time
@@ -148,7 +148,7 @@ template <int S> struct VecLoad<__nv_bfloat16, S> {
   }
 };
 
-// ---- storage precision of the persistent solution (Sec. 3.1 "storage") ----------------------
+// ---- storage precision of the persistent solution (Sec. 4.1 "storage") ----------------------
 // FP64 -> storage format, round to nearest with ties to even.  bf16 and fp16 go through FP32
 // rounded to odd (truncate, then set the last bit if anything was cut off): with at least two
 // more bits than the target, rounding to odd and then to nearest even equals direct rounding
@@ -380,8 +380,8 @@ __device__ __forceinline__ void ncp_at_node(const PP<T>& pp, const T* sF, const 
 
 // ------------------------------------------------------------------------------------------------
 // predictor + volume integral + face traces
-// CK = false: Picard sweeps (Sec. 2.1, eq. Picard).  CK = true: Cauchy-Kowalevskaya for the
-// linear PDEs (Sec. 2.1, last paragraph): d_t^{m+1} Q = -sum_dir d_dir F_dir(d_t^m Q) for
+// CK = false: Picard sweeps (Sec. 3.1, eq. Picard).  CK = true: Cauchy-Kowalevskaya for the
+// linear PDEs (Sec. 3.1, last paragraph): d_t^{m+1} Q = -sum_dir d_dir F_dir(d_t^m Q) for
 // m < N, q_k = sum_m (xi_k dt)^m / m! d_t^m Q at the time nodes; N derivative evaluations per
 // cell instead of about (N+1)^2 flux slices.  Both end in the same final stage.
 // ------------------------------------------------------------------------------------------------
@@ -898,7 +898,7 @@ __device__ void exact_solution(int scen, const double* sp, const PdeParams& pp, 
     const int nm = (int)sp[4];
     for (int j = 0; j < nm; ++j) h += sp[5 + 4 * j] * sin(sp[6 + 4 * j] * x[0] + sp[7 + 4 * j] * x[1] + sp[8 + 4 * j]);
     Q[0] = h;
-  } else if (scen == 5) {  // advected density bell (Sec. 4.3.1), nearest periodic image
+  } else if (scen == 5) {  // advected density bell (Sec. 5.3.1), nearest periodic image
     if constexpr (D == 2 && V == 4) {
       double r2 = 0.0, u2 = 0.0;
 #pragma unroll
@@ -914,7 +914,7 @@ __device__ void exact_solution(int scen, const double* sp, const PdeParams& pp, 
       Q[2] = rho * sp[6];
       Q[3] = sp[7] / (pp.gamma - 1.0) + 0.5 * rho * u2;
     }
-  } else if (scen == 6) {  // isentropic vortex (Sec. 4.3.2), isentropic pressure
+  } else if (scen == 6) {  // isentropic vortex (Sec. 5.3.2), isentropic pressure
     if constexpr (D == 2 && V == 4) {
       double dd[2], r2 = 0.0;
 #pragma unroll

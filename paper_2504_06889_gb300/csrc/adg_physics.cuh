@@ -1,4 +1,4 @@
-// Pointwise physics of Sec. 4 of arXiv 2504.06889 for the CUDA kernels:
+// Pointwise physics of Sec. 5 of arXiv 2504.06889 for the CUDA kernels:
 // fluxes F_dir(q) for all directions at once, and the spectral radius of dF_dir/dq.
 #pragma once
 
@@ -266,7 +266,7 @@ template <int D> struct Phys<2, D> {
   }
 };
 
-// ---- shallow water, flat bathymetry (Sec. 4.4): F_dir = (h v_dir, h v v_dir + g h^2/2 e_dir) --
+// ---- shallow water, flat bathymetry (Sec. 5.4): F_dir = (h v_dir, h v v_dir + g h^2/2 e_dir) --
 template <> struct Phys<3, 2> {
   static constexpr int V = 3;
   static constexpr bool linear = false;

@@ -1,5 +1,5 @@
 // Tensor-core Picard predictor with whole sweeps batched (3D meshes; bf16 or fp16 inputs, FP32
-// accumulation in tensor memory).  arXiv 2504.06889, Sec. 2.1, eq. (Picard):
+// accumulation in tensor memory).  arXiv 2504.06889, Sec. 3.1, eq. (Picard):
 //     q_k = Q - dt sum_l P[k][l] R_l,   R_l = sum_dir D_dir F_dir(q_l).
 // Both operators are contractions, and the whole sweep goes through the tensor cores in two
 // MMA rounds (the time slices of a sweep are independent: every flux comes from the previous

@@ -1,8 +1,9 @@
-// Kernel instantiations: linear acoustics (Sec. 4.1).
+// Kernel instantiations: linear acoustics (Sec. 5.1).
 #include "adg_kernels.cuh"
 #include "adg_tc.cuh"
 #include "adg_adjoint.cuh"
 #include "adg_tc_sweep.cuh"
+#include "adg_refine.cuh"
 
 namespace adg {
 template <int D, int N>
@@ -24,6 +25,7 @@ void register_acoustic() {
     Entry e = make_entry<0, 3, 4, false>();
     add_tc<0, 3, 4>(e);
     add_tcs<0, 4>(e);
+    add_refine<0, 3, 4>(e);
     add_ck<0, 3, 4>(e);
     add_adjoint<3, 4>(e);
     register_entry(e);

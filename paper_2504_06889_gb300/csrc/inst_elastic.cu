@@ -1,4 +1,4 @@
-// Kernel instantiations: linear elasticity, velocity-stress form (Sec. 4.2).
+// Kernel instantiations: linear elasticity, velocity-stress form (Sec. 5.2).
 #include "adg_kernels.cuh"
 #include "adg_tc.cuh"
 

@@ -1,4 +1,4 @@
-// Kernel instantiations: 2D compressible Euler (Sec. 4.3: density bell, isentropic vortex).
+// Kernel instantiations: 2D compressible Euler (Sec. 5.3: density bell, isentropic vortex).
 #include "adg_kernels.cuh"
 
 namespace adg {

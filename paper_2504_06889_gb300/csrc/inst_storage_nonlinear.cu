@@ -1,4 +1,4 @@
-// Kernel instantiations with the persistent solution stored in FP32, bf16 or fp16 (Sec. 3.1
+// Kernel instantiations with the persistent solution stored in FP32, bf16 or fp16 (Sec. 4.1
 // "storage"): compressible Euler and shallow water.
 #include "adg_kernels.cuh"
 

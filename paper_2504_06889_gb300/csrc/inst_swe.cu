@@ -1,4 +1,4 @@
-// Kernel instantiations: shallow water with flat bathymetry (Sec. 4.4), including the bf16
+// Kernel instantiations: shallow water with flat bathymetry (Sec. 5.4), including the bf16
 // Riemann/corrector variants of the per-kernel precision sweep.
 #include "adg_kernels.cuh"
 

@@ -1,5 +1,5 @@
 // Kernel instantiations: shallow water with bathymetry in the non-conservative form of
-// Sec. 4.4 (eq. swe_canonical), 2D.
+// Sec. 5.4 (eq. swe_canonical), 2D.
 #include "adg_kernels.cuh"
 
 namespace adg {

@@ -16,8 +16,8 @@ Scenario encodings (float64 arrays):
   GAUSS_PULSE  [x0, y0, z0, sigma, amp]  p = amp exp(-|x-x0|^2/(2 sigma^2)), v = 0
 
 The planar-wave eigenpairs are the textbook ones for the acoustic system
-(Sec. 4.1 of arXiv 2504.06889) and the velocity-stress elastic system
-(Sec. 4.2), with the sign convention of eq. (elastic_matrices).
+(Sec. 5.1 of arXiv 2504.06889) and the velocity-stress elastic system
+(Sec. 5.2), with the sign convention of eq. (elastic_matrices).
 """
 from __future__ import annotations
 
@@ -116,13 +116,13 @@ def lake(eta0=2.0, b0=0.0, ab=1.0, kb=(2 * np.pi, 2 * np.pi), nmodes=0, amp=1e-2
 
 
 def euler_bell(rho0=0.02, amp=1.0, width=50.0, x0=(0.0, 0.0), u=(1.0, 1.0), p0=1.0):
-    """Advected Gaussian density bell (Sec. 4.3.1): rho = rho0 (1 + amp exp(-width |x - x0 -
+    """Advected Gaussian density bell (Sec. 5.3.1): rho = rho0 (1 + amp exp(-width |x - x0 -
     u t|^2)), velocity u, pressure p0."""
     return np.asarray([rho0, amp, width, x0[0], x0[1], u[0], u[1], p0], dtype=np.float64)
 
 
 def euler_vortex(rho_inf=1.0, p_inf=1.0, beta=5.0, x0=(0.0, 0.0), u=(0.0, 0.0)):
-    """Isentropic vortex (Sec. 4.3.2) centred at x0, carried with the velocity u."""
+    """Isentropic vortex (Sec. 5.3.2) centred at x0, carried with the velocity u."""
     return np.asarray([rho_inf, p_inf, beta, x0[0], x0[1], u[0], u[1]], dtype=np.float64)
 
 
@@ -240,14 +240,14 @@ def swe2d_lake(m=27, N=5, steps=200, eta0=2.0, b0=0.0):
 
 
 def euler2d_bell(m=27, N=5, steps=100):
-    """2D Euler, gamma = 1.4, the density bell of Sec. 4.3.1 on [-1, 1]^2 (one traversal of
+    """2D Euler, gamma = 1.4, the density bell of Sec. 5.3.1 on [-1, 1]^2 (one traversal of
     the domain per unit time)."""
     return Workload("eulerbell_N%d_%dx%d" % (N, m, m), 2, N, (m, m), EULER, (1.4,), SC_EULER_BELL,
                     euler_bell(), steps, lo=(-1.0, -1.0), hi=(1.0, 1.0))
 
 
 def euler2d_vortex(m=27, N=5, steps=100):
-    """2D Euler, gamma = 1.4, the static isentropic vortex of Sec. 4.3.2 on [-5, 5]^2."""
+    """2D Euler, gamma = 1.4, the static isentropic vortex of Sec. 5.3.2 on [-5, 5]^2."""
     return Workload("eulervortex_N%d_%dx%d" % (N, m, m), 2, N, (m, m), EULER, (1.4,), SC_EULER_VORTEX,
                     euler_vortex(), steps, lo=(-5.0, -5.0), hi=(5.0, 5.0))
 

@@ -1,12 +1,12 @@
-"""Precision studies in the manner of Sec. 5: run one workload to a final time in several
+"""Precision studies in the manner of Secs. 6 and 7: run one workload to a final time in several
 precision mixes through the C ABI and report the eq. (L2gauss) error against the closed form.
 
 ``python -m paper_2504_06889_gb300.study lake|bell|vortex [t_end]`` prints the table of one
 scenario on the paper's mesh (27^2 cells, order 5): per-kernel precisions with FP64 storage,
 and storage precisions with FP64 or FP32 kernels.  lake: the lake at rest (shallow water with
-bathymetry, Sec. 4.4, eta0 = 2, t = 1), the scenario the paper finds most sensitive to
-precision; bell: the advected density bell (2D Euler, Sec. 4.3.1, t = 2); vortex: the static
-isentropic vortex (Sec. 4.3.2, t = 10).
+bathymetry, Sec. 5.4, eta0 = 2, t = 1), the scenario the paper finds most sensitive to
+precision; bell: the advected density bell (2D Euler, Sec. 5.3.1, t = 2); vortex: the static
+isentropic vortex (Sec. 5.3.2, t = 10).
 """
 from __future__ import annotations
 
@@ -91,7 +91,7 @@ def lake_table(t_end=1.0, m=27, N=5, eta0=2.0, b0=0.0, mixes=LAKE_MIXES):
     return out
 
 
-# the 2D Euler scenarios of Sec. 4.3 on the paper's mesh and end times
+# the 2D Euler scenarios of Sec. 5.3 on the paper's mesh and end times
 SCENARIOS = {
     "lake": (lambda: I.swe2d_lake(), 1.0),
     "bell": (lambda: I.euler2d_bell(), 2.0),

@@ -1,4 +1,4 @@
-"""GPU Cauchy-Kowalevskaya predictor (linear PDEs, Sec. 2.1) against the oracle's CK
+"""GPU Cauchy-Kowalevskaya predictor (linear PDEs, Sec. 3.1) against the oracle's CK
 predictor, through the C ABI.
 
 Tolerances as for the Picard path: FP64 elementwise <= 1e-12 max|Q| (rounding order only);

@@ -1,4 +1,4 @@
-"""The 2D Euler scenarios of Sec. 4.3 (density bell, isentropic vortex) on the GPU against the
+"""The 2D Euler scenarios of Sec. 5.3 (density bell, isentropic vortex) on the GPU against the
 oracle: FP64 elementwise <= 1e-12 max|Q|, FP32 relative eq.-(L2gauss) distance <= 1e-5, and
 the device's error functional against the closed forms equal to the oracle's."""
 import numpy as np

@@ -1,4 +1,4 @@
-"""Storage precision of the persistent solution (Sec. 3.1 "storage") on the GPU, against the
+"""Storage precision of the persistent solution (Sec. 4.1 "storage") on the GPU, against the
 oracle with the same storage format.
 
 Both sides round the same FP64 sums to the format after each traversal.  The sums agree to

@@ -1,4 +1,4 @@
-"""The lake-at-rest precision study (Sec. 5, shallow water with bathymetry) on a short run:
+"""The lake-at-rest precision study (Secs. 6.3 and 7, shallow water with bathymetry) on a short run:
 the FP64 scheme stays well balanced, and the error grows as the precision of the kernels or
 of the stored solution drops."""
 import pytest

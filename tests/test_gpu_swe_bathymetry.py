@@ -1,4 +1,4 @@
-"""Shallow water with bathymetry (Sec. 4.4, non-conservative form, well-balanced Rusanov) on
+"""Shallow water with bathymetry (Sec. 5.4, non-conservative form, well-balanced Rusanov) on
 the GPU against the oracle.
 
 Tolerances as for the other PDEs: FP64 elementwise <= 1e-12 max|Q|; FP32 relative

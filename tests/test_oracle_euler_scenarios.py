@@ -1,4 +1,4 @@
-"""Pins of the two 2D Euler scenarios of Sec. 4.3 in the oracle.
+"""Pins of the two 2D Euler scenarios of Sec. 5.3 in the oracle.
 
 * Both closed forms solve the Euler equations: the space-time residual
   dQ/dt + div F(Q), taken by central differences of the oracle's exact solution and flux, is

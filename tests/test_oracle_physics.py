@@ -1,4 +1,4 @@
-"""Pins of the oracle's pointwise physics (Sec. 4 of arXiv 2504.06889).
+"""Pins of the oracle's pointwise physics (Sec. 5 of arXiv 2504.06889).
 
 The fluxes are checked through their eigenstructure, which is textbook and does
 not depend on how the flux is written: the Jacobian of F_dir must have the

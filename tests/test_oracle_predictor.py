@@ -1,4 +1,4 @@
-"""Pins of the oracle's space-time predictor (Sec. 2.1 of arXiv 2504.06889).
+"""Pins of the oracle's space-time predictor (Sec. 3.1 of arXiv 2504.06889).
 
 1. Brute force: for a linear PDE the Picard fixed point equals a dense solve of
    eq. (Picard), assembled here by direct quadrature of every integral in that

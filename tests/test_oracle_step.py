@@ -1,8 +1,8 @@
-"""Pins of the oracle's whole ADER-DG step (Sec. 2 and Algorithm 1 of arXiv 2504.06889).
+"""Pins of the oracle's whole ADER-DG step (Sec. 3 and Algorithm 1 of arXiv 2504.06889).
 
 Invariants (free stream, conservation of the cell-mean totals on periodic
 meshes, the Euler density wave's constant velocity and pressure), the observed
-convergence order N+1 against the analytic solutions of Sec. 4, the closed-form
+convergence order N+1 against the analytic solutions of Sec. 5, the closed-form
 time step of eq. (CFL_condition) for linear PDEs, and properties of eq. (L2gauss).
 """
 import os

@@ -1,4 +1,4 @@
-"""Pins of the oracle's storage precision (Sec. 3.1 "storage", Table precision_bits).
+"""Pins of the oracle's storage precision (Sec. 4.1 "storage", Table precision_bits).
 
 The rounding to a format is checked against library conversions (numpy's float32 and float16
 casts, both round to nearest with ties to even) and, for bf16, which numpy lacks, against

@@ -1,4 +1,4 @@
-"""Pins of the oracle's shallow-water form with bathymetry (Sec. 4.4): conservative fluxes of
+"""Pins of the oracle's shallow-water form with bathymetry (Sec. 5.4): conservative fluxes of
 eq. (swe_cons), the non-conservative product of eq. (swe_noncons), the well-balanced Rusanov
 flux of eq. (swe_custom_riemann) with its path-conservative jump term, the lake at rest of
 eq. (lake_initial).

@@ -1,6 +1,6 @@
 """Pins of the oracle's 1D tables against library routines and closed forms.
 
-Sec. 2, eq. (piecewise_solution) of arXiv 2504.06889: tensor-product Lagrange
+Sec. 3, eq. (piecewise_solution) of arXiv 2504.06889: tensor-product Lagrange
 polynomials on Gauss-Legendre support points; eq. (Picard) for the time operator.
 """
 import numpy as np
