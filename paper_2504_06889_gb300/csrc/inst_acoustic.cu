@@ -2,7 +2,6 @@
 #include "adg_kernels.cuh"
 #include "adg_tc.cuh"
 #include "adg_adjoint.cuh"
-#include "adg_tc_sweep.cuh"
 #include "adg_refine.cuh"
 
 namespace adg {
@@ -24,7 +23,6 @@ void register_acoustic() {
   {
     Entry e = make_entry<0, 3, 4, false>();
     add_tc<0, 3, 4>(e);
-    add_tcs<0, 4>(e);
     add_refine<0, 3, 4>(e);
     add_ck<0, 3, 4>(e);
     add_adjoint<3, 4>(e);
@@ -38,7 +36,6 @@ void register_acoustic() {
   {
     Entry e = make_entry<0, 3, 2, false>();
     add_tc<0, 3, 2>(e);
-    add_tcs<0, 2>(e);
     add_ck<0, 3, 2>(e);
     add_adjoint<3, 2>(e);
     register_entry(e);
