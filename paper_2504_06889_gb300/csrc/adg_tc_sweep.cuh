@@ -133,7 +133,8 @@ __device__ __forceinline__ void put_row(unsigned char* Ad, int row, int m, const
 }  // namespace tc
 
 template <class C, class TIN, class TS>
-__global__ void __launch_bounds__(TsCfg<C>::THREADS, TsCfg<C>::THREADS > 128 ? 2 : 1) k_predictor_tcs(const __grid_constant__ StepArgs a) {
+__global__ void __launch_bounds__(TsCfg<C>::THREADS, TsCfg<C>::THREADS > 128 ? 2 : 1)
+    k_predictor_tcs(const __grid_constant__ StepArgs a) {
   using Ph = Phys<C::PDE, C::D>;
   using G = TsCfg<C>;
   constexpr int n = C::n, V = C::V, NS = C::NS, n2 = n * n;
@@ -280,223 +281,226 @@ __global__ void __launch_bounds__(TsCfg<C>::THREADS, TsCfg<C>::THREADS > 128 ? 2
 
   // ---- persistent loop over the cells -------------------------------------------------------------
   for (int cell = blockIdx.x; cell < a.ncells && !stop; cell += gridDim.x) {
-  __syncthreads();  // the previous cell is finished with the shared scalars
-  if (tid == 0) {
-    s_fmax[0] = s_fmax[1] = s_fmax[2] = 0u;
-    s_rmax[0] = s_rmax[1] = s_rmax[2] = 0u;
-  }
-  const PP<float> pp = make_pp<float>(a.pp, cell);
-  float Qh[V];
-  {
-    const double* Qc = a.Q + (size_t)cell * V * NS;
-#pragma unroll
-    for (int v = 0; v < V; ++v) Qh[v] = (float)Qc[v * NS + i];
-  }
-  if (tid == 0) {
-    float F[3][V];
-    Ph::flux(pp, Qh, F);
-#pragma unroll
-    for (int d = 0; d < 3; ++d)
-#pragma unroll
-      for (int v = 0; v < V; ++v) s_fc[d][v] = F[d][v];
-  }
-  __syncthreads();
-  if (owner) {  // scale of the first sweep: max |F(Q) - offset|
-    float F[3][V];
-    Ph::flux(pp, Qh, F);
-#pragma unroll
-    for (int d = 0; d < 3; ++d)
-#pragma unroll
-      for (int v = 0; v < V; ++v) F[d][v] -= s_fc[d][v];
-    atomicMax(&s_fmax[2], __float_as_uint(fmax_of(F)));
-  }
-  __syncthreads();
-  float q[n][V];
-#pragma unroll
-  for (int k = 0; k < n; ++k)
-#pragma unroll
-    for (int v = 0; v < V; ++v) q[k][v] = Qh[v];
-
-  for (int r = 0; r < a.picard_iters && !stop; ++r) {
-    const bool comp = r >= a.picard_iters - a.comp_sweeps;
-    const int npass = comp ? 2 : 1;
-    const bool first = r == 0;
-    const int nk = first ? 1 : n;  // time nodes with distinct fluxes
-    const float scF = scale_from(s_fmax[(r + 2) % 3]);
+    __syncthreads();  // the previous cell is finished with the shared scalars
     if (tid == 0) {
-      s_fmax[(r + 1) % 3] = 0u;
-      s_rmax[(r + 1) % 3] = 0u;
+      s_fmax[0] = s_fmax[1] = s_fmax[2] = 0u;
+      s_rmax[0] = s_rmax[1] = s_rmax[2] = 0u;
     }
-    // ---- spatial round: A_dir rows (k, pencil) <- F_dir(q_k) -------------------------------------
-    for (int pass = 0; pass < npass; ++pass) {
-      if (owner) {
-        float fmx = 0.0f;
-        // one time node per iteration, always q[0]: the iterate is rotated by one slot per
-        // iteration (n rotations restore it), so the loop is not unrolled and registers hold
-        // one iteration's values
+    const PP<float> pp = make_pp<float>(a.pp, cell);
+    float Qh[V];
+    {
+      const double* Qc = a.Q + (size_t)cell * V * NS;
+#pragma unroll
+      for (int v = 0; v < V; ++v) Qh[v] = (float)Qc[v * NS + i];
+    }
+    if (tid == 0) {
+      float F[3][V];
+      Ph::flux(pp, Qh, F);
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int v = 0; v < V; ++v) s_fc[d][v] = F[d][v];
+    }
+    __syncthreads();
+    if (owner) {  // scale of the first sweep: max |F(Q) - offset|
+      float F[3][V];
+      Ph::flux(pp, Qh, F);
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int v = 0; v < V; ++v) F[d][v] -= s_fc[d][v];
+      atomicMax(&s_fmax[2], __float_as_uint(fmax_of(F)));
+    }
+    __syncthreads();
+    float q[n][V];
+#pragma unroll
+    for (int k = 0; k < n; ++k)
+#pragma unroll
+      for (int v = 0; v < V; ++v) q[k][v] = Qh[v];
+
+    for (int r = 0; r < a.picard_iters && !stop; ++r) {
+      const bool comp = r >= a.picard_iters - a.comp_sweeps;
+      const int npass = comp ? 2 : 1;
+      const bool first = r == 0;
+      const int nk = first ? 1 : n;  // time nodes with distinct fluxes
+      const float scF = scale_from(s_fmax[(r + 2) % 3]);
+      if (tid == 0) {
+        s_fmax[(r + 1) % 3] = 0u;
+        s_rmax[(r + 1) % 3] = 0u;
+      }
+      // ---- spatial round: A_dir rows (k, pencil) <- F_dir(q_k) -------------------------------------
+      for (int pass = 0; pass < npass; ++pass) {
+        if (owner) {
+          float fmx = 0.0f;
+          // one time node per iteration, always q[0]: the iterate is rotated by one slot per
+          // iteration (n rotations restore it), so the loop is not unrolled and registers hold
+          // one iteration's values
 #pragma unroll 1
-        for (int k = 0; k < n; ++k) {
-          if (k < nk) {
-            float F[3][V];
-            Ph::flux(pp, q[0], F);
+          for (int k = 0; k < n; ++k) {
+            if (k < nk) {
+              float F[3][V];
+              Ph::flux(pp, q[0], F);
+#pragma unroll
+              for (int d = 0; d < 3; ++d)
+#pragma unroll
+                for (int v = 0; v < V; ++v) F[d][v] -= s_fc[d][v];
+              if (per_cell_scale) fmx = fmaxf(fmx, fmax_of(F));
+#pragma unroll
+              for (int d = 0; d < 3; ++d) {
+                float x[V];
+#pragma unroll
+                for (int v = 0; v < V; ++v) x[v] = per_cell_scale ? F[d][v] * scF : F[d][v];
+                if (pass == 0)
+                  tc::put_row<TIN, n, V, ABUF, false>(Abuf + d * KSTEPS * ABUF, k * n2 + pen[d], idx[d], x);
+                else
+                  tc::put_row<TIN, n, V, ABUF, true>(Abuf + d * KSTEPS * ABUF, k * n2 + pen[d], idx[d], x);
+              }
+            }
+            float t0[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) t0[v] = q[0][v];
+#pragma unroll
+            for (int kk = 0; kk + 1 < n; ++kk)
+#pragma unroll
+              for (int v = 0; v < V; ++v) q[kk][v] = q[kk + 1][v];
+#pragma unroll
+            for (int v = 0; v < V; ++v) q[n - 1][v] = t0[v];
+          }
+          if (per_cell_scale && pass == 0) atomicMax(&s_fmax[r % 3], __float_as_uint(fmx));
+        }
+        tc::fence_async_smem();
+        tc::fence_before();
+        __syncthreads();
+        if (s_timeout) {
+          stop = true;
+          break;
+        }
+        if (tid == 0) {
+          tc::fence_after();
+          const uint32_t ab = launder(a_base), bb = launder(b_base);
+          const int mts = first ? 1 : MT;
+#pragma unroll
+          for (int d = 0; d < 3; ++d)
+            for (int mt = 0; mt < mts; ++mt)
+#pragma unroll
+              for (int ks = 0; ks < KSTEPS; ++ks) {
+                const uint32_t dt_ = tmem + (uint32_t)((d * MT + mt) * NC);
+                const int bt = G::B_SP + (d * KSTEPS + ks) * 2;
+                if (pass == 0) {
+                  tc::mma<TIN>(dt_, adesc(ab, d, ks, mt), bdesc(bb, bt), idesc, ks > 0 ? 1u : 0u);
+                  if (comp) tc::mma<TIN>(dt_, adesc(ab, d, ks, mt), bdesc(bb, bt + 1), idesc, 1u);
+                } else {
+                  tc::mma<TIN>(dt_, adesc(ab, d, ks, mt), bdesc(bb, bt), idesc, 1u);
+                }
+              }
+          tc::commit(&s_mbar);
+        }
+        wait_mma();
+      }
+      if (stop) break;
+      // ---- R_dir back from TMEM (row = (k, pencil) of this thread) -----------------------------------
+      // The scale of R follows the previous sweep's max |R|; the first sweep finds its own first.
+      const bool rows_live = first ? (warp * 32 < n2) : (warp * 32 < NS);  // warp-uniform
+      if (per_cell_scale && first) {
+        if (rows_live) {
+          float mm = 0.0f;
+#pragma unroll 1
+          for (int d = 0; d < 3; ++d) {
+            float o[NC];
+            tc::ldc<NC>(tmem + tlane + (uint32_t)((d * MT + wtile) * NC), o);
+#pragma unroll
+            for (int j = 0; j < G::KC; ++j) mm = fmaxf(mm, fabsf(o[j]));
+          }
+          if (tid < n2) atomicMax(&s_rmax[2], __float_as_uint(mm / scF));
+        }
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+      }
+      // R in the time operand: R_true = o / scF, scaled by scR with max |R scR| in [1, 2)
+      const float scR = per_cell_scale ? scale_from(s_rmax[(r + 2) % 3]) : 1.0f;
+      const float ratio = scR / scF;
+      // ---- time round: A_t rows (node) <- R_dir(k, node) ----------------------------------------------
+      for (int pass = 0; pass < npass; ++pass) {
+        if (rows_live) {
+          float rmx = 0.0f;
+#pragma unroll 1
+          for (int d = 0; d < 3; ++d) {
+            float o[NC];
+            tc::ldc<NC>(tmem + tlane + (uint32_t)((d * MT + wtile) * NC), o);
+            if (per_cell_scale && pass == 0) {
+#pragma unroll
+              for (int j = 0; j < G::KC; ++j) rmx = fmaxf(rmx, fabsf(o[j]));
+            }
+            if (tid < (first ? n2 : NS)) {
+              unsigned char* Ad = Abuf + d * KSTEPS * ABUF;
+#pragma unroll
+              for (int oo = 0; oo < n; ++oo) {
+                float x[V];
+#pragma unroll
+                for (int v = 0; v < V; ++v) x[v] = per_cell_scale ? o[tcs_col<n>(oo, v)] * ratio : o[tcs_col<n>(oo, v)];
+                if (pass == 0)
+                  tc::put_row<TIN, n, V, ABUF, false>(Ad, node_on(d, oo), kr, x);
+                else
+                  tc::put_row<TIN, n, V, ABUF, true>(Ad, node_on(d, oo), kr, x);
+              }
+            }
+          }
+          if (per_cell_scale && pass == 0 && tid < (first ? n2 : NS))
+            atomicMax(&s_rmax[r % 3], __float_as_uint(rmx / scF));
+        }
+        tc::fence_async_smem();
+        tc::fence_before();
+        __syncthreads();
+        if (s_timeout) {
+          stop = true;
+          break;
+        }
+        if (tid == 0) {
+          tc::fence_after();
+          const uint32_t ab = launder(a_base), bb = launder(b_base);
+          const int bt0 = first ? G::B_T0 : G::B_T;
+#pragma unroll
+          for (int mt = 0; mt < MT; ++mt) {
+            const uint32_t dt_ = tmem + (uint32_t)(G::TCOL_T + mt * NC);
 #pragma unroll
             for (int d = 0; d < 3; ++d)
 #pragma unroll
-              for (int v = 0; v < V; ++v) F[d][v] -= s_fc[d][v];
-            if (per_cell_scale) fmx = fmaxf(fmx, fmax_of(F));
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-              float x[V];
-#pragma unroll
-              for (int v = 0; v < V; ++v) x[v] = per_cell_scale ? F[d][v] * scF : F[d][v];
-              if (pass == 0)
-                tc::put_row<TIN, n, V, ABUF, false>(Abuf + d * KSTEPS * ABUF, k * n2 + pen[d], idx[d], x);
-              else
-                tc::put_row<TIN, n, V, ABUF, true>(Abuf + d * KSTEPS * ABUF, k * n2 + pen[d], idx[d], x);
-            }
-          }
-          float t0[V];
-#pragma unroll
-          for (int v = 0; v < V; ++v) t0[v] = q[0][v];
-#pragma unroll
-          for (int kk = 0; kk + 1 < n; ++kk)
-#pragma unroll
-            for (int v = 0; v < V; ++v) q[kk][v] = q[kk + 1][v];
-#pragma unroll
-          for (int v = 0; v < V; ++v) q[n - 1][v] = t0[v];
-        }
-        if (per_cell_scale && pass == 0) atomicMax(&s_fmax[r % 3], __float_as_uint(fmx));
-      }
-      tc::fence_async_smem();
-      tc::fence_before();
-      __syncthreads();
-      if (s_timeout) {
-        stop = true;
-        break;
-      }
-      if (tid == 0) {
-        tc::fence_after();
-        const uint32_t ab = launder(a_base), bb = launder(b_base);
-        const int mts = first ? 1 : MT;
-#pragma unroll
-        for (int d = 0; d < 3; ++d)
-          for (int mt = 0; mt < mts; ++mt)
-#pragma unroll
-            for (int ks = 0; ks < KSTEPS; ++ks) {
-              const uint32_t dt_ = tmem + (uint32_t)((d * MT + mt) * NC);
-              const int bt = G::B_SP + (d * KSTEPS + ks) * 2;
-              if (pass == 0) {
-                tc::mma<TIN>(dt_, adesc(ab, d, ks, mt), bdesc(bb, bt), idesc, ks > 0 ? 1u : 0u);
-                if (comp) tc::mma<TIN>(dt_, adesc(ab, d, ks, mt), bdesc(bb, bt + 1), idesc, 1u);
-              } else {
-                tc::mma<TIN>(dt_, adesc(ab, d, ks, mt), bdesc(bb, bt), idesc, 1u);
+              for (int ks = 0; ks < KSTEPS; ++ks) {
+                const int bt = bt0 + ks * 2;
+                if (pass == 0) {
+                  tc::mma<TIN>(dt_, adesc(ab, d, ks, mt), bdesc(bb, bt), idesc, (d > 0 || ks > 0) ? 1u : 0u);
+                  if (comp) tc::mma<TIN>(dt_, adesc(ab, d, ks, mt), bdesc(bb, bt + 1), idesc, 1u);
+                } else {
+                  tc::mma<TIN>(dt_, adesc(ab, d, ks, mt), bdesc(bb, bt), idesc, 1u);
+                }
               }
-            }
-        tc::commit(&s_mbar);
-      }
-      wait_mma();
-    }
-    if (stop) break;
-    // ---- R_dir back from TMEM (row = (k, pencil) of this thread) -----------------------------------
-    // The scale of R follows the previous sweep's max |R|; the first sweep finds its own first.
-    const bool rows_live = first ? (warp * 32 < n2) : (warp * 32 < NS);  // warp-uniform
-    if (per_cell_scale && first) {
-      if (rows_live) {
-        float mm = 0.0f;
-#pragma unroll 1
-        for (int d = 0; d < 3; ++d) {
-          float o[NC];
-          tc::ldc<NC>(tmem + tlane + (uint32_t)((d * MT + wtile) * NC), o);
-#pragma unroll
-          for (int j = 0; j < G::KC; ++j) mm = fmaxf(mm, fabsf(o[j]));
+          }
+          tc::commit(&s_mbar);
         }
-        if (tid < n2) atomicMax(&s_rmax[2], __float_as_uint(mm / scF));
+        wait_mma();
+      }
+      if (stop) break;
+      // ---- q_k = Q - (sum_l dt P[k][l] R_l) at this thread's node --------------------------------------
+      if (warp * 32 < NS) {
+        float o[NC];
+        tc::ldc<NC>(tmem + tlane + (uint32_t)(G::TCOL_T + wtile * NC), o);
+        const float inv = 1.0f / scR;
+#pragma unroll
+        for (int k = 0; k < n; ++k)
+#pragma unroll
+          for (int v = 0; v < V; ++v) {
+            const float acc = o[tcs_col<n>(k, v)];
+            q[k][v] = Qh[v] - (per_cell_scale ? acc * inv : acc);
+          }
       }
       tc::fence_before();
-      __syncthreads();
+      __syncthreads();  // accumulators read before the next sweep's MMAs; max |F| complete
       tc::fence_after();
     }
-    // R in the time operand: R_true = o / scF, scaled by scR with max |R scR| in [1, 2)
-    const float scR = per_cell_scale ? scale_from(s_rmax[(r + 2) % 3]) : 1.0f;
-    const float ratio = scR / scF;
-    // ---- time round: A_t rows (node) <- R_dir(k, node) ----------------------------------------------
-    for (int pass = 0; pass < npass; ++pass) {
-      if (rows_live) {
-        float rmx = 0.0f;
-#pragma unroll 1
-        for (int d = 0; d < 3; ++d) {
-          float o[NC];
-          tc::ldc<NC>(tmem + tlane + (uint32_t)((d * MT + wtile) * NC), o);
-          if (per_cell_scale && pass == 0) {
-#pragma unroll
-            for (int j = 0; j < G::KC; ++j) rmx = fmaxf(rmx, fabsf(o[j]));
-          }
-          if (tid < (first ? n2 : NS)) {
-            unsigned char* Ad = Abuf + d * KSTEPS * ABUF;
-#pragma unroll
-            for (int oo = 0; oo < n; ++oo) {
-              float x[V];
-#pragma unroll
-              for (int v = 0; v < V; ++v) x[v] = per_cell_scale ? o[tcs_col<n>(oo, v)] * ratio : o[tcs_col<n>(oo, v)];
-              if (pass == 0)
-                tc::put_row<TIN, n, V, ABUF, false>(Ad, node_on(d, oo), kr, x);
-              else
-                tc::put_row<TIN, n, V, ABUF, true>(Ad, node_on(d, oo), kr, x);
-            }
-          }
-        }
-        if (per_cell_scale && pass == 0 && tid < (first ? n2 : NS))
-          atomicMax(&s_rmax[r % 3], __float_as_uint(rmx / scF));
-      }
-      tc::fence_async_smem();
-      tc::fence_before();
-      __syncthreads();
-      if (s_timeout) {
-        stop = true;
-        break;
-      }
-      if (tid == 0) {
-        tc::fence_after();
-        const uint32_t ab = launder(a_base), bb = launder(b_base);
-        const int bt0 = first ? G::B_T0 : G::B_T;
-#pragma unroll
-        for (int mt = 0; mt < MT; ++mt) {
-          const uint32_t dt_ = tmem + (uint32_t)(G::TCOL_T + mt * NC);
-#pragma unroll
-          for (int d = 0; d < 3; ++d)
-#pragma unroll
-            for (int ks = 0; ks < KSTEPS; ++ks) {
-              const int bt = bt0 + ks * 2;
-              if (pass == 0) {
-                tc::mma<TIN>(dt_, adesc(ab, d, ks, mt), bdesc(bb, bt), idesc, (d > 0 || ks > 0) ? 1u : 0u);
-                if (comp) tc::mma<TIN>(dt_, adesc(ab, d, ks, mt), bdesc(bb, bt + 1), idesc, 1u);
-              } else {
-                tc::mma<TIN>(dt_, adesc(ab, d, ks, mt), bdesc(bb, bt), idesc, 1u);
-              }
-            }
-        }
-        tc::commit(&s_mbar);
-      }
-      wait_mma();
-    }
     if (stop) break;
-    // ---- q_k = Q - (sum_l dt P[k][l] R_l) at this thread's node --------------------------------------
-    if (warp * 32 < NS) {
-      float o[NC];
-      tc::ldc<NC>(tmem + tlane + (uint32_t)(G::TCOL_T + wtile * NC), o);
-      const float inv = 1.0f / scR;
-#pragma unroll
-      for (int k = 0; k < n; ++k)
-#pragma unroll
-        for (int v = 0; v < V; ++v) q[k][v] = per_cell_scale ? Qh[v] - o[tcs_col<n>(k, v)] * inv : Qh[v] - o[tcs_col<n>(k, v)];
-    }
-    tc::fence_before();
-    __syncthreads();  // accumulators read before the next sweep's MMAs; max |F| complete
-    tc::fence_after();
-  }
-  if (stop) break;
-  predictor_final<C, float, float, TS>(a, q, sFin, sVm, sw, sp0, sp1, dt, 0, i, cell, true, cell, idx, pb,
-                                       owner);
+    predictor_final<C, float, float, TS>(a, q, sFin, sVm, sw, sp0, sp1, dt, 0, i, cell, true, cell, idx, pb,
+                                         owner);
   }  // cells
   tc::fence_before();
   __syncthreads();
