@@ -826,29 +826,57 @@ __global__ void __launch_bounds__(C::THREADS) k_corrector(const __grid_constant_
 // ------------------------------------------------------------------------------------------------
 template <class C>
 __global__ void k_lambda(const __grid_constant__ StepArgs a) {
+  // lambda_max(Q) exactly in FP64, with the FP64 spectral radius (FP64 division and square
+  // root, slow on this part) evaluated only where it can matter: a first pass takes the FP32
+  // estimate of every node of this block's share and their maximum; a second pass evaluates
+  // FP64 only on the nodes whose estimate is within 1e-4 (relative) of that maximum, or whose
+  // estimate is unreliable.  The FP32 relative error is far below 1e-4 for well-conditioned
+  // states, so the block's FP64 maximum is among them.
   using Ph = Phys<C::PDE, C::D>;
   constexpr int V = C::V, NS = C::NS;
   __shared__ unsigned long long s_lam;
-  __shared__ unsigned int s_bad;
+  __shared__ unsigned int s_bad, s_l32;
   if (threadIdx.x == 0) {
     s_lam = 0ull;
     s_bad = 0u;
+    s_l32 = 0u;
   }
   __syncthreads();
-  double lam = 0.0;
-  bool bad = false;
   const size_t total = (size_t)a.ncells * NS;
-  for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < total;
-       g += (size_t)gridDim.x * blockDim.x) {
-    const int cell = (int)(g / NS), i = (int)(g % NS);
-    double q[V];
+  const size_t first = blockIdx.x * (size_t)blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
+  auto load = [&](size_t g, double* q, float* qf, int& cell) {
+    cell = (int)(g / NS);
+    const int i = (int)(g % NS);
 #pragma unroll
     for (int v = 0; v < V; ++v) {
       q[v] = a.Q[((size_t)cell * V + v) * NS + i];
-      bad |= !isfinite(q[v]);
+      qf[v] = (float)q[v];
     }
-    const PP<double> pd = make_pp<double>(a.pp, cell);
-    lam = fmax(lam, Ph::maxspeed(pd, q));
+  };
+  bool bad = false;
+  float est = 0.0f;
+  for (size_t g = first; g < total; g += stride) {
+    double q[V];
+    float qf[V];
+    int cell;
+    load(g, q, qf, cell);
+#pragma unroll
+    for (int v = 0; v < V; ++v) bad |= !isfinite(q[v]);
+    const float l32 = Ph::maxspeed(make_pp<float>(a.pp, cell), qf);
+    if (l32 < 3.0e38f && !Ph::speed_is_ill_conditioned(qf)) est = fmaxf(est, l32);
+  }
+  atomicMax(&s_l32, __float_as_uint(est));
+  __syncthreads();
+  const float thr = __uint_as_float(s_l32) * (1.0f - 1.0e-4f);
+  double lam = 0.0;
+  for (size_t g = first; g < total; g += stride) {
+    double q[V];
+    float qf[V];
+    int cell;
+    load(g, q, qf, cell);
+    const float l32 = Ph::maxspeed(make_pp<float>(a.pp, cell), qf);
+    const bool risky = !(l32 < 3.0e38f) || Ph::speed_is_ill_conditioned(qf);
+    if (risky || l32 >= thr) lam = fmax(lam, Ph::maxspeed(make_pp<double>(a.pp, cell), q));
   }
   bad |= !isfinite(lam);
   if (!bad) atomicMax(&s_lam, (unsigned long long)__double_as_longlong(lam));
