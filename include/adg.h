@@ -141,9 +141,13 @@ ADG_API int adg_set_pde(adg_ctx* c, int pde, const double* params, int nparams);
 /* Precision of one kernel (Sec. 4.1).  Built combinations:
  *   PICARD     FP64, FP32 (SIMT, must equal PREDICTOR); BF16, FP16, FP8E4M3 with PREDICTOR
  *              FP32 (tensor cores, FP32 accumulation, 3D meshes, CORRECTOR FP32 or FP64; flags
- *              (ADG_F_*) given with the PICARD call select compensation and per-cell scaling);
+ *              (ADG_F_*) given with the PICARD call select compensation and per-cell scaling;
+ *              the operands hold F - F_c, F_c the flux at the cell's first node, which the
+ *              derivative annihilates; 3D Euler runs whole sweeps per MMA round, the other
+ *              PDEs and E4M3 one round per time slice);
  *              BF16 with PREDICTOR BF16: the whole predictor in bf16 arithmetic (SIMT, built
- *              for shallow water)
+ *              for shallow water); FP32 or BF16 with PREDICTOR FP64 and adg_set_refinement:
+ *              low-precision sweeps refined by FP64 sweeps
  *   PREDICTOR  FP64, FP32, BF16 (see PICARD)
  *   RIEMANN    FP64, FP32, BF16 (bf16 built for shallow water)
  *   CORRECTOR  FP64, FP32, BF16 (bf16 built for shallow water)
