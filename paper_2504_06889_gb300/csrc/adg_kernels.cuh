@@ -378,6 +378,82 @@ __device__ __forceinline__ void ncp_at_node(const PP<T>& pp, const T* sF, const 
   }
 }
 
+// One Picard sweep of eq. (Picard) in arithmetic T on the node-per-thread layout: q (this
+// node's iterate at every time node) is replaced by Q - dt P R(q), R_k = sum_dir D_dir F_dir(q_k)
+// (plus the non-conservative product B(q_k) grad q_k where the PDE has one).  first: every time
+// node holds Q, so one flux slice serves all of them (q = Q - dt (sum_l P[k][l]) R).  buf is the
+// double-buffer index of the flux slices: one barrier per slice.
+template <class C, class T>
+__device__ __forceinline__ void picard_sweep(T (&q)[C::n][C::V], const T (&Qh)[C::V], T* sFbuf, const T* sdtP,
+                                             const T* sdtProw, const T (&Dr)[C::D][Pencil<C>::S], const PP<T>& pp,
+                                             const int* pb, const int* idx, int lc, bool first, int& buf) {
+  using Ph = Phys<C::PDE, C::D>;
+  constexpr int n = C::n, V = C::V, D = C::D, VX = C::VX;
+  constexpr int S = Pencil<C>::S, PD = Pencil<C>::PER_DIR;
+  constexpr size_t bufsz = (size_t)C::CPB * D * VX * PD;
+  auto write_slice = [&](T* sF, const T* qk) {
+    T F[D][V];
+    Ph::flux(pp, qk, F);
+#pragma unroll
+    for (int dir = 0; dir < D; ++dir)
+#pragma unroll
+      for (int v = 0; v < V; ++v)
+        if (Ph::nz(dir, v)) sF[(dir * VX + v) * PD + pb[dir] + idx[dir]] = F[dir][v];
+    write_ncp_pencils<C>(sF, qk, pb, idx);
+  };
+  auto deriv = [&](const T* sF, const T* ncpv, int v) {
+    T rv = ncpv[v];
+#pragma unroll
+    for (int dir = 0; dir < D; ++dir) {
+      if (!Ph::nz(dir, v)) continue;
+      T f[S];
+      VecLoad<T, S>::load(sF + (dir * VX + v) * PD + pb[dir], f);
+#pragma unroll
+      for (int m = 0; m < n; ++m) rv += Dr[dir][m] * f[m];
+    }
+    return rv;
+  };
+  if (first) {
+    T* sF = sFbuf + buf * bufsz + (size_t)lc * D * VX * PD;
+    write_slice(sF, Qh);
+    __syncthreads();
+    T ncpv[V];
+    ncp_at_node<C>(pp, sF, Qh, pb, Dr, ncpv);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const T rv = deriv(sF, ncpv, v);
+#pragma unroll
+      for (int kk = 0; kk < n; ++kk) q[kk][v] = Qh[v] - sdtProw[kk] * rv;
+    }
+    buf ^= 1;
+    return;
+  }
+  T qn[n][V];
+#pragma unroll
+  for (int k = 0; k < n; ++k)
+#pragma unroll
+    for (int v = 0; v < V; ++v) qn[k][v] = Qh[v];
+#pragma unroll
+  for (int k = 0; k < n; ++k) {
+    T* sF = sFbuf + buf * bufsz + (size_t)lc * D * VX * PD;
+    write_slice(sF, q[k]);
+    __syncthreads();
+    T ncpv[V];
+    ncp_at_node<C>(pp, sF, q[k], pb, Dr, ncpv);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const T rv = deriv(sF, ncpv, v);
+#pragma unroll
+      for (int kk = 0; kk < n; ++kk) qn[kk][v] -= sdtP[kk * n + k] * rv;
+    }
+    buf ^= 1;  // the next slice writes the other buffer
+  }
+#pragma unroll
+  for (int k = 0; k < n; ++k)
+#pragma unroll
+    for (int v = 0; v < V; ++v) q[k][v] = qn[k][v];
+}
+
 // ------------------------------------------------------------------------------------------------
 // predictor + volume integral + face traces
 // CK = false: Picard sweeps (Sec. 3.1, eq. Picard).  CK = true: Cauchy-Kowalevskaya for the
@@ -518,83 +594,10 @@ __global__ void __launch_bounds__(C::THREADS) k_predictor(const __grid_constant_
       buf ^= 1;  // double buffering: one barrier per derivative
     }
   }
-  // Sweep 1 starts from q = Q at every time node, so all time slices share one flux and one
-  // derivative R: q^1[kk] = Q - dt (sum_l P[kk][l]) R.
-  if (!CK && a.picard_iters > 0) {
-    T* sF = sFbuf + (size_t)lc * D * VX * PD;
-    {
-      T F[D][V];
-      Ph::flux(pp, Qh, F);
-#pragma unroll
-      for (int dir = 0; dir < D; ++dir)
-#pragma unroll
-        for (int v = 0; v < V; ++v)
-          if (Ph::nz(dir, v)) sF[(dir * VX + v) * PD + pb[dir] + idx[dir]] = F[dir][v];
-      write_ncp_pencils<C>(sF, Qh, pb, idx);
-    }
-    __syncthreads();
-    T ncpv[V];
-    ncp_at_node<C>(pp, sF, Qh, pb, Dr, ncpv);
-#pragma unroll
-    for (int v = 0; v < V; ++v) {
-      T rv = ncpv[v];
-#pragma unroll
-      for (int dir = 0; dir < D; ++dir) {
-        if (!Ph::nz(dir, v)) continue;
-        T f[S];
-        VecLoad<T, S>::load(sF + (dir * VX + v) * PD + pb[dir], f);
-#pragma unroll
-        for (int m = 0; m < n; ++m) rv += Dr[dir][m] * f[m];
-      }
-#pragma unroll
-      for (int kk = 0; kk < n; ++kk) q[kk][v] = Qh[v] - sdtProw[kk] * rv;
-    }
-    buf = 1;
-  }
-  for (int r = 1; !CK && r < a.picard_iters; ++r) {
-    T qn[n][V];
-#pragma unroll
-    for (int k = 0; k < n; ++k)
-#pragma unroll
-      for (int v = 0; v < V; ++v) qn[k][v] = Qh[v];
-#pragma unroll
-    for (int k = 0; k < n; ++k) {
-      T* sF = sFbuf + buf * bufsz + (size_t)lc * D * VX * PD;
-      {
-        T F[D][V];
-        Ph::flux(pp, q[k], F);
-#pragma unroll
-        for (int dir = 0; dir < D; ++dir)
-#pragma unroll
-          for (int v = 0; v < V; ++v)
-            if (Ph::nz(dir, v)) sF[(dir * VX + v) * PD + pb[dir] + idx[dir]] = F[dir][v];
-        write_ncp_pencils<C>(sF, q[k], pb, idx);
-      }
-      __syncthreads();
-      T ncpv[V];
-      ncp_at_node<C>(pp, sF, q[k], pb, Dr, ncpv);
-#pragma unroll
-      for (int v = 0; v < V; ++v) {
-        T rv = ncpv[v];
-#pragma unroll
-        for (int dir = 0; dir < D; ++dir) {
-          if (!Ph::nz(dir, v)) continue;
-          T f[S];
-          VecLoad<T, S>::load(sF + (dir * VX + v) * PD + pb[dir], f);
-#pragma unroll
-          for (int m = 0; m < n; ++m) rv += Dr[dir][m] * f[m];
-        }
-        // q_new[kk] = Q - dt sum_l P[kk][l] R_l  (column l = k)
-#pragma unroll
-        for (int kk = 0; kk < n; ++kk) qn[kk][v] -= sdtP[kk * n + k] * rv;
-      }
-      buf ^= 1;  // the next slice writes the other buffer: one barrier per slice
-    }
-#pragma unroll
-    for (int k = 0; k < n; ++k)
-#pragma unroll
-      for (int v = 0; v < V; ++v) q[k][v] = qn[k][v];
-  }
+  // Picard sweeps (eq. Picard); the first starts from q = Q at every time node
+  if (!CK && a.picard_iters > 0) picard_sweep<C, T>(q, Qh, sFbuf, sdtP, sdtProw, Dr, pp, pb, idx, lc, true, buf);
+  for (int r = 1; !CK && r < a.picard_iters; ++r)
+    picard_sweep<C, T>(q, Qh, sFbuf, sdtP, sdtProw, Dr, pp, pb, idx, lc, false, buf);
   __syncthreads();
 
   predictor_final<C, T, TP, TS, TQ>(a, q, reinterpret_cast<TP*>(smem_raw), sVm, sw, sp0, sp1, dt, lc, i,

@@ -15,76 +15,6 @@
 
 namespace adg {
 
-// One Picard sweep in arithmetic T on the node-per-thread layout: q (this node's iterate at
-// every time node) is replaced by Q - dt P R(q).  first: every time node holds Q, so one flux
-// slice serves all of them.  buf is the double-buffer index of the flux slices (one barrier
-// per slice).
-template <class C, class T>
-__device__ __forceinline__ void picard_sweep(T (&q)[C::n][C::V], const T (&Qh)[C::V], T* sFbuf, const T* sdtP,
-                                             const T* sdtProw, const T (&Dr)[C::D][Pencil<C>::S], const PP<T>& pp,
-                                             const int* pb, const int* idx, int lc, bool first, int& buf) {
-  using Ph = Phys<C::PDE, C::D>;
-  constexpr int n = C::n, V = C::V, D = C::D, VX = C::VX;
-  constexpr int S = Pencil<C>::S, PD = Pencil<C>::PER_DIR;
-  constexpr size_t bufsz = (size_t)C::CPB * D * VX * PD;
-  auto write_slice = [&](T* sF, const T* qk) {
-    T F[D][V];
-    Ph::flux(pp, qk, F);
-#pragma unroll
-    for (int dir = 0; dir < D; ++dir)
-#pragma unroll
-      for (int v = 0; v < V; ++v)
-        if (Ph::nz(dir, v)) sF[(dir * VX + v) * PD + pb[dir] + idx[dir]] = F[dir][v];
-  };
-  auto deriv = [&](const T* sF, int v) {
-    T rv = T(0);
-#pragma unroll
-    for (int dir = 0; dir < D; ++dir) {
-      if (!Ph::nz(dir, v)) continue;
-      T f[S];
-      VecLoad<T, S>::load(sF + (dir * VX + v) * PD + pb[dir], f);
-#pragma unroll
-      for (int m = 0; m < n; ++m) rv += Dr[dir][m] * f[m];
-    }
-    return rv;
-  };
-  if (first) {
-    T* sF = sFbuf + buf * bufsz + (size_t)lc * D * VX * PD;
-    write_slice(sF, Qh);
-    __syncthreads();
-#pragma unroll
-    for (int v = 0; v < V; ++v) {
-      const T rv = deriv(sF, v);
-#pragma unroll
-      for (int kk = 0; kk < n; ++kk) q[kk][v] = Qh[v] - sdtProw[kk] * rv;
-    }
-    buf ^= 1;
-    return;
-  }
-  T qn[n][V];
-#pragma unroll
-  for (int k = 0; k < n; ++k)
-#pragma unroll
-    for (int v = 0; v < V; ++v) qn[k][v] = Qh[v];
-#pragma unroll
-  for (int k = 0; k < n; ++k) {
-    T* sF = sFbuf + buf * bufsz + (size_t)lc * D * VX * PD;
-    write_slice(sF, q[k]);
-    __syncthreads();
-#pragma unroll
-    for (int v = 0; v < V; ++v) {
-      const T rv = deriv(sF, v);
-#pragma unroll
-      for (int kk = 0; kk < n; ++kk) qn[kk][v] -= sdtP[kk * n + k] * rv;
-    }
-    buf ^= 1;  // the next slice writes the other buffer
-  }
-#pragma unroll
-  for (int k = 0; k < n; ++k)
-#pragma unroll
-    for (int v = 0; v < V; ++v) q[k][v] = qn[k][v];
-}
-
 template <class C, class TL> struct RefSmem {
   using P = PredSmem<C, double, double>;
   static constexpr size_t big = P::big;  // FP64 flux slices / final stage (TL slices fit)
@@ -186,7 +116,8 @@ __global__ void __launch_bounds__(C::THREADS) k_predictor_refine(const __grid_co
       for (int v = 0; v < V; ++v) qL[k][v] = QL[v];
     int buf = 0;
     for (int r = 0; r < nlo; ++r)
-      picard_sweep<C, TL>(qL, QL, reinterpret_cast<TL*>(sFraw), sdtPL, sdtProwL, Dr, ppL, pb, idx, lc, r == 0, buf);
+      picard_sweep<C, TL>(qL, QL, reinterpret_cast<TL*>(sFraw), sdtPL, sdtProwL, Dr, ppL, pb, idx, lc, r == 0,
+                          buf);
 #pragma unroll
     for (int k = 0; k < n; ++k)
 #pragma unroll
