@@ -86,7 +86,11 @@ enum adg_predictor { ADG_PRED_PICARD = 0, ADG_PRED_CK = 1 };
 enum adg_flags {
   ADG_F_COMPENSATED_LAST = 1, /* tensor-core Picard: last sweep with split hi/lo products */
   ADG_F_PER_CELL_SCALE = 2,   /* tensor-core Picard: power-of-two scaling per cell */
-  ADG_F_COMPENSATED_TWO = 4   /* tensor-core Picard: last two sweeps with hi/lo products */
+  ADG_F_COMPENSATED_TWO = 4,  /* tensor-core Picard: last two sweeps with hi/lo products */
+  /* Testing aid, no use in a computation: the tensor-core predictors issue no MMA in their
+   * first round, so the bounded wait for it (about one second) runs out.  The kernels then stop,
+   * release their tensor memory and the step returns ADG_ETIMEOUT; the context stays usable. */
+  ADG_F_TEST_SKIP_MMA = 256
 };
 
 /* Scenario closed forms for adg_set_initial() / adg_error_vs_exact(); the

@@ -18,6 +18,7 @@ ACOUSTIC, ELASTIC, EULER, SWE, SWE_B = 0, 1, 2, 3, 4
 K_PICARD, K_PREDICTOR, K_RIEMANN, K_CORRECTOR, K_STORAGE = 0, 1, 2, 3, 4
 FP64, FP32, BF16, FP16, FP8E4M3 = 0, 1, 2, 3, 4
 F_COMPENSATED_LAST, F_PER_CELL_SCALE, F_COMPENSATED_TWO = 1, 2, 4
+F_TEST_SKIP_MMA = 256  # testing aid: the tensor-core predictors' first MMA round is skipped
 PRED_PICARD, PRED_CK = 0, 1
 SC_PLANAR, SC_EULER_WAVE, SC_SWE_MODES, SC_GAUSS_PULSE, SC_LAKE = 0, 1, 2, 3, 4
 SC_EULER_BELL, SC_EULER_VORTEX = 5, 6

@@ -323,6 +323,7 @@ static void fill_step_args(const adg_ctx* c, StepArgs* a) {
   a->comp_sweeps = (c->flags & ADG_F_COMPENSATED_TWO) ? 2 : (c->flags & ADG_F_COMPENSATED_LAST) ? 1 : 0;
   a->per_cell_scale = (c->flags & ADG_F_PER_CELL_SCALE) ? 1 : 0;
   a->refine_sweeps = c->refine;
+  a->test_skip_mma = (c->flags & ADG_F_TEST_SKIP_MMA) ? 1 : 0;
   a->tab = c->tab;
   a->pp = c->pp;
   finalize_step_args(a);

@@ -65,6 +65,7 @@ struct StepArgs {
   int comp_sweeps;     // tensor-core Picard: number of final sweeps with hi/lo compensation
   int per_cell_scale;  // tensor-core Picard: power-of-two scaling of the flux per cell
   int refine_sweeps;   // refinement predictor: the last sweeps run in FP64
+  int test_skip_mma;   // testing aid: the tensor-core predictors issue no MMA in their first round
   // surface-integral coefficients psi_side(xi_i) / (h_dir w_i) [side][dir][i], FP64 and rounded
   // to FP32 (set by finalize_step_args)
   double surf[2][3][kMaxN1];

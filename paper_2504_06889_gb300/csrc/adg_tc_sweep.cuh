@@ -375,7 +375,7 @@ __global__ void __launch_bounds__(TsCfg<C>::THREADS, TsCfg<C>::THREADS > 128 ? 2
           stop = true;
           break;
         }
-        if (tid == 0) {
+        if (tid == 0 && !(a.test_skip_mma && first)) {  // (testing aid: see adg.h)
           tc::fence_after();
           const uint32_t ab = launder(a_base), bb = launder(b_base);
           const int mts = first ? 1 : MT;

@@ -159,3 +159,31 @@ def test_16bit_mixes_meet_the_fp32_tolerance(adg, oracle_mod, pic):
     Qg, _ = run(adg, wl, pic, adg.F_COMPENSATED_LAST | adg.F_PER_CELL_SCALE, wl.steps)
     rel = M.l2_diff(Qg, Qo)[1] / M.l2_diff(Qo, M.zeros())[1]
     assert rel <= 1e-5, rel
+
+
+@pytest.mark.parametrize("pic", ["bf16", "fp8"])
+def test_bounded_wait_runs_out_cleanly(adg, oracle_mod, pic):
+    """Failure detection without a fault: with ADG_F_TEST_SKIP_MMA the tensor-core predictor
+    (sweep-batched kernel for bf16, per-slice kernel for E4M3) issues no MMA in its first round,
+    so nothing completes the barrier it waits on.  The wait gives up after about a second, the
+    kernel releases its tensor memory and the step returns ADG_ETIMEOUT; the device and the
+    library stay usable, and the same step without the flag matches the oracle."""
+    import time
+
+    wl = I.euler3d_wave(N=5).with_cells((2, 2, 2), 1)
+    prec = {"picard": pic, "predictor": "fp32", "riemann": "fp32", "corrector": "fp32"}
+    s = adg.Solver(wl.dim, wl.N, wl.cells, wl.pde, wl.params, cfl=wl.cfl, precision=prec,
+                   flags=adg.F_COMPENSATED_LAST | adg.F_PER_CELL_SCALE | adg.F_TEST_SKIP_MMA)
+    s.set_initial(wl.scenario, wl.sp)
+    t0 = time.time()
+    with pytest.raises(adg.AdgError) as e:
+        s.step(1)
+    assert e.value.code == adg.ETIMEOUT
+    assert time.time() - t0 < 60
+    s.close()
+    M = oracle_mod.Mesh(wl.dim, wl.N, wl.cells, wl.pde, wl.params, cfl=wl.cfl)
+    Qo = M.interpolate(wl.scenario, wl.sp)
+    M.run(Qo, 1)
+    Qg, _ = run(adg, wl, pic, adg.F_COMPENSATED_LAST | adg.F_PER_CELL_SCALE, 1)
+    rel = M.l2_diff(Qg, Qo)[1] / M.l2_diff(Qo, M.zeros())[1]
+    assert rel <= U[pic] * 0.1, rel
