@@ -698,10 +698,28 @@ __global__ void __launch_bounds__(C::THREADS) k_corrector(const __grid_constant_
     sS[it] = tmax(sm, sp);
   }
   __syncthreads();
-  for (int f = i; f < 2 * D; f += NS) {
-    TR s = sS[f * NF];
-    for (int jj = 1; jj < NF; ++jj) s = tmax(s, sS[f * NF + jj]);
-    sSmax[f] = s;
+  // one Rusanov speed per face: the maximum over its NF nodes.  With many nodes per face (3D)
+  // one warp per face (lanes stride over the nodes, then a butterfly of shuffles; only full
+  // warps take part); with few (2D) one thread per face.
+  if constexpr (NF < 16) {
+    for (int f = i; f < 2 * D; f += NS) {
+      TR s = sS[f * NF];
+      for (int jj = 1; jj < NF; ++jj) s = tmax(s, sS[f * NF + jj]);
+      sSmax[f] = s;
+    }
+  } else {
+    constexpr int NFACE = CPB * 2 * D, FULL_WARPS = C::THREADS / 32;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp < FULL_WARPS) {
+      for (int fg = warp; fg < NFACE; fg += FULL_WARPS) {
+        const TR* src = sSall + (size_t)fg * NF;
+        TR s = src[lane < NF ? lane : 0];
+        for (int jj = lane + 32; jj < NF; jj += 32) s = tmax(s, src[jj]);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s = tmax(s, __shfl_xor_sync(0xffffffffu, s, off));
+        if (lane == 0) sSall[(size_t)NFACE * NF + fg] = s;  // = sSmax of cell fg / 2d, face fg % 2d
+      }
+    }
   }
   __syncthreads();
   // Rusanov: G = (Fm + Fp)/2 + s/2 (qm - qp), s = max over the face's nodes
