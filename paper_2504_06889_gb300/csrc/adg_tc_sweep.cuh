@@ -22,7 +22,8 @@
 // Columns pack (m, v) as 4 m + v for v < 4 (one 8-byte store per node and direction) and
 // 4 n + m for Euler's fifth variable.  Operand tiles are K-major 8x8 core matrices without
 // swizzle (the layout of adg_tc.cuh).  Per-cell power-of-two scaling keeps fp16 in range: F is
-// scaled by the previous sweep's max |F| (the first sweep by max |F(Q)|), R by its own max.
+// scaled by the previous sweep's max |F - F_c| (the first sweep by that of F(Q)), R by the previous
+// sweep's max |R| (the first sweep measures its own).  bf16 has FP32's exponent range and skips it.
 // In the compensated sweeps every operand is split x = hi + lo and the products hi hi + hi lo +
 // lo hi accumulate in the same tile; the lo operands go in a second pass through the same
 // shared-memory buffers.  The first sweep starts from q = Q at all time nodes: only the k = 0
