@@ -175,9 +175,123 @@ __device__ __forceinline__ float store_to_float(float x) { return x; }
 __device__ __forceinline__ float store_to_float(__nv_bfloat16 x) { return __bfloat162float(x); }
 __device__ __forceinline__ float store_to_float(__half x) { return __half2float(x); }
 
+// Pencil-task form of a Picard sweep (picard_sweep_pt below; FP32 arithmetic, PDEs without a
+// non-conservative product).
+//
+// In the node-per-thread form every node reads the n values of each of its pencils, one per
+// contraction FMA, so shared-memory bandwidth (128 B per clock per SM) caps the contraction at a
+// quarter of the FP32 rate.  Here a time slice takes two barriers: the node threads write the
+// fluxes; then each thread takes whole pencils ("tasks": one direction, one flux component, one
+// pencil), reads its n values once and writes all n derivatives, D times the pencil; then each
+// node reads back its D derivatives per variable.  Per node and flux component that is one flux
+// store, one pencil value read, one derivative written and one read, instead of one store and n
+// reads.  The derivative matrix comes from the kernel parameters (constant bank); the node applies
+// the 1/h of each direction.
+//
+// Layout, the same for the fluxes and the derivatives: per cell and flux component ("combo":
+// direction d and variable v with a nonzero flux, direction-major) a region of CS values, value
+// (p, m) at p + m MS ("position-major"), p the pencil (the node's other two coordinates), m the
+// position along d; optionally the x pencils pencil-major (p SF0 + m).  A task's addresses are
+// compile-time offsets from one base.  The constants per configuration (pt_layout) come from a
+// bank-conflict model of these accesses; for 3D Euler at N = 5 it counts 516 shared-memory
+// wavefronts per cell and slice, against about 790 for the node-per-thread form.
+// Layout constants of the pencil-task form per (d, n, flux components), from the bank model
+// pencil_layout_model.py (beside this file): xpm = 1 stores the x pencils pencil-major (read and
+// written by the tasks with 8-byte accesses), ord1 = 1 numbers the y pencils z + n x instead of
+// x + n z, MS is the stride of the position along a direction, CS the values per component.
+struct PtLayout {
+  int xpm, ord1, MS, CS;
+};
+__host__ __device__ constexpr PtLayout pt_layout(int D, int n, int ncmb) {
+  const int NP = D == 3 ? n * n : n;
+  return (D == 2 && n == 4 && ncmb == 4)    ? PtLayout{0, 0, 4, 20}     // acoustic 2D N=3
+         : (D == 2 && n == 3 && ncmb == 4)  ? PtLayout{0, 0, 3, 12}     // acoustic 2D N=2
+         : (D == 3 && n == 5 && ncmb == 6)  ? PtLayout{0, 0, 25, 156}   // acoustic 3D N=4
+         : (D == 3 && n == 3 && ncmb == 6)  ? PtLayout{0, 0, 9, 44}     // acoustic 3D N=2
+         : (D == 3 && n == 7 && ncmb == 24) ? PtLayout{0, 0, 55, 380}   // elastic 3D N=6
+         : (D == 3 && n == 3 && ncmb == 24) ? PtLayout{0, 0, 9, 44}     // elastic 3D N=2
+         : (D == 2 && n == 4 && ncmb == 10) ? PtLayout{0, 0, 4, 20}     // elastic 2D N=3
+         : (D == 3 && n == 6 && ncmb == 15) ? PtLayout{1, 1, 36, 228}   // Euler 3D N=5
+         : (D == 3 && n == 3 && ncmb == 15) ? PtLayout{0, 0, 9, 44}     // Euler 3D N=2
+         : (D == 2 && n == 6 && ncmb == 8)  ? PtLayout{0, 0, 6, 40}     // Euler 2D N=5
+         : (D == 2 && n == 4 && ncmb == 8)  ? PtLayout{0, 0, 4, 20}     // Euler 2D N=3
+         : (D == 2 && n == 5 && ncmb == 6)  ? PtLayout{0, 0, 5, 28}     // shallow water N=4
+         : (D == 2 && n == 3 && ncmb == 6)  ? PtLayout{0, 0, 3, 12}     // shallow water N=2
+                                            : PtLayout{0, 0, NP + 2, ((n - 1) * (NP + 2) + NP + 3) / 4 * 4};
+}
+
+template <class C> struct PencilTasks {
+  using Ph = Phys<C::PDE, C::D>;
+  static constexpr int n = C::n, D = C::D, V = C::V, NP = C::NF;
+  __host__ __device__ static constexpr int cidx(int d, int v) {  // combo index of (d, v)
+    int c = 0;
+    for (int dd = 0; dd < D; ++dd)
+      for (int vv = 0; vv < V; ++vv) {
+        if (dd == d && vv == v) return c;
+        if (Ph::nz(dd, vv)) ++c;
+      }
+    return c;
+  }
+  static constexpr int NCMB = cidx(D, 0);
+  static constexpr PtLayout LAY = pt_layout(D, n, NCMB);
+  static constexpr bool XPM = LAY.xpm != 0;
+  static constexpr int SF0 = (n % 2 == 0) ? n : n + 1;  // stride of the pencil-major x pencils
+  static constexpr int MS = LAY.MS, CS = LAY.CS;
+  static_assert(MS >= NP && CS >= (n - 1) * MS + NP && (!XPM || CS >= NP * SF0) && CS % 4 == 0,
+                "pencil-task layout: a component's region must hold all its values");
+  static constexpr int NT = NCMB * NP;                          // tasks per cell and slice
+  static constexpr int CELL = NCMB * CS;                        // values per cell in each region
+  __host__ __device__ static constexpr int ncd(int d) { return cidx(d + 1, 0) - cidx(d, 0); }
+  __host__ __device__ static constexpr int max_ncd() {
+    int m = 0;
+    for (int d = 0; d < D; ++d) m = ncd(d) > m ? ncd(d) : m;
+    return m;
+  }
+  // Task slots (tasks per thread).  With x pencil-major, slot j holds the tasks of direction j
+  // (thread i takes task i of that direction), so each slot has one access pattern; otherwise
+  // slot j holds task threadIdx.x + j THREADS of all of them.
+  static_assert(!XPM || C::CPB * max_ncd() * NP <= C::THREADS, "x pencil-major needs one slot per direction");
+  static constexpr int NSLOT = XPM ? D : (C::CPB * NT + C::THREADS - 1) / C::THREADS;
+  // pencil of node (x, y, z) along d (its other coordinates)
+  __device__ static __forceinline__ int pen(const int* idx, int d) {
+    return d == 0 ? idx[1] + n * idx[2]
+                  : (d == 1 ? (LAY.ord1 ? idx[2] + n * idx[0] : idx[0] + n * idx[2]) : idx[0] + n * idx[1]);
+  }
+  // offset of node (x, y, z) inside a region of direction d
+  __device__ static __forceinline__ int node_off(const int* idx, int d) {
+    return (XPM && d == 0) ? pen(idx, 0) * SF0 + idx[0] : pen(idx, d) + idx[d] * MS;
+  }
+  // offset of this thread's task in slot j in either region (its first value), -1 if none
+  __device__ static __forceinline__ int task_base(int j) {
+    if constexpr (XPM) {
+      const int t = threadIdx.x, nt = ncd(j) * NP;  // tasks of direction j per cell
+      if (t >= C::CPB * nt) return -1;
+      const int cl = t / nt, r = t - cl * nt, c = r / NP, p = r - c * NP;
+      return cl * CELL + (cidx(j, 0) + c) * CS + (j == 0 ? p * SF0 : p);
+    } else {
+      const int t = threadIdx.x + j * C::THREADS;
+      if (t >= C::CPB * NT) return -1;
+      const int cl = t / NT, r = t - cl * NT, c = r / NP;
+      return cl * CELL + c * CS + (r - c * NP);
+    }
+  }
+};
+template <class C, class T> struct UsePencilTasks {
+  static constexpr bool value = std::is_same<T, float>::value && C::NG == 0;
+};
+// Blocks per SM the predictor asks the register allocator for.  The direction-slot tasks of the
+// x pencil-major layout (3D Euler N=5) take 109 registers unconstrained (2 blocks of 216 threads
+// per SM); three blocks (80 registers, a few bytes of spills) made the predictor 11% faster.
+template <class C, class T, bool CK> struct PredMinBlocks {
+  static constexpr int value = (!CK && UsePencilTasks<C, T>::value && PencilTasks<C>::XPM) ? 3 : 1;
+};
+
 template <class C, class T, class TP> struct PredSmem {
   // two flux-slice buffers (double buffering) during the sweeps
-  static constexpr size_t sweep = sizeof(T) * 2 * C::CPB * C::D * C::VX * Pencil<C>::PER_DIR;
+  static constexpr size_t sweep_np = sizeof(T) * 2 * C::CPB * C::D * C::VX * Pencil<C>::PER_DIR;
+  // the pencil-task form: flux and derivative regions
+  static constexpr size_t sweep_pt = sizeof(T) * 2 * C::CPB * PencilTasks<C>::CELL;
+  static constexpr size_t sweep = sweep_np > sweep_pt ? sweep_np : sweep_pt;
   // final stage: Fbar in pencil layout + Qbar (+ the state pencils of every time node for a
   // non-conservative product)
   static constexpr size_t fin =
@@ -454,6 +568,128 @@ __device__ __forceinline__ void picard_sweep(T (&q)[C::n][C::V], const T (&Qh)[C
     for (int v = 0; v < V; ++v) q[k][v] = qn[k][v];
 }
 
+// One task: the n derivatives D f of the pencil at f (stride S), written to o with the same
+// stride.  S = 1 with n even uses 8-byte accesses.
+template <int n, int S, class T>
+__device__ __forceinline__ void pencil_task(const T* f, T* o, const Tables& tab) {
+  T fv[n];
+  if constexpr (S == 1 && n % 2 == 0) {
+#pragma unroll
+    for (int m = 0; m < n; m += 2) {
+      const float2 v2 = *reinterpret_cast<const float2*>(f + m);
+      fv[m] = v2.x;
+      fv[m + 1] = v2.y;
+    }
+  } else {
+#pragma unroll
+    for (int m = 0; m < n; ++m) fv[m] = f[m * S];
+  }
+  auto row = [&](int i) {
+    T s = tab.fD[i][0] * fv[0];
+#pragma unroll
+    for (int m = 1; m < n; ++m) s = fmaf(tab.fD[i][m], fv[m], s);
+    return s;
+  };
+  if constexpr (S == 1 && n % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < n; i += 2) *reinterpret_cast<float2*>(o + i) = make_float2(row(i), row(i + 1));
+  } else {
+#pragma unroll
+    for (int i = 0; i < n; ++i) o[i * S] = row(i);
+  }
+}
+
+// The tasks of one slice: this thread's pencils (tb: their offsets, -1 for an empty slot; in the
+// generic slots only the last can be empty).
+template <class C, class T>
+__device__ __forceinline__ void pencil_tasks(const T* sF, T* sR, const Tables& tab,
+                                             const int (&tb)[PencilTasks<C>::NSLOT]) {
+  using L = PencilTasks<C>;
+#pragma unroll
+  for (int j = 0; j < L::NSLOT; ++j) {
+    if ((L::XPM || j == L::NSLOT - 1) && tb[j] < 0) continue;
+    if (L::XPM && j == 0)
+      pencil_task<C::n, 1>(sF + tb[j], sR + tb[j], tab);
+    else
+      pencil_task<C::n, L::MS>(sF + tb[j], sR + tb[j], tab);
+  }
+}
+
+// One Picard sweep of eq. (Picard) in the pencil-task form (same result as picard_sweep up to
+// FP32 rounding order).  sF, sR: the block's flux and derivative regions; off: this node's
+// offset inside a combo's region, per direction; cF: this node's cell region (lc * CELL);
+// tb: this thread's task offsets (see pencil_tasks).
+template <class C, class T>
+__device__ __forceinline__ void picard_sweep_pt(T (&q)[C::n][C::V], const T (&Qh)[C::V], T* sF, T* sR,
+                                                const T* sdtP, const T* sdtProw, const Tables& tab,
+                                                const T (&ih)[C::D], const PP<T>& pp, const int (&off)[C::D],
+                                                int cF, const int (&tb)[PencilTasks<C>::NSLOT], bool first) {
+  using Ph = Phys<C::PDE, C::D>;
+  using L = PencilTasks<C>;
+  constexpr int n = C::n, V = C::V, D = C::D;
+  auto write_slice = [&](const T* qk) {
+    T F[D][V];
+    Ph::flux(pp, qk, F);
+#pragma unroll
+    for (int d = 0; d < D; ++d)
+#pragma unroll
+      for (int v = 0; v < V; ++v)
+        if (Ph::nz(d, v)) sF[cF + L::cidx(d, v) * L::CS + off[d]] = F[d][v];
+  };
+  auto deriv = [&](int v) {
+    T rv = T(0);
+#pragma unroll
+    for (int d = 0; d < D; ++d)
+      if (Ph::nz(d, v)) rv = fmaf(ih[d], sR[cF + L::cidx(d, v) * L::CS + off[d]], rv);
+    return rv;
+  };
+  if (first) {
+    write_slice(Qh);
+    __syncthreads();
+    pencil_tasks<C, T>(sF, sR, tab, tb);
+    __syncthreads();
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const T rv = deriv(v);
+#pragma unroll
+      for (int kk = 0; kk < n; ++kk) q[kk][v] = Qh[v] - sdtProw[kk] * rv;
+    }
+    return;
+  }
+  T qn[n][V];
+#pragma unroll
+  for (int k = 0; k < n; ++k)
+#pragma unroll
+    for (int v = 0; v < V; ++v) qn[k][v] = Qh[v];
+#pragma unroll
+  for (int k = 0; k < n; ++k) {
+    // the derivatives of the previous slice are read before this slice's fluxes are written; the
+    // barrier after the writes orders both against the tasks that overwrite them
+    if (k > 0) {
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        const T rv = deriv(v);
+#pragma unroll
+        for (int kk = 0; kk < n; ++kk) qn[kk][v] -= sdtP[kk * n + k - 1] * rv;
+      }
+    }
+    write_slice(q[k]);
+    __syncthreads();
+    pencil_tasks<C, T>(sF, sR, tab, tb);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    const T rv = deriv(v);
+#pragma unroll
+    for (int kk = 0; kk < n; ++kk) qn[kk][v] -= sdtP[kk * n + n - 1] * rv;
+  }
+#pragma unroll
+  for (int k = 0; k < n; ++k)
+#pragma unroll
+    for (int v = 0; v < V; ++v) q[k][v] = qn[k][v];
+}
+
 // ------------------------------------------------------------------------------------------------
 // predictor + volume integral + face traces
 // CK = false: Picard sweeps (Sec. 3.1, eq. Picard).  CK = true: Cauchy-Kowalevskaya for the
@@ -462,7 +698,7 @@ __device__ __forceinline__ void picard_sweep(T (&q)[C::n][C::V], const T (&Qh)[C
 // cell instead of about (N+1)^2 flux slices.  Both end in the same final stage.
 // ------------------------------------------------------------------------------------------------
 template <class C, class T, class TP, class TS, bool CK = false, class TQ = double>
-__global__ void __launch_bounds__(C::THREADS) k_predictor(const __grid_constant__ StepArgs a) {
+__global__ void __launch_bounds__(C::THREADS, PredMinBlocks<C, T, CK>::value) k_predictor(const __grid_constant__ StepArgs a) {
   using Ph = Phys<C::PDE, C::D>;
   constexpr int n = C::n, V = C::V, D = C::D, NS = C::NS, CPB = C::CPB, VX = C::VX;
   constexpr int S = Pencil<C>::S, PD = Pencil<C>::PER_DIR;
@@ -595,9 +831,29 @@ __global__ void __launch_bounds__(C::THREADS) k_predictor(const __grid_constant_
     }
   }
   // Picard sweeps (eq. Picard); the first starts from q = Q at every time node
-  if (!CK && a.picard_iters > 0) picard_sweep<C, T>(q, Qh, sFbuf, sdtP, sdtProw, Dr, pp, pb, idx, lc, true, buf);
-  for (int r = 1; !CK && r < a.picard_iters; ++r)
-    picard_sweep<C, T>(q, Qh, sFbuf, sdtP, sdtProw, Dr, pp, pb, idx, lc, false, buf);
+  if constexpr (!CK && UsePencilTasks<C, T>::value) {
+    using L = PencilTasks<C>;
+    T* sF = reinterpret_cast<T*>(smem_raw);
+    T* sR = sF + C::CPB * L::CELL;
+    int off[D], tb[L::NSLOT];
+    T ih[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      off[d] = L::node_off(idx, d);
+      ih[d] = conv<T>(a.invh[d]);
+    }
+#pragma unroll
+    for (int j = 0; j < L::NSLOT; ++j) tb[j] = L::task_base(j);
+    const int cF = lc * L::CELL;
+    if (a.picard_iters > 0)
+      picard_sweep_pt<C, T>(q, Qh, sF, sR, sdtP, sdtProw, a.tab, ih, pp, off, cF, tb, true);
+    for (int r = 1; r < a.picard_iters; ++r)
+      picard_sweep_pt<C, T>(q, Qh, sF, sR, sdtP, sdtProw, a.tab, ih, pp, off, cF, tb, false);
+  } else {
+    if (!CK && a.picard_iters > 0) picard_sweep<C, T>(q, Qh, sFbuf, sdtP, sdtProw, Dr, pp, pb, idx, lc, true, buf);
+    for (int r = 1; !CK && r < a.picard_iters; ++r)
+      picard_sweep<C, T>(q, Qh, sFbuf, sdtP, sdtProw, Dr, pp, pb, idx, lc, false, buf);
+  }
   __syncthreads();
 
   predictor_final<C, T, TP, TS, TQ>(a, q, reinterpret_cast<TP*>(smem_raw), sVm, sw, sp0, sp1, dt, lc, i,

@@ -1,0 +1,212 @@
+"""Shared-memory bank model of the pencil-task Picard sweep (picard_sweep_pt in adg_kernels.cuh).
+
+Counts the shared-memory wavefronts of one time slice of one block: the node threads' flux
+stores and derivative loads (one 4-byte access per node and flux component), and the tasks'
+pencil loads and derivative stores (n per task; 8-byte accesses where the x direction is stored
+pencil-major and n is even).  A 4-byte warp access costs as many wavefronts as the largest
+number of distinct words that map to one of the 32 banks; an 8-byte access is served per
+half-warp.  For each configuration it searches the layout of PencilLayout:
+
+  xpm   0: every direction position-major, value (p, m) at p + m MS
+        1: x pencil-major (p SF0 + m), y and z position-major
+  ord1  numbering of the y pencils: 0 p = x + n z, 1 p = z + n x
+  MS    stride of the position along a direction (>= NP)
+  CS    values per flux component and cell
+
+and prints the best against the ideal (no conflicts).  pt_layout in adg_kernels.cuh holds these
+results for the configurations the library builds; others use xpm = 0, ord1 = 0, MS = NP + 2.
+check() replays the kernel's index arithmetic for a layout (bounds, coverage, alignment).
+
+    python pencil_layout_model.py
+"""
+import itertools
+
+
+def wavefronts32(addrs):
+    banks = {}
+    for a in addrs:
+        if a is not None:
+            banks.setdefault(a % 32, set()).add(a)
+    return max((len(s) for s in banks.values()), default=0)
+
+
+def wavefronts64(addrs):
+    total = 0
+    for half in (addrs[:16], addrs[16:]):
+        banks = {}
+        for a in half:
+            if a is not None:
+                for w in (a, a + 1):
+                    banks.setdefault(w % 32, set()).add(w)
+        total += max((len(s) for s in banks.values()), default=0)
+    return total
+
+
+class Config:
+    def __init__(self, name, D, n, combos_per_dir):
+        self.name, self.D, self.n = name, D, n
+        self.NS, self.NP = n ** D, n ** (D - 1)
+        self.CPB = 1 if self.NS >= 96 else 128 // self.NS
+        self.THREADS = self.CPB * self.NS
+        self.dir_of = [d for d in range(D) for _ in range(combos_per_dir[d])]
+        self.NC = len(self.dir_of)
+        self.SF0 = n if n % 2 == 0 else n + 1
+
+    def pencil(self, i, d, ord1):
+        n = self.n
+        x, y, z = i % n, (i // n) % n, i // (n * n)
+        if d == 0:
+            return y + n * z, x
+        if d == 1:
+            return (z + n * x) if ord1 else (x + n * z), y
+        return x + n * y, z
+
+    def addr(self, lay, cl, c, p, m):
+        xpm, ord1, MS, CS = lay
+        off = p * self.SF0 + m if (xpm and self.dir_of[c] == 0) else p + m * MS
+        return cl * self.NC * CS + c * CS + off
+
+    def slots(self, lay):
+        """Task slots as the kernel assigns them: with xpm, slot j holds the tasks of direction j
+        (thread i takes task i of that direction); otherwise slot j holds task i + j THREADS of the
+        combo-major list.  Yields (slot, [(cell, combo, pencil) or None per thread])."""
+        xpm = lay[0]
+        NP, TH, CPB = self.NP, self.THREADS, self.CPB
+        if xpm:
+            for j in range(self.D):
+                combos = [c for c in range(self.NC) if self.dir_of[c] == j]
+                nt = len(combos) * NP
+                yield j, [(t // nt, combos[(t % nt) // NP], t % NP) if t < CPB * nt else None for t in range(TH)]
+        else:
+            NT = self.NC * NP
+            for j in range((CPB * NT + TH - 1) // TH):
+                yield j, [((t // NT), (t % NT) // NP, t % NP) if t < CPB * NT else None
+                          for t in (i + j * TH for i in range(TH))]
+
+    def count(self, lay):
+        xpm, ord1, MS, CS = lay
+        node = 0
+        for w in range(0, self.THREADS, 32):
+            lanes = [w + l if w + l < self.THREADS else None for l in range(32)]
+            for c in range(self.NC):
+                d = self.dir_of[c]
+                node += wavefronts32([None if t is None else
+                                      self.addr(lay, t // self.NS, c, *self.pencil(t % self.NS, d, ord1))
+                                      for t in lanes])
+        tasks = 0
+        for j, tl in self.slots(lay):
+            for w in range(0, self.THREADS, 32):
+                cp = tl[w:w + 32] + [None] * max(0, w + 32 - self.THREADS)
+                if all(x is None for x in cp):
+                    continue
+                pm = [x if (x and xpm and self.dir_of[x[1]] == 0) else None for x in cp]
+                po = [x if (x and not (xpm and self.dir_of[x[1]] == 0)) else None for x in cp]
+                if any(pm):
+                    if self.n % 2 == 0:
+                        for m in range(0, self.n, 2):
+                            tasks += wavefronts64([None if x is None else self.addr(lay, *x, m) for x in pm])
+                    else:
+                        for m in range(self.n):
+                            tasks += wavefronts32([None if x is None else self.addr(lay, *x, m) for x in pm])
+                if any(po):
+                    for m in range(self.n):
+                        tasks += wavefronts32([None if x is None else self.addr(lay, *x, m) for x in po])
+        # fluxes and derivatives share the layout: stores and loads cost the same
+        return 2 * (node + tasks)
+
+    def check(self, lay):
+        """The kernel's index arithmetic for layout lay, replayed: every node writes its own slot
+        of each flux component inside its cell's region; the tasks of all threads read exactly the
+        slots the nodes write and write (once each) exactly the slots the nodes read; 8-byte task
+        accesses are aligned.  Slots: with xpm, slot j holds the tasks of direction j (thread i takes
+        task i); otherwise slot j holds task i + j THREADS.  Raises AssertionError on a violation."""
+        xpm, ord1, MS, CS = lay
+        n, NP, NS, CPB, TH = self.n, self.NP, self.NS, self.CPB, self.THREADS
+        assert MS >= NP and CS % 4 == 0 and CS >= (n - 1) * MS + NP and (not xpm or CS >= NP * self.SF0)
+        assert self.D == 3 or (not xpm and not ord1)
+        CELL = self.NC * CS
+        written = set()
+        for tid in range(TH):
+            cl, i = tid // NS, tid % NS
+            for c in range(self.NC):
+                a = self.addr(lay, cl, c, *self.pencil(i, self.dir_of[c], ord1))
+                assert cl * CELL + c * CS <= a < cl * CELL + (c + 1) * CS and a not in written
+                written.add(a)
+        cstart = [self.dir_of.index(d) for d in range(self.D)]
+        ncd = [self.dir_of.count(d) for d in range(self.D)]
+        NT = self.NC * NP
+        nslot = self.D if xpm else (CPB * NT + TH - 1) // TH
+        if xpm:
+            assert all(CPB * k * NP <= TH for k in ncd)
+        read, wrote = set(), set()
+        for tid in range(TH):
+            for j in range(nslot):
+                # the kernel's task_base(j)
+                if xpm:
+                    nt = ncd[j] * NP
+                    if tid >= CPB * nt:
+                        continue
+                    cl, r = tid // nt, tid % nt
+                    c, p = cstart[j] + r // NP, r % NP
+                    base, stride = cl * CELL + c * CS + (p * self.SF0 if j == 0 else p), (1 if j == 0 else MS)
+                    if j == 0 and n % 2 == 0:
+                        assert base % 2 == 0
+                else:
+                    t = tid + j * TH
+                    if t >= CPB * NT:
+                        assert j == nslot - 1
+                        continue
+                    cl, r = t // NT, t % NT
+                    base, stride = cl * CELL + (r // NP) * CS + r % NP, MS
+                for m in range(n):
+                    a = base + m * stride
+                    assert a in written and a not in wrote
+                    read.add(a)
+                    wrote.add(a)
+        assert read == written and wrote == written
+        return True
+
+    def ideal(self):
+        return 2 * (self.NC * self.THREADS / 32 + self.CPB * self.NC * self.NP * self.n / 32)
+
+    def search(self):
+        best = None
+        for xpm, ord1 in itertools.product((0, 1) if self.D == 3 else (0,), (0, 1) if self.D == 3 else (0,)):
+            for MS in range(self.NP, self.NP + 8):
+                ext = (self.n - 1) * MS + self.NP
+                if xpm:
+                    ext = max(ext, self.NP * self.SF0)
+                for CS in range((ext + 3) // 4 * 4, (ext + 3) // 4 * 4 + 48, 4):
+                    lay = (xpm, ord1, MS, CS)
+                    if xpm and any(self.CPB * self.dir_of.count(d) * self.NP > self.THREADS for d in range(self.D)):
+                        continue
+                    w = self.count(lay)
+                    if best is None or w < best[0]:
+                        best = (w, lay)
+        return best
+
+
+# nonzero flux components per direction of the PDEs built with an FP32 predictor
+CONFIGS = [
+    Config("acoustic 2D N=3", 2, 4, [2, 2]),
+    Config("acoustic 2D N=2", 2, 3, [2, 2]),
+    Config("acoustic 3D N=4", 3, 5, [2, 2, 2]),
+    Config("acoustic 3D N=2", 3, 3, [2, 2, 2]),
+    Config("elastic 3D N=6", 3, 7, [8, 8, 8]),
+    Config("elastic 3D N=2", 3, 3, [8, 8, 8]),
+    Config("elastic 2D N=3", 2, 4, [5, 5]),
+    Config("Euler 3D N=5", 3, 6, [5, 5, 5]),
+    Config("Euler 3D N=2", 3, 3, [5, 5, 5]),
+    Config("Euler 2D N=5", 2, 6, [4, 4]),
+    Config("Euler 2D N=3", 2, 4, [4, 4]),
+    Config("shallow water N=4", 2, 5, [3, 3]),
+    Config("shallow water N=2", 2, 3, [3, 3]),
+]
+
+if __name__ == "__main__":
+    for cfg in CONFIGS:
+        default = (0, 0, cfg.NP + 2, ((cfg.n - 1) * (cfg.NP + 2) + cfg.NP + 3) // 4 * 4)
+        w, lay = cfg.search()
+        print(f"{cfg.name:18s} D={cfg.D} n={cfg.n} combos={cfg.NC:2d}: best xpm={lay[0]} ord1={lay[1]} "
+              f"MS={lay[2]} CS={lay[3]}: {w} wavefronts (default {cfg.count(default)}, ideal {cfg.ideal():.0f})",
+              flush=True)
