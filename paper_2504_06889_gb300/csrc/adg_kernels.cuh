@@ -175,18 +175,18 @@ __device__ __forceinline__ float store_to_float(float x) { return x; }
 __device__ __forceinline__ float store_to_float(__nv_bfloat16 x) { return __bfloat162float(x); }
 __device__ __forceinline__ float store_to_float(__half x) { return __half2float(x); }
 
-// Pencil-task form of a Picard sweep (picard_sweep_pt below; FP32 arithmetic, PDEs without a
+// Pencil-task form of the Picard sweeps (picard_pt below; FP32 arithmetic, PDEs without a
 // non-conservative product).
 //
 // In the node-per-thread form every node reads the n values of each of its pencils, one per
 // contraction FMA, so shared-memory bandwidth (128 B per clock per SM) caps the contraction at a
-// quarter of the FP32 rate.  Here a time slice takes two barriers: the node threads write the
-// fluxes; then each thread takes whole pencils ("tasks": one direction, one flux component, one
-// pencil), reads its n values once and writes all n derivatives, D times the pencil; then each
-// node reads back its D derivatives per variable.  Per node and flux component that is one flux
-// store, one pencil value read, one derivative written and one read, instead of one store and n
-// reads.  The derivative matrix comes from the kernel parameters (constant bank); the node applies
-// the 1/h of each direction.
+// quarter of the FP32 rate.  Here a time slice has three steps, separated by barriers: the node
+// threads write the fluxes; each thread takes whole pencils ("tasks": one direction, one flux
+// component, one pencil), reads its n values once and writes all n derivatives, D times the
+// pencil; each node reads back its D derivatives per variable.  picard_pt overlaps the steps of
+// consecutive slices.  Per node and flux component that is one flux store, one pencil value read,
+// one derivative written and one read, instead of one store and n reads.  The derivative matrix
+// comes from the kernel parameters (constant bank); the node applies the 1/h of each direction.
 //
 // Layout, the same for the fluxes and the derivatives: per cell and flux component ("combo":
 // direction d and variable v with a nonzero flux, direction-major) a region of CS values, value
@@ -279,18 +279,20 @@ template <class C> struct PencilTasks {
 template <class C, class T> struct UsePencilTasks {
   static constexpr bool value = std::is_same<T, float>::value && C::NG == 0;
 };
-// Blocks per SM the predictor asks the register allocator for.  The direction-slot tasks of the
+// Blocks per SM the predictor asks the register allocator for (0: the compiler's own choice, as
+// without the bound; an explicit 1 made it take more registers).  The direction-slot tasks of the
 // x pencil-major layout (3D Euler N=5) take 109 registers unconstrained (2 blocks of 216 threads
-// per SM); three blocks (80 registers, a few bytes of spills) made the predictor 11% faster.
+// per SM); three blocks (80 registers) made that predictor 11% faster.
 template <class C, class T, bool CK> struct PredMinBlocks {
-  static constexpr int value = (!CK && UsePencilTasks<C, T>::value && PencilTasks<C>::XPM) ? 3 : 1;
+  static constexpr int value = (!CK && UsePencilTasks<C, T>::value && PencilTasks<C>::XPM) ? 3 : 0;
 };
 
-template <class C, class T, class TP> struct PredSmem {
+// PT: the kernel runs the pencil-task sweeps (their four regions replace the two flux buffers)
+template <class C, class T, class TP, bool PT = false> struct PredSmem {
   // two flux-slice buffers (double buffering) during the sweeps
   static constexpr size_t sweep_np = sizeof(T) * 2 * C::CPB * C::D * C::VX * Pencil<C>::PER_DIR;
-  // the pencil-task form: flux and derivative regions
-  static constexpr size_t sweep_pt = sizeof(T) * 2 * C::CPB * PencilTasks<C>::CELL;
+  // the pencil-task form: two flux and two derivative regions
+  static constexpr size_t sweep_pt = PT ? sizeof(T) * 4 * C::CPB * PencilTasks<C>::CELL : 0;
   static constexpr size_t sweep = sweep_np > sweep_pt ? sweep_np : sweep_pt;
   // final stage: Fbar in pencil layout + Qbar (+ the state pencils of every time node for a
   // non-conservative product)
@@ -615,19 +617,29 @@ __device__ __forceinline__ void pencil_tasks(const T* sF, T* sR, const Tables& t
   }
 }
 
-// One Picard sweep of eq. (Picard) in the pencil-task form (same result as picard_sweep up to
-// FP32 rounding order).  sF, sR: the block's flux and derivative regions; off: this node's
-// offset inside a combo's region, per direction; cF: this node's cell region (lc * CELL);
-// tb: this thread's task offsets (see pencil_tasks).
+// All Picard sweeps of eq. (Picard) in the pencil-task form (the same result as picard_sweep up
+// to FP32 rounding order), pipelined over the time slices: the fluxes and the derivatives each
+// have two buffers, and one barrier separates phase k, in which the tasks differentiate slice
+// k - 1, the nodes write the fluxes of slice k and read the derivatives of slice k - 2, from
+// phase k + 1.  A node's flux at slice k needs only its own iterate, so a sweep takes n + 1
+// barriers instead of 2 n.  No buffer is read and written in the same phase, and every buffer
+// is rewritten at least one barrier after it was last read.
+// sbuf: the block's four regions (fluxes 0, 1, derivatives 0, 1); off: this node's offset
+// inside a combo's region, per direction; cF: this node's cell region (lc * CELL); tb: this
+// thread's task offsets (see pencil_tasks).
 template <class C, class T>
-__device__ __forceinline__ void picard_sweep_pt(T (&q)[C::n][C::V], const T (&Qh)[C::V], T* sF, T* sR,
-                                                const T* sdtP, const T* sdtProw, const Tables& tab,
-                                                const T (&ih)[C::D], const PP<T>& pp, const int (&off)[C::D],
-                                                int cF, const int (&tb)[PencilTasks<C>::NSLOT], bool first) {
+__device__ __forceinline__ void picard_pt(T (&q)[C::n][C::V], const T (&Qh)[C::V], T* sbuf, const T* sdtP,
+                                          const T* sdtProw, const Tables& tab, const T (&ih)[C::D],
+                                          const PP<T>& pp, const int (&off)[C::D], int cF,
+                                          const int (&tb)[PencilTasks<C>::NSLOT], int iters) {
   using Ph = Phys<C::PDE, C::D>;
   using L = PencilTasks<C>;
-  constexpr int n = C::n, V = C::V, D = C::D;
-  auto write_slice = [&](const T* qk) {
+  constexpr int n = C::n, V = C::V, D = C::D, B = C::CPB * L::CELL;
+  T* const sF0 = sbuf;
+  T* const sF1 = sbuf + B;
+  T* const sR0 = sbuf + 2 * B;
+  T* const sR1 = sbuf + 3 * B;
+  auto write_slice = [&](T* sF, const T* qk) {
     T F[D][V];
     Ph::flux(pp, qk, F);
 #pragma unroll
@@ -636,58 +648,55 @@ __device__ __forceinline__ void picard_sweep_pt(T (&q)[C::n][C::V], const T (&Qh
       for (int v = 0; v < V; ++v)
         if (Ph::nz(d, v)) sF[cF + L::cidx(d, v) * L::CS + off[d]] = F[d][v];
   };
-  auto deriv = [&](int v) {
+  auto deriv = [&](const T* sR, int v) {
     T rv = T(0);
 #pragma unroll
     for (int d = 0; d < D; ++d)
       if (Ph::nz(d, v)) rv = fmaf(ih[d], sR[cF + L::cidx(d, v) * L::CS + off[d]], rv);
     return rv;
   };
-  if (first) {
-    write_slice(Qh);
-    __syncthreads();
-    pencil_tasks<C, T>(sF, sR, tab, tb);
-    __syncthreads();
+  // qn -= dt P[:, l] R_l (slice l's column of the time operator)
+  auto consume = [&](const T* sR, int l, T (&qn)[n][V]) {
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-      const T rv = deriv(v);
+      const T rv = deriv(sR, v);
 #pragma unroll
-      for (int kk = 0; kk < n; ++kk) q[kk][v] = Qh[v] - sdtProw[kk] * rv;
+      for (int kk = 0; kk < n; ++kk) qn[kk][v] -= sdtP[kk * n + l] * rv;
     }
-    return;
-  }
-  T qn[n][V];
-#pragma unroll
-  for (int k = 0; k < n; ++k)
-#pragma unroll
-    for (int v = 0; v < V; ++v) qn[k][v] = Qh[v];
-#pragma unroll
-  for (int k = 0; k < n; ++k) {
-    // the derivatives of the previous slice are read before this slice's fluxes are written; the
-    // barrier after the writes orders both against the tasks that overwrite them
-    if (k > 0) {
-#pragma unroll
-      for (int v = 0; v < V; ++v) {
-        const T rv = deriv(v);
-#pragma unroll
-        for (int kk = 0; kk < n; ++kk) qn[kk][v] -= sdtP[kk * n + k - 1] * rv;
-      }
-    }
-    write_slice(q[k]);
-    __syncthreads();
-    pencil_tasks<C, T>(sF, sR, tab, tb);
-    __syncthreads();
-  }
+  };
+  if (iters <= 0) return;
+  // first sweep: every time node holds Q, so one flux slice serves all of them
+  write_slice(sF0, Qh);
+  __syncthreads();
+  pencil_tasks<C, T>(sF0, sR0, tab, tb);
+  __syncthreads();
 #pragma unroll
   for (int v = 0; v < V; ++v) {
-    const T rv = deriv(v);
+    const T rv = deriv(sR0, v);
 #pragma unroll
-    for (int kk = 0; kk < n; ++kk) qn[kk][v] -= sdtP[kk * n + n - 1] * rv;
+    for (int kk = 0; kk < n; ++kk) q[kk][v] = Qh[v] - sdtProw[kk] * rv;
   }
+  for (int r = 1; r < iters; ++r) {
+    T qn[n][V];
 #pragma unroll
-  for (int k = 0; k < n; ++k)
+    for (int k = 0; k < n; ++k)
 #pragma unroll
-    for (int v = 0; v < V; ++v) q[k][v] = qn[k][v];
+      for (int v = 0; v < V; ++v) qn[k][v] = Qh[v];
+    write_slice(sF0, q[0]);
+    __syncthreads();
+#pragma unroll
+    for (int k = 1; k <= n; ++k) {
+      pencil_tasks<C, T>((k - 1) % 2 ? sF1 : sF0, (k - 1) % 2 ? sR1 : sR0, tab, tb);  // slice k - 1
+      if (k < n) write_slice(k % 2 ? sF1 : sF0, q[k]);
+      if (k >= 2) consume(k % 2 ? sR1 : sR0, k - 2, qn);  // slice k - 2 (same parity as k)
+      __syncthreads();
+    }
+    consume((n - 1) % 2 ? sR1 : sR0, n - 1, qn);
+#pragma unroll
+    for (int k = 0; k < n; ++k)
+#pragma unroll
+      for (int v = 0; v < V; ++v) q[k][v] = qn[k][v];
+  }
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -702,15 +711,16 @@ __global__ void __launch_bounds__(C::THREADS, PredMinBlocks<C, T, CK>::value) k_
   using Ph = Phys<C::PDE, C::D>;
   constexpr int n = C::n, V = C::V, D = C::D, NS = C::NS, CPB = C::CPB, VX = C::VX;
   constexpr int S = Pencil<C>::S, PD = Pencil<C>::PER_DIR;
+  constexpr bool kPT = !CK && UsePencilTasks<C, T>::value;  // pencil-task sweeps
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double s_dt;
   if (a.sc->bad) return;
   const double dt = block_dt(a, D, C::N, &s_dt);
 
   // tables: dt P and its row sums (T), then Vm, w, psi0, psi1 (TP)
-  T* sdtP = reinterpret_cast<T*>(smem_raw + PredSmem<C, T, TP>::big);
+  T* sdtP = reinterpret_cast<T*>(smem_raw + PredSmem<C, T, TP, kPT>::big);
   T* sdtProw = sdtP + n * n;
-  TP* sVm = reinterpret_cast<TP*>(reinterpret_cast<unsigned char*>(smem_raw + PredSmem<C, T, TP>::big) +
+  TP* sVm = reinterpret_cast<TP*>(reinterpret_cast<unsigned char*>(smem_raw + PredSmem<C, T, TP, kPT>::big) +
                                   ((sizeof(T) * (n * n + n) + sizeof(TP) - 1) / sizeof(TP)) * sizeof(TP));
   TP* sw = sVm + n * n;
   TP* sp0 = sw + n;
@@ -831,10 +841,9 @@ __global__ void __launch_bounds__(C::THREADS, PredMinBlocks<C, T, CK>::value) k_
     }
   }
   // Picard sweeps (eq. Picard); the first starts from q = Q at every time node
-  if constexpr (!CK && UsePencilTasks<C, T>::value) {
+  if constexpr (kPT) {
     using L = PencilTasks<C>;
-    T* sF = reinterpret_cast<T*>(smem_raw);
-    T* sR = sF + C::CPB * L::CELL;
+    T* sbuf = reinterpret_cast<T*>(smem_raw);
     int off[D], tb[L::NSLOT];
     T ih[D];
 #pragma unroll
@@ -845,10 +854,7 @@ __global__ void __launch_bounds__(C::THREADS, PredMinBlocks<C, T, CK>::value) k_
 #pragma unroll
     for (int j = 0; j < L::NSLOT; ++j) tb[j] = L::task_base(j);
     const int cF = lc * L::CELL;
-    if (a.picard_iters > 0)
-      picard_sweep_pt<C, T>(q, Qh, sF, sR, sdtP, sdtProw, a.tab, ih, pp, off, cF, tb, true);
-    for (int r = 1; r < a.picard_iters; ++r)
-      picard_sweep_pt<C, T>(q, Qh, sF, sR, sdtP, sdtProw, a.tab, ih, pp, off, cF, tb, false);
+    picard_pt<C, T>(q, Qh, sbuf, sdtP, sdtProw, a.tab, ih, pp, off, cF, tb, a.picard_iters);
   } else {
     if (!CK && a.picard_iters > 0) picard_sweep<C, T>(q, Qh, sFbuf, sdtP, sdtProw, Dr, pp, pb, idx, lc, true, buf);
     for (int r = 1; !CK && r < a.picard_iters; ++r)
@@ -1357,7 +1363,9 @@ __global__ void k_l2_final(const double* partial, int nblocks, double* out) {
 // ------------------------------------------------------------------------------------------------
 template <class C, class T, class TP, class TS, bool CK = false, class TQ = double>
 cudaError_t launch_predictor(const StepArgs& a, cudaStream_t s) {
-  const size_t smem = PredSmem<C, T, TP>::total;
+  constexpr bool kPT = !CK && UsePencilTasks<C, T>::value;
+  static_assert(PredSmem<C, T, TP, kPT>::total <= 227 * 1024, "predictor shared memory above the per-block limit");
+  const size_t smem = PredSmem<C, T, TP, kPT>::total;
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_predictor<C, T, TP, TS, CK, TQ>,

@@ -186,6 +186,47 @@ class Config:
         return best
 
 
+def check_schedule(n, iters):
+    """Replays the phases of picard_pt (barriers between phases) with two flux buffers F0, F1 and
+    two derivative buffers R0, R1, each holding the tag (sweep, slice) of its last write.  Asserts
+    that every read sees the slice it means to, and that no buffer is read and written in one
+    phase (so a barrier always separates a write from the reads before and after it)."""
+    buf = {}
+    phases = []
+
+    def phase(ops):
+        reads = {b for op, b, _ in ops if op == "r"}
+        writes = {b for op, b, _ in ops if op == "w"}
+        assert not reads & writes, ops
+        for op, b, tag in ops:
+            if op == "r":
+                assert buf.get(b) == tag, (b, buf.get(b), tag)
+        for op, b, tag in ops:
+            if op == "w":
+                buf[b] = tag
+        phases.append(ops)
+
+    F = lambda k: "F%d" % (k % 2)
+    R = lambda k: "R%d" % (k % 2)
+    if iters <= 0:
+        return 0
+    phase([("w", "F0", (0, 0))])                                   # first sweep: one slice
+    phase([("r", "F0", (0, 0)), ("w", "R0", (0, 0))])              # its tasks
+    pending = [("r", "R0", (0, 0))]                                # q = Q - dt rowsum(P) R
+    for r in range(1, iters):
+        phase(pending + [("w", "F0", (r, 0))])
+        for k in range(1, n + 1):
+            ops = [("r", F(k - 1), (r, k - 1)), ("w", R(k - 1), (r, k - 1))]
+            if k < n:
+                ops.append(("w", F(k), (r, k)))
+            if k >= 2:
+                ops.append(("r", R(k), (r, k - 2)))
+            phase(ops)
+        pending = [("r", R(n - 1), (r, n - 1))]
+    phase(pending)                                                 # the final stage follows
+    return len(phases) - 1                                         # barriers
+
+
 # nonzero flux components per direction of the PDEs built with an FP32 predictor
 CONFIGS = [
     Config("acoustic 2D N=3", 2, 4, [2, 2]),

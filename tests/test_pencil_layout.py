@@ -2,7 +2,8 @@
 CPU: for every configuration the library builds, the shared-memory indices of the node threads and
 of the tasks stay inside their regions, every slot is written once, the tasks read exactly what the
 nodes write and write exactly what they read, and the 8-byte accesses are aligned.  The constants
-are parsed from the kernel source, so a change there is checked before it runs on a GPU."""
+are parsed from the kernel source, so a change there is checked before it runs on a GPU.  The
+double-buffered phase schedule of picard_pt is replayed as well."""
 import importlib.util
 import os
 import re
@@ -44,6 +45,13 @@ def test_layout_indices(cfg):
 def test_default_layout_indices(cfg):
     NP, n = cfg.NP, cfg.n
     assert cfg.check((0, 0, NP + 2, ((n - 1) * (NP + 2) + NP + 3) // 4 * 4))
+
+
+@pytest.mark.parametrize("n", [3, 4, 5, 6, 7])
+@pytest.mark.parametrize("iters", [1, 2, 3, 7])
+def test_pipelined_schedule(n, iters):
+    # every read sees its slice; n + 1 barriers per sweep after the first (which takes 2)
+    assert M.check_schedule(n, iters) == 2 + (iters - 1) * (n + 1)
 
 
 def test_a_wrong_stride_is_caught():
