@@ -22,6 +22,9 @@ struct Tables {
   // FP32 copies for the FP32 kernels (rounded from the FP64 values)
   float fD[kMaxN1][kMaxN1], fP[kMaxN1][kMaxN1], fVm[kMaxN1][kMaxN1];
   float fw[kMaxN1], fpsi0[kMaxN1], fpsi1[kMaxN1];
+  // even and odd parts of D for the FP32 pencil contractions, i, m < n/2:
+  // fDe[i][m] = (D[i][m] + D[i][n-1-m]) / 2, fDo[i][m] = (D[i][m] - D[i][n-1-m]) / 2
+  float fDe[kMaxN1 / 2][kMaxN1 / 2], fDo[kMaxN1 / 2][kMaxN1 / 2];
 };
 
 // PDE parameters (acoustic rho,K; elastic rho,cp,cs; euler gamma; swe g)

@@ -571,9 +571,16 @@ __device__ __forceinline__ void picard_sweep(T (&q)[C::n][C::V], const T (&Qh)[C
 }
 
 // One task: the n derivatives D f of the pencil at f (stride S), written to o with the same
-// stride.  S = 1 with n even uses 8-byte accesses.
+// stride.  S = 1 with n even uses 8-byte accesses.  The nodes are symmetric about the cell's
+// centre (xi_{n-1-i} = 1 - xi_i), so D is centro-antisymmetric, D[n-1-i][n-1-m] = -D[i][m], and
+// the product splits into even and odd parts (the even-odd decomposition of a centro-symmetric
+// matrix-vector product): with fe_m = f_m + f_{n-1-m}, fo_m = f_m - f_{n-1-m} (m < n/2),
+//   (D f)_i = a_i + b_i,  (D f)_{n-1-i} = a_i - b_i  (i < n/2),
+// a_i = sum_m fDo[i][m] fo_m and b_i = sum_m fDe[i][m] fe_m (+ D[i][c] f_c for odd n, c the
+// middle node, whose own row is sum_m D[c][m] fo_m).  About n^2/2 + 2n operations instead of n^2.
 template <int n, int S, class T>
 __device__ __forceinline__ void pencil_task(const T* f, T* o, const Tables& tab) {
+  constexpr int h = n / 2;
   T fv[n];
   if constexpr (S == 1 && n % 2 == 0) {
 #pragma unroll
@@ -586,18 +593,37 @@ __device__ __forceinline__ void pencil_task(const T* f, T* o, const Tables& tab)
 #pragma unroll
     for (int m = 0; m < n; ++m) fv[m] = f[m * S];
   }
-  auto row = [&](int i) {
-    T s = tab.fD[i][0] * fv[0];
+  T fe[h], fo[h];
 #pragma unroll
-    for (int m = 1; m < n; ++m) s = fmaf(tab.fD[i][m], fv[m], s);
-    return s;
-  };
+  for (int m = 0; m < h; ++m) {
+    fe[m] = fv[m] + fv[n - 1 - m];
+    fo[m] = fv[m] - fv[n - 1 - m];
+  }
+  T out[n];
+#pragma unroll
+  for (int i = 0; i < h; ++i) {
+    T ai = tab.fDo[i][0] * fo[0], bi = tab.fDe[i][0] * fe[0];
+#pragma unroll
+    for (int m = 1; m < h; ++m) {
+      ai = fmaf(tab.fDo[i][m], fo[m], ai);
+      bi = fmaf(tab.fDe[i][m], fe[m], bi);
+    }
+    if constexpr (n % 2 == 1) bi = fmaf(tab.fD[i][h], fv[h], bi);
+    out[i] = ai + bi;
+    out[n - 1 - i] = ai - bi;
+  }
+  if constexpr (n % 2 == 1) {
+    T c = tab.fD[h][0] * fo[0];
+#pragma unroll
+    for (int m = 1; m < h; ++m) c = fmaf(tab.fD[h][m], fo[m], c);
+    out[h] = c;
+  }
   if constexpr (S == 1 && n % 2 == 0) {
 #pragma unroll
-    for (int i = 0; i < n; i += 2) *reinterpret_cast<float2*>(o + i) = make_float2(row(i), row(i + 1));
+    for (int i = 0; i < n; i += 2) *reinterpret_cast<float2*>(o + i) = make_float2(out[i], out[i + 1]);
   } else {
 #pragma unroll
-    for (int i = 0; i < n; ++i) o[i * S] = row(i);
+    for (int i = 0; i < n; ++i) o[i * S] = out[i];
   }
 }
 
