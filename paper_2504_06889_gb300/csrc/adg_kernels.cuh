@@ -261,6 +261,41 @@ template <class C> struct PencilTasks {
   __device__ static __forceinline__ int node_off(const int* idx, int d) {
     return (XPM && d == 0) ? pen(idx, 0) * SF0 + idx[0] : pen(idx, d) + idx[d] * MS;
   }
+  // cell (of the block), combo and pencil of this thread's task in slot j (the task of
+  // task_base(j)); false if the slot is empty
+  __device__ static __forceinline__ bool task_of(int j, int* cl, int* c, int* p) {
+    if constexpr (XPM) {
+      const int t = threadIdx.x, nt = ncd(j) * NP;
+      if (t >= C::CPB * nt) return false;
+      *cl = t / nt;
+      const int r = t - *cl * nt;
+      *c = cidx(j, 0) + r / NP;
+      *p = r % NP;
+    } else {
+      const int t = threadIdx.x + j * C::THREADS;
+      if (t >= C::CPB * NT) return false;
+      *cl = t / NT;
+      const int r = t - *cl * NT;
+      *c = r / NP;
+      *p = r - *c * NP;
+    }
+    return true;
+  }
+  // direction and variable of combo c
+  __device__ static __forceinline__ void combo_dv(int c, int* d, int* v) {
+#pragma unroll
+    for (int dd = 0; dd < D; ++dd)
+#pragma unroll
+      for (int vv = 0; vv < V; ++vv)
+        if (Ph::nz(dd, vv) && c == cidx(dd, vv)) {
+          *d = dd;
+          *v = vv;
+        }
+  }
+  // index of pencil p along d among the face nodes of a face normal to d (node_of_face's j)
+  __device__ static __forceinline__ int face_of(int d, int p) {
+    return (d == 1 && LAY.ord1) ? p / n + n * (p % n) : p;
+  }
   // offset of this thread's task in slot j in either region (its first value), -1 if none
   __device__ static __forceinline__ int task_base(int j) {
     if constexpr (XPM) {
@@ -278,6 +313,12 @@ template <class C> struct PencilTasks {
 };
 template <class C, class T> struct UsePencilTasks {
   static constexpr bool value = std::is_same<T, float>::value && C::NG == 0;
+};
+// The final stage in pencil-task form (predictor_final_pt) where it measured faster: 3D Euler
+// N=5 5%, 3D acoustics 9%, shallow water 7%; for 3D elasticity N=6 (one 343-thread block per
+// SM) the node-per-thread final stage was 3% faster, and its configurations keep it.
+template <class C> struct UseFinalPt {
+  static constexpr bool value = !(C::PDE == 1 && C::D == 3);
 };
 // Blocks per SM the predictor asks the register allocator for (0: the compiler's own choice, as
 // without the bound; an explicit 1 made it take more registers).  The direction-slot tasks of the
@@ -725,6 +766,147 @@ __device__ __forceinline__ void picard_pt(T (&q)[C::n][C::V], const T (&Qh)[C::V
   }
 }
 
+// One task of the final stage: the pencil of Fbar at f (stride S) times Vm, written to o (the
+// node reads it back for the volume integral), and times psi(0), psi(1): its two face traces.
+template <int n, int S, class T>
+__device__ __forceinline__ void final_task(const T* f, T* o, const Tables& tab, T* s0, T* s1) {
+  T fv[n];
+#pragma unroll
+  for (int m = 0; m < n; ++m) fv[m] = f[m * S];
+#pragma unroll
+  for (int i = 0; i < n; ++i) {
+    T s = tab.fVm[i][0] * fv[0];
+#pragma unroll
+    for (int m = 1; m < n; ++m) s = fmaf(tab.fVm[i][m], fv[m], s);
+    o[i * S] = s;
+  }
+  T a0 = tab.fpsi0[0] * fv[0], a1 = tab.fpsi1[0] * fv[0];
+#pragma unroll
+  for (int m = 1; m < n; ++m) {
+    a0 = fmaf(tab.fpsi0[m], fv[m], a0);
+    a1 = fmaf(tab.fpsi1[m], fv[m], a1);
+  }
+  *s0 = a0;
+  *s1 = a1;
+}
+
+// Final stage of the pencil-task predictor (the result of predictor_final, FP32 arithmetic, no
+// non-conservative product): the time averages Qbar = sum_k w_k q_k and Fbar = sum_k w_k F(q_k) of
+// the last iterate; then pencil tasks: each Fbar pencil times Vm (the volume integral, read back
+// by its nodes) and times psi(0), psi(1) (the traces of Fbar.n on the faces normal to its
+// direction), and each Qbar pencil times psi(0), psi(1) (its traces); the nodes add dt times the
+// volume integral to Q in FP64.  The Fbar tasks are the sweeps' (tb); the Qbar tasks are numbered
+// by face node, so their trace stores are contiguous.  sbuf: the pencil-task regions (Fbar in
+// the first, Qbar [cell][v][node] in the second, Vm Fbar in the third).
+template <class C, class T, class TS, class TQ>
+__device__ __forceinline__ void predictor_final_pt(const StepArgs& a, const T (*q)[C::V], T* sbuf, const PP<T>& pp,
+                                                   const T (&ih)[C::D], double dt, int lc, int i, int cell,
+                                                   bool valid, const int (&off)[C::D], int cF,
+                                                   const int (&tb)[PencilTasks<C>::NSLOT]) {
+  using Ph = Phys<C::PDE, C::D>;
+  using L = PencilTasks<C>;
+  constexpr int n = C::n, V = C::V, D = C::D, NS = C::NS, NF = C::NF, B = C::CPB * L::CELL;
+  constexpr int TPC = D * 2 * 2 * V * NF;  // trace values per cell: [dir][side][Qbar, Fbar.n][v][face node]
+  static_assert(V * NS <= L::CELL, "Qbar of a cell must fit its region");
+  T* const sFb = sbuf;
+  T* const sQb = sbuf + B;
+  T* const sVo = sbuf + 2 * B;
+  T Fb[D][V], Qb[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    Qb[v] = T(0);
+#pragma unroll
+    for (int d = 0; d < D; ++d) Fb[d][v] = T(0);
+  }
+#pragma unroll
+  for (int k = 0; k < n; ++k) {
+    T F[D][V];
+    Ph::flux(pp, q[k], F);
+    const T wk = a.tab.fw[k];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      Qb[v] += wk * q[k][v];
+#pragma unroll
+      for (int d = 0; d < D; ++d) Fb[d][v] += wk * F[d][v];
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    sQb[lc * L::CELL + v * NS + i] = Qb[v];
+#pragma unroll
+    for (int d = 0; d < D; ++d)
+      if (Ph::nz(d, v)) sFb[cF + L::cidx(d, v) * L::CS + off[d]] = Fb[d][v];
+  }
+  __syncthreads();
+
+  // Fbar tasks: Vm Fbar for the nodes, Fbar.n traces
+#pragma unroll
+  for (int j = 0; j < L::NSLOT; ++j) {
+    int tcl, c, p;
+    if (!L::task_of(j, &tcl, &c, &p)) continue;
+    T s0, s1;
+    if (L::XPM && j == 0)
+      final_task<n, 1>(sFb + tb[j], sVo + tb[j], a.tab, &s0, &s1);
+    else
+      final_task<n, L::MS>(sFb + tb[j], sVo + tb[j], a.tab, &s0, &s1);
+    const int tcell = blockIdx.x * C::CPB + tcl;
+    if (tcell < a.ncells) {
+      int d = 0, v = 0;
+      L::combo_dv(c, &d, &v);
+      TS* tr = reinterpret_cast<TS*>(a.traces) + (size_t)tcell * TPC + v * NF + L::face_of(d, p);
+      tr[((d * 2 + 0) * 2 + 1) * V * NF] = conv<TS>(s0);
+      tr[((d * 2 + 1) * 2 + 1) * V * NF] = conv<TS>(s1);
+    }
+  }
+  // Qbar tasks: Qbar traces, and zero Fbar.n traces for the flux components that vanish
+  constexpr int NQ = C::CPB * D * V * NF;
+#pragma unroll
+  for (int k = 0; k < (NQ + C::THREADS - 1) / C::THREADS; ++k) {
+    const int t = threadIdx.x + k * C::THREADS;
+    if (t >= NQ) break;
+    const int tcl = t / (D * V * NF), r = t - tcl * (D * V * NF);
+    const int d = r / (V * NF), v = (r / NF) % V, jf = r % NF;
+    const int tcell = blockIdx.x * C::CPB + tcl;
+    if (tcell >= a.ncells) continue;
+    const T* qb = sQb + tcl * L::CELL + v * NS;
+    T s0 = T(0), s1 = T(0);
+#pragma unroll
+    for (int m = 0; m < n; ++m) {
+      const T x = qb[node_of_face<D, n>(d, jf, m)];
+      s0 = fmaf(a.tab.fpsi0[m], x, s0);
+      s1 = fmaf(a.tab.fpsi1[m], x, s1);
+    }
+    TS* tr = reinterpret_cast<TS*>(a.traces) + (size_t)tcell * TPC + v * NF + jf;
+    tr[((d * 2 + 0) * 2 + 0) * V * NF] = conv<TS>(s0);
+    tr[((d * 2 + 1) * 2 + 0) * V * NF] = conv<TS>(s1);
+    if (!Ph::nz(d, v)) {
+      tr[((d * 2 + 0) * 2 + 1) * V * NF] = conv<TS>(T(0));
+      tr[((d * 2 + 1) * 2 + 1) * V * NF] = conv<TS>(T(0));
+    }
+  }
+  __syncthreads();
+
+  // volume integral: Q_i += dt sum_dir (1/h_dir) (Vm Fbar_dir)_i, in FP64 (rounded to the
+  // storage format when the solution is stored below FP64)
+  if (valid) {
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      T vol = T(0);
+#pragma unroll
+      for (int d = 0; d < D; ++d)
+        if (Ph::nz(d, v)) vol = fmaf(ih[d], sVo[cF + L::cidx(d, v) * L::CS + off[d]], vol);
+      if constexpr (std::is_same<TQ, double>::value) {
+        double* Qw = a.Q + (size_t)cell * V * NS;
+        Qw[v * NS + i] += dt * (double)vol;
+      } else {
+        TQ* Qsw = static_cast<TQ*>(a.Qs) + (size_t)cell * V * NS;
+        const double qv = store_widen(Qsw[v * NS + i]) + dt * (double)vol;
+        Qsw[v * NS + i] = store_round<TQ>(qv);
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------------------------------------------------
 // predictor + volume integral + face traces
 // CK = false: Picard sweeps (Sec. 3.1, eq. Picard).  CK = true: Cauchy-Kowalevskaya for the
@@ -881,15 +1063,20 @@ __global__ void __launch_bounds__(C::THREADS, PredMinBlocks<C, T, CK>::value) k_
     for (int j = 0; j < L::NSLOT; ++j) tb[j] = L::task_base(j);
     const int cF = lc * L::CELL;
     picard_pt<C, T>(q, Qh, sbuf, sdtP, sdtProw, a.tab, ih, pp, off, cF, tb, a.picard_iters);
+    __syncthreads();
+    if constexpr (UseFinalPt<C>::value)
+      predictor_final_pt<C, T, TS, TQ>(a, q, sbuf, pp, ih, dt, lc, i, cell, valid, off, cF, tb);
+    else
+      predictor_final<C, T, TP, TS, TQ>(a, q, reinterpret_cast<TP*>(smem_raw), sVm, sw, sp0, sp1, dt, lc, i,
+                                        cell, valid, cl, idx, pb);
   } else {
     if (!CK && a.picard_iters > 0) picard_sweep<C, T>(q, Qh, sFbuf, sdtP, sdtProw, Dr, pp, pb, idx, lc, true, buf);
     for (int r = 1; !CK && r < a.picard_iters; ++r)
       picard_sweep<C, T>(q, Qh, sFbuf, sdtP, sdtProw, Dr, pp, pb, idx, lc, false, buf);
+    __syncthreads();
+    predictor_final<C, T, TP, TS, TQ>(a, q, reinterpret_cast<TP*>(smem_raw), sVm, sw, sp0, sp1, dt, lc, i,
+                                      cell, valid, cl, idx, pb);
   }
-  __syncthreads();
-
-  predictor_final<C, T, TP, TS, TQ>(a, q, reinterpret_cast<TP*>(smem_raw), sVm, sw, sp0, sp1, dt, lc, i,
-                                    cell, valid, cl, idx, pb);
 }
 
 // ------------------------------------------------------------------------------------------------

@@ -3,7 +3,8 @@ CPU: for every configuration the library builds, the shared-memory indices of th
 of the tasks stay inside their regions, every slot is written once, the tasks read exactly what the
 nodes write and write exactly what they read, and the 8-byte accesses are aligned.  The constants
 are parsed from the kernel source, so a change there is checked before it runs on a GPU.  The
-double-buffered phase schedule of picard_pt is replayed as well."""
+double-buffered phase schedule of picard_pt and the trace stores of the final stage
+(predictor_final_pt) are replayed as well."""
 import importlib.util
 import os
 import re
@@ -39,6 +40,11 @@ def test_table_covers_the_built_configurations():
 @pytest.mark.parametrize("cfg", M.CONFIGS, ids=[c.name for c in M.CONFIGS])
 def test_layout_indices(cfg):
     assert cfg.check(TABLE[(cfg.D, cfg.n, cfg.NC)])
+
+
+@pytest.mark.parametrize("cfg", M.CONFIGS, ids=[c.name for c in M.CONFIGS])
+def test_final_stage_traces(cfg):
+    assert cfg.check_final(TABLE[(cfg.D, cfg.n, cfg.NC)])
 
 
 @pytest.mark.parametrize("cfg", M.CONFIGS, ids=[c.name for c in M.CONFIGS])
