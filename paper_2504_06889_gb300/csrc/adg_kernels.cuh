@@ -323,9 +323,10 @@ template <class C> struct UseFinalPt {
 // Blocks per SM the predictor asks the register allocator for (0: the compiler's own choice, as
 // without the bound; an explicit 1 made it take more registers).  The direction-slot tasks of the
 // x pencil-major layout (3D Euler N=5) take 109 registers unconstrained (2 blocks of 216 threads
-// per SM); three blocks (80 registers) made that predictor 11% faster.
+// per SM); three blocks (80 registers) made that predictor 11% faster, four (72 registers, no
+// spills; 4 x 57 KB of shared memory fill the SM) another 2.5%.
 template <class C, class T, bool CK> struct PredMinBlocks {
-  static constexpr int value = (!CK && UsePencilTasks<C, T>::value && PencilTasks<C>::XPM) ? 3 : 0;
+  static constexpr int value = (!CK && UsePencilTasks<C, T>::value && PencilTasks<C>::XPM) ? 4 : 0;
 };
 
 // PT: the kernel runs the pencil-task sweeps (their four regions replace the two flux buffers)
