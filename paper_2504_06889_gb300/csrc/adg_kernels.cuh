@@ -193,8 +193,9 @@ __device__ __forceinline__ float store_to_float(__half x) { return __half2float(
 // (p, m) at p + m MS ("position-major"), p the pencil (the node's other two coordinates), m the
 // position along d; optionally the x pencils pencil-major (p SF0 + m).  A task's addresses are
 // compile-time offsets from one base.  The constants per configuration (pt_layout) come from a
-// bank-conflict model of these accesses; for 3D Euler at N = 5 it counts 516 shared-memory
+// bank-conflict model of these accesses; for 3D Euler at N = 5 it counts 504 shared-memory
 // wavefronts per cell and slice, against about 790 for the node-per-thread form.
+
 // Layout constants of the pencil-task form per (d, n, flux components), from the bank model
 // pencil_layout_model.py (beside this file): xpm = 1 stores the x pencils pencil-major (read and
 // written by the tasks with 8-byte accesses), ord1 = 1 numbers the y pencils z + n x instead of
@@ -298,28 +299,24 @@ template <class C> struct PencilTasks {
   }
   // offset of this thread's task in slot j in either region (its first value), -1 if none
   __device__ static __forceinline__ int task_base(int j) {
-    if constexpr (XPM) {
-      const int t = threadIdx.x, nt = ncd(j) * NP;  // tasks of direction j per cell
-      if (t >= C::CPB * nt) return -1;
-      const int cl = t / nt, r = t - cl * nt, c = r / NP, p = r - c * NP;
-      return cl * CELL + (cidx(j, 0) + c) * CS + (j == 0 ? p * SF0 : p);
-    } else {
-      const int t = threadIdx.x + j * C::THREADS;
-      if (t >= C::CPB * NT) return -1;
-      const int cl = t / NT, r = t - cl * NT, c = r / NP;
-      return cl * CELL + c * CS + (r - c * NP);
-    }
+    int cl, c, p;
+    if (!task_of(j, &cl, &c, &p)) return -1;
+    return cl * CELL + c * CS + ((XPM && j == 0) ? p * SF0 : p);
   }
 };
+
+// The Picard sweeps take the pencil-task form in FP32 for PDEs without a non-conservative product.
 template <class C, class T> struct UsePencilTasks {
   static constexpr bool value = std::is_same<T, float>::value && C::NG == 0;
 };
+
 // The final stage in pencil-task form (predictor_final_pt) where it measured faster: 3D Euler
 // N=5 5%, 3D acoustics 9%, shallow water 7%; for 3D elasticity N=6 (one 343-thread block per
 // SM) the node-per-thread final stage was 3% faster, and its configurations keep it.
 template <class C> struct UseFinalPt {
   static constexpr bool value = !(C::PDE == 1 && C::D == 3);
 };
+
 // Blocks per SM the predictor asks the register allocator for (0: the compiler's own choice, as
 // without the bound; an explicit 1 made it take more registers).  The direction-slot tasks of the
 // x pencil-major layout (3D Euler N=5) take 109 registers unconstrained (2 blocks of 216 threads
@@ -329,7 +326,8 @@ template <class C, class T, bool CK> struct PredMinBlocks {
   static constexpr int value = (!CK && UsePencilTasks<C, T>::value && PencilTasks<C>::XPM) ? 4 : 0;
 };
 
-// PT: the kernel runs the pencil-task sweeps (their four regions replace the two flux buffers)
+// Dynamic shared memory of the predictor.  PT: the kernel runs the pencil-task sweeps, whose four
+// regions (two for the fluxes, two for the derivatives) share the space of the other forms' buffers.
 template <class C, class T, class TP, bool PT = false> struct PredSmem {
   // two flux-slice buffers (double buffering) during the sweeps
   static constexpr size_t sweep_np = sizeof(T) * 2 * C::CPB * C::D * C::VX * Pencil<C>::PER_DIR;
