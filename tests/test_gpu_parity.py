@@ -174,6 +174,34 @@ def test_anisotropic_box(adg, oracle_mod):
     assert abs(tg - to) <= 1e-14 * to
 
 
+ANISO = [
+    # (workload, lo, hi): h differs per direction, so each direction's 1/h must reach its own
+    # derivatives; FP32 runs the pencil-task predictor (2D: several cells per block; 3D Euler
+    # N=5: x pencils pencil-major with direction slots; N=2: several cells per block)
+    (I.acoustic2d_planar(N=3).with_cells((4, 5), 4), [0.0, -1.0], [1.0, 2.0]),
+    (I.euler3d_wave(N=5).with_cells((3, 2, 2), 3), [0.0, 0.0, 0.0], [1.0, 2.0, 1.0]),
+    (I.euler3d_wave(N=2).with_cells((3, 4, 2), 3), [0.0, 0.0, -1.0], [1.0, 1.0, 1.0]),
+]
+
+
+@pytest.mark.parametrize("wl,lo,hi", ANISO, ids=["acoustic2d_N3", "euler3d_N5", "euler3d_N2"])
+def test_anisotropic_box_fp32(adg, oracle_mod, wl, lo, hi):
+    sp = wl.sp
+    if wl.pde == I.ACOUSTIC:
+        sp = I.planar(3, [I.acoustic_wave((2 * np.pi, 2 * np.pi / 3), 1.0, 1.0)])
+    M = oracle_mod.Mesh(wl.dim, wl.N, wl.cells, wl.pde, wl.params, lo=lo, hi=hi, cfl=wl.cfl)
+    Qo = M.interpolate(wl.scenario, sp)
+    to, _ = M.run(Qo, wl.steps)
+    prec = {"picard": "fp32", "predictor": "fp32", "riemann": "fp32", "corrector": "fp32"}
+    s = adg.Solver(wl.dim, wl.N, wl.cells, wl.pde, wl.params, lo=lo, hi=hi, cfl=wl.cfl, precision=prec)
+    s.set_initial(wl.scenario, sp)
+    tg, _ = s.step(wl.steps)
+    Qg = s.state()
+    s.close()
+    assert abs(tg - to) <= 1e-6 * to
+    assert rel_l2(M, Qg, Qo) <= 1e-5
+
+
 def test_set_state_roundtrip_and_l2_diff(adg, oracle_mod):
     wl = I.euler3d_wave(N=5).with_cells((2, 2, 2))
     M = oracle_mod.Mesh(wl.dim, wl.N, wl.cells, wl.pde, wl.params, cfl=wl.cfl)
