@@ -180,6 +180,11 @@ bool build_tables(int n, Tables* T) {
     T->fpsi0[k] = (float)T->psi0[k];
     T->fpsi1[k] = (float)T->psi1[k];
   }
+  for (int k = 0; k < n; ++k) {
+    double r = 0.0;
+    for (int l = 0; l < n; ++l) r += T->P[k][l];
+    T->fProw[k] = (float)r;
+  }
   for (int i = 0; i < n / 2; ++i)
     for (int m = 0; m < n / 2; ++m) {
       T->fDe[i][m] = (float)((D[i][m] + D[i][n - 1 - m]) / 2);

@@ -690,12 +690,13 @@ __device__ __forceinline__ void pencil_tasks(const T* sF, T* sR, const Tables& t
 // phase k + 1.  A node's flux at slice k needs only its own iterate, so a sweep takes n + 1
 // barriers instead of 2 n.  No buffer is read and written in the same phase, and every buffer
 // is rewritten at least one barrier after it was last read.
-// sbuf: the block's four regions (fluxes 0, 1, derivatives 0, 1); off: this node's offset
-// inside a combo's region, per direction; cF: this node's cell region (lc * CELL); tb: this
-// thread's task offsets (see pencil_tasks).
+// sbuf: the block's four regions (fluxes 0, 1, derivatives 0, 1); dtT: the step in FP32 (the
+// time operator dt P takes P and its row sums from the kernel parameters and multiplies the
+// derivative by dt once); off: this node's offset inside a combo's region, per direction; cF: this
+// node's cell region (lc * CELL); tb: this thread's task offsets (see pencil_tasks).
 template <class C, class T>
-__device__ __forceinline__ void picard_pt(T (&q)[C::n][C::V], const T (&Qh)[C::V], T* sbuf, const T* sdtP,
-                                          const T* sdtProw, const Tables& tab, const T (&ih)[C::D],
+__device__ __forceinline__ void picard_pt(T (&q)[C::n][C::V], const T (&Qh)[C::V], T* sbuf, T dtT,
+                                          const Tables& tab, const T (&ih)[C::D],
                                           const PP<T>& pp, const int (&off)[C::D], int cF,
                                           const int (&tb)[PencilTasks<C>::NSLOT], int iters) {
   using Ph = Phys<C::PDE, C::D>;
@@ -725,9 +726,9 @@ __device__ __forceinline__ void picard_pt(T (&q)[C::n][C::V], const T (&Qh)[C::V
   auto consume = [&](const T* sR, int l, T (&qn)[n][V]) {
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-      const T rv = deriv(sR, v);
+      const T drv = dtT * deriv(sR, v);
 #pragma unroll
-      for (int kk = 0; kk < n; ++kk) qn[kk][v] -= sdtP[kk * n + l] * rv;
+      for (int kk = 0; kk < n; ++kk) qn[kk][v] = fmaf(-tab.fP[kk][l], drv, qn[kk][v]);
     }
   };
   if (iters <= 0) return;
@@ -738,9 +739,9 @@ __device__ __forceinline__ void picard_pt(T (&q)[C::n][C::V], const T (&Qh)[C::V
   __syncthreads();
 #pragma unroll
   for (int v = 0; v < V; ++v) {
-    const T rv = deriv(sR0, v);
+    const T drv = dtT * deriv(sR0, v);
 #pragma unroll
-    for (int kk = 0; kk < n; ++kk) q[kk][v] = Qh[v] - sdtProw[kk] * rv;
+    for (int kk = 0; kk < n; ++kk) q[kk][v] = fmaf(-tab.fProw[kk], drv, Qh[v]);
   }
   for (int r = 1; r < iters; ++r) {
     T qn[n][V];
@@ -1061,7 +1062,7 @@ __global__ void __launch_bounds__(C::THREADS, PredMinBlocks<C, T, CK>::value) k_
 #pragma unroll
     for (int j = 0; j < L::NSLOT; ++j) tb[j] = L::task_base(j);
     const int cF = lc * L::CELL;
-    picard_pt<C, T>(q, Qh, sbuf, sdtP, sdtProw, a.tab, ih, pp, off, cF, tb, a.picard_iters);
+    picard_pt<C, T>(q, Qh, sbuf, dtT, a.tab, ih, pp, off, cF, tb, a.picard_iters);
     __syncthreads();
     if constexpr (UseFinalPt<C>::value)
       predictor_final_pt<C, T, TS, TQ>(a, q, sbuf, pp, ih, dt, lc, i, cell, valid, off, cF, tb);
