@@ -934,7 +934,10 @@ __global__ void __launch_bounds__(C::THREADS, PredMinBlocks<C, T, CK>::value) k_
   TP* sp0 = sw + n;
   TP* sp1 = sp0 + n;
   const T dtT = conv<T>(dt);
-  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+  // the pencil-task form takes its tables from the kernel parameters (with the node-by-node
+  // final stage it still reads Vm, w, psi0, psi1 from here)
+  constexpr bool kTables = !kPT || !UseFinalPt<C>::value;
+  for (int t = threadIdx.x; kTables && t < n * n; t += blockDim.x) {
     const int r = t / n, cidx = t % n;
     if constexpr (CK) {
       // Taylor factor of time derivative r at time node cidx: (xi dt)^r / r!, built up one
@@ -947,7 +950,7 @@ __global__ void __launch_bounds__(C::THREADS, PredMinBlocks<C, T, CK>::value) k_
     }
     sVm[t] = Tab<TP>::Vm(a.tab, r, cidx);
   }
-  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+  for (int t = threadIdx.x; kTables && t < n; t += blockDim.x) {
     sw[t] = Tab<TP>::w(a.tab, t);
     sp0[t] = Tab<TP>::psi0(a.tab, t);
     sp1[t] = Tab<TP>::psi1(a.tab, t);
@@ -1000,7 +1003,7 @@ __global__ void __launch_bounds__(C::THREADS, PredMinBlocks<C, T, CK>::value) k_
   T* sFbuf = reinterpret_cast<T*>(smem_raw);
   constexpr size_t bufsz = (size_t)CPB * D * VX * PD;
   // zero the pencil pads once (they are read as part of the vector loads and multiplied by 0)
-  if (S != n)
+  if (!kPT && S != n)
     for (size_t t = threadIdx.x; t < 2 * bufsz; t += blockDim.x) sFbuf[t] = T(0);
 
   T q[n][V];
