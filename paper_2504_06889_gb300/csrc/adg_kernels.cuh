@@ -715,18 +715,22 @@ __device__ __forceinline__ void picard_pt(T (&q)[C::n][C::V], const T (&Qh)[C::V
       for (int v = 0; v < V; ++v)
         if (Ph::nz(d, v)) sF[cF + L::cidx(d, v) * L::CS + off[d]] = F[d][v];
   };
-  auto deriv = [&](const T* sR, int v) {
+  // dt R_v = sum_dir (dt / h_dir) (D F_dir)_v
+  T dih[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) dih[d] = dtT * ih[d];
+  auto dt_deriv = [&](const T* sR, int v) {
     T rv = T(0);
 #pragma unroll
     for (int d = 0; d < D; ++d)
-      if (Ph::nz(d, v)) rv = fmaf(ih[d], sR[cF + L::cidx(d, v) * L::CS + off[d]], rv);
+      if (Ph::nz(d, v)) rv = fmaf(dih[d], sR[cF + L::cidx(d, v) * L::CS + off[d]], rv);
     return rv;
   };
   // qn -= dt P[:, l] R_l (slice l's column of the time operator)
   auto consume = [&](const T* sR, int l, T (&qn)[n][V]) {
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-      const T drv = dtT * deriv(sR, v);
+      const T drv = dt_deriv(sR, v);
 #pragma unroll
       for (int kk = 0; kk < n; ++kk) qn[kk][v] = fmaf(-tab.fP[kk][l], drv, qn[kk][v]);
     }
@@ -739,7 +743,7 @@ __device__ __forceinline__ void picard_pt(T (&q)[C::n][C::V], const T (&Qh)[C::V
   __syncthreads();
 #pragma unroll
   for (int v = 0; v < V; ++v) {
-    const T drv = dtT * deriv(sR0, v);
+    const T drv = dt_deriv(sR0, v);
 #pragma unroll
     for (int kk = 0; kk < n; ++kk) q[kk][v] = fmaf(-tab.fProw[kk], drv, Qh[v]);
   }
