@@ -152,7 +152,7 @@ def predictor_bytes_per_cell(pde, dim, N, trace_bytes, state_bytes=8):
 # the traffic of a launch is proportional to its cells.  Only valid while the kernel is
 # unchanged since the capture (the profile named beside it).
 MEASURED_TRAFFIC = {
-    ("euler3d_N5_64^3", "fp32"): (790.324e6 / 32768, "profiles/k_predictor_fp32_euler3d_N5_32cubed.md"),
+    ("euler3d_N5_64^3", "fp32"): (790.026e6 / 32768, "profiles/k_predictor_fp32_euler3d_N5_32cubed.md"),
     ("euler3d_N5_64^3", "bf16tc"): (796.997e6 / 32768, "profiles/k_predictor_tcs_bf16_euler3d_N5_32cubed.md"),
     ("euler3d_N5_64^3", "fp8tc"): (792.707e6 / 32768, "profiles/k_predictor_tc_fp8_euler3d_N5_32cubed.md"),
 }
