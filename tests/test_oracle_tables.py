@@ -74,3 +74,30 @@ def test_boundary_values_and_time_operator(oracle_mod, n):
     # K1 . 1 = psi(0) because sum_l psi_l = 1 and int psi_k' = psi_k(1) - psi_k(0)
     np.testing.assert_allclose(T["K1"] @ np.ones(n), T["psi0"], atol=1e-12)
     np.testing.assert_allclose(T["K1inv"] @ T["K1"], np.eye(n), atol=1e-11)
+
+
+@pytest.mark.parametrize("n", range(2, 9))
+def test_derivative_and_volume_matrices_are_centro_antisymmetric(oracle_mod, n):
+    """The nodes are symmetric about 1/2 (xi_{n-1-i} = 1 - xi_i), so psi_{n-1-m}(1 - x) = psi_m(x)
+    and D[n-1-i][n-1-m] = -D[i][m]; with symmetric weights Vm inherits it.  The FP32 predictor's
+    pencil contractions use this (the even-odd decomposition of D f): with fe = f_m + f_{n-1-m},
+    fo = f_m - f_{n-1-m} (m < n/2), (D f)_i = a_i + b_i and (D f)_{n-1-i} = a_i - b_i."""
+    T = oracle_mod.tables(n)
+    D, Vm, xi = T["D"], T["Vm"], T["xi"]
+    np.testing.assert_allclose(xi[::-1], 1.0 - xi, rtol=0, atol=1e-15)
+    scale = np.abs(D).max()
+    np.testing.assert_allclose(D[::-1, ::-1], -D, rtol=0, atol=1e-13 * scale)
+    np.testing.assert_allclose(Vm[::-1, ::-1], -Vm, rtol=0, atol=1e-13 * np.abs(Vm).max())
+    h = n // 2
+    De = (D[:h, :h] + D[:h, ::-1][:, :h]) / 2
+    Do = (D[:h, :h] - D[:h, ::-1][:, :h]) / 2
+    f = np.random.default_rng(n).standard_normal(n)
+    fe, fo = f[:h] + f[::-1][:h], f[:h] - f[::-1][:h]
+    out = np.zeros(n)
+    for i in range(h):
+        a = Do[i] @ fo
+        b = De[i] @ fe + (D[i, h] * f[h] if n % 2 else 0.0)
+        out[i], out[n - 1 - i] = a + b, a - b
+    if n % 2:
+        out[h] = D[h, :h] @ fo
+    np.testing.assert_allclose(out, D @ f, rtol=0, atol=1e-13 * scale * np.abs(f).sum())
