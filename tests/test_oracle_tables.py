@@ -83,7 +83,8 @@ def test_derivative_and_volume_matrices_are_centro_antisymmetric(oracle_mod, n):
     pencil contractions use this (the even-odd decomposition of D f): with fe = f_m + f_{n-1-m},
     fo = f_m - f_{n-1-m} (m < n/2), (D f)_i = a_i + b_i and (D f)_{n-1-i} = a_i - b_i."""
     T = oracle_mod.tables(n)
-    D, Vm, xi = T["D"], T["Vm"], T["xi"]
+    D, w, xi = T["D"], T["w"], T["xi"]
+    Vm = (w[None, :] * D.T) / w[:, None]  # the volume operator: Vm[i][m] = w_m D[m][i] / w_i
     np.testing.assert_allclose(xi[::-1], 1.0 - xi, rtol=0, atol=1e-15)
     scale = np.abs(D).max()
     np.testing.assert_allclose(D[::-1, ::-1], -D, rtol=0, atol=1e-13 * scale)
