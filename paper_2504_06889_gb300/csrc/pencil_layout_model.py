@@ -1,11 +1,11 @@
-"""Shared-memory bank model of the pencil-task Picard sweep (picard_sweep_pt in adg_kernels.cuh).
+"""Shared-memory bank model of the pencil-task Picard sweeps (picard_pt in adg_kernels.cuh).
 
 Counts the shared-memory wavefronts of one time slice of one block: the node threads' flux
 stores and derivative loads (one 4-byte access per node and flux component), and the tasks'
 pencil loads and derivative stores (n per task; 8-byte accesses where the x direction is stored
 pencil-major and n is even).  A 4-byte warp access costs as many wavefronts as the largest
 number of distinct words that map to one of the 32 banks; an 8-byte access is served per
-half-warp.  For each configuration it searches the layout of PencilLayout:
+half-warp.  For each configuration it searches the layout (PtLayout in adg_kernels.cuh):
 
   xpm   0: every direction position-major, value (p, m) at p + m MS
         1: x pencil-major (p SF0 + m), y and z position-major
@@ -15,7 +15,8 @@ half-warp.  For each configuration it searches the layout of PencilLayout:
 
 and prints the best against the ideal (no conflicts).  pt_layout in adg_kernels.cuh holds these
 results for the configurations the library builds; others use xpm = 0, ord1 = 0, MS = NP + 2.
-check() replays the kernel's index arithmetic for a layout (bounds, coverage, alignment).
+check() replays the kernel's index arithmetic for a layout (bounds, coverage, alignment),
+check_final() the final stage's trace stores, check_schedule() the double-buffered phases.
 
     python pencil_layout_model.py
 """
