@@ -43,6 +43,13 @@ def test_layout_indices(cfg):
 
 
 @pytest.mark.parametrize("cfg", M.CONFIGS, ids=[c.name for c in M.CONFIGS])
+def test_table_holds_the_models_best_layout(cfg):
+    # the kernel's constants reach the fewest modelled wavefronts of the search space (ties allowed)
+    best, _ = cfg.search()
+    assert cfg.count(TABLE[(cfg.D, cfg.n, cfg.NC)]) == best
+
+
+@pytest.mark.parametrize("cfg", M.CONFIGS, ids=[c.name for c in M.CONFIGS])
 def test_final_stage_traces(cfg):
     assert cfg.check_final(TABLE[(cfg.D, cfg.n, cfg.NC)])
 
