@@ -54,7 +54,8 @@ enum adg_status {
   ADG_ENOTINIT = -2,     /* a prerequisite call is missing */
   ADG_ECUDA = -3,        /* a CUDA runtime call failed; adg_last_error() has its text */
   ADG_ENONFINITE = -4,   /* a step produced Inf/NaN; t stops at the last good step */
-  ADG_ETIMEOUT = -5,     /* reserved: a bounded device wait ran out */
+  ADG_ETIMEOUT = -5,     /* a bounded device wait ran out (tensor-core predictors; the state is
+                            not valid, the context stays usable) */
   ADG_EUNSUPPORTED = -6, /* valid but not built (e.g. no kernel for this (PDE, d, N)) */
   ADG_ENOMEM = -7        /* workspace smaller than adg_workspace_bytes() */
 };
@@ -75,7 +76,7 @@ enum adg_kernel {
   ADG_K_PREDICTOR = 1, /* final flux, time averages, face extrapolation, volume integral */
   ADG_K_RIEMANN = 2,   /* Rusanov flux arithmetic */
   ADG_K_CORRECTOR = 3, /* face-trace storage and surface-integral arithmetic */
-  ADG_K_STORAGE = 4    /* persistent state: FP64 only */
+  ADG_K_STORAGE = 4    /* persistent state: FP64, or FP32/bf16/fp16 (see adg_set_kernel_precision) */
 };
 
 enum adg_prec { ADG_FP64 = 0, ADG_FP32 = 1, ADG_BF16 = 2, ADG_FP16 = 3, ADG_FP8E4M3 = 4 };
@@ -133,8 +134,9 @@ ADG_API int adg_destroy(adg_ctx* c);
 /* cuda_stream: a cudaStream_t (e.g. torch.cuda.current_stream().cuda_stream); NULL = legacy. */
 ADG_API int adg_set_stream(adg_ctx* c, void* cuda_stream);
 
-/* Uniform periodic mesh of [lo,hi]^dim with cells[d] cells per direction and
- * order N (dim in {2,3}).  Sec. 3: tree-structured Cartesian grid, here uniform. */
+/* Uniform mesh of [lo,hi]^dim with cells[d] cells per direction and order N (dim in {2,3}).
+ * Sec. 3: tree-structured Cartesian grid, here uniform.  Every direction is periodic: the
+ * library has no other boundary condition (so no periodic mask is taken). */
 ADG_API int adg_init_mesh(adg_ctx* c, int dim, int order_N, const int* cells, const double* lo,
                   const double* hi);
 
@@ -171,9 +173,16 @@ ADG_API int adg_set_pde(adg_ctx* c, int pde, const double* params, int nparams);
  * buffers again. */
 ADG_API int adg_set_kernel_precision(adg_ctx* c, int kernel, int prec, int flags);
 
-/* C_CFL of eq. (CFL_condition) (dt = cfl h / (d (2N+1) lambda_max)) and the
- * number of Picard sweeps (<= 0: N+1). */
-ADG_API int adg_set_numerics(adg_ctx* c, double cfl, int picard_iters);
+/* C_CFL of eq. (CFL_condition) (dt = cfl h / (d (2N+1) lambda_max)), the number of Picard sweeps
+ * of eq. (Picard) (<= 0: N+1; at most 1000) and an optional stopping tolerance of the Picard
+ * iteration.  Sec. 3.1 iterates eq. (Picard) and states no stopping rule; the library's reading is
+ * a fixed number of sweeps, with picard_tol > 0 adding one: a cell stops sweeping once the largest
+ * change of its space-time iterate over a sweep, max over time nodes, variables and nodes of
+ * |q^(r) - q^(r-1)|, is at most picard_tol (picard_iters stays the most).  picard_tol = 0 (the
+ * default) turns it off; negative or non-finite values return ADG_EINVAL.  It is built for the
+ * SIMT Picard predictor with PICARD == PREDICTOR in {FP64, FP32}; other mixes, the refinement
+ * predictor, the Cauchy-Kowalevskaya scheme and adg_adjoint return ADG_EUNSUPPORTED with it. */
+ADG_API int adg_set_numerics(adg_ctx* c, double cfl, int picard_iters, double picard_tol);
 
 /* Predictor scheme (Sec. 3.1).  ADG_PRED_PICARD (default): the Picard sweeps of eq. (Picard),
  * any PDE.  ADG_PRED_CK: the Cauchy-Kowalevskaya procedure of the last paragraph of Sec. 3.1,
@@ -185,9 +194,8 @@ ADG_API int adg_set_numerics(adg_ctx* c, double cfl, int picard_iters);
  * allocation-free adg_step_noalloc always runs the FP64 Picard kernels. */
 ADG_API int adg_set_predictor(adg_ctx* c, int scheme);
 
-/* Iterative-refinement predictor (NEXT-1 of the hot-path scope; the precision split of the
- * mixed-precision iterative refinement discussed in Sec. 2, applied to the Picard iteration of
- * eq. (Picard)).  fp64_sweeps = k > 0: of the I Picard sweeps (adg_set_numerics), the first I - k
+/* Iterative-refinement predictor (the precision split of the mixed-precision iterative
+ * refinement discussed in Sec. 2, applied to the Picard iteration of eq. (Picard)).  fp64_sweeps = k > 0: of the I Picard sweeps (adg_set_numerics), the first I - k
  * run in the PICARD precision, FP32 or BF16 (SIMT arithmetic), and the last k, started from that
  * iterate, together with the final stage (time averages, volume integral, face traces) in FP64;
  * PREDICTOR must be FP64.  Each FP64 sweep shrinks the low-precision sweeps' error by the
@@ -292,11 +300,14 @@ ADG_API int adg_nvar(int pde, int dim);
  * Limits and behaviour:
  *  - the FP64 face traces, cells * dim * 4 * V * (N+1)^(dim-1) * 8 bytes, must fit in
  *    ADG_NOALLOC_SCRATCH_BYTES - 256; larger meshes return ADG_ENOMEM before any work;
- *  - the first call on a device, with that device current, looks up the array's device address
- *    (cudaGetSymbolAddress) and keeps it; make that first call before any stream capture;
+ *  - every call looks up the array's device address on the current device
+ *    (cudaGetSymbolAddress), so a device reset between calls is handled; the first call on a
+ *    device also loads the library's device code there: make that first call before any stream
+ *    capture;
  *  - all calls share the array and it keeps the last call's contents; each call clears the
  *    scalars it needs before using them.  Calls that overlap on the GPU (other streams or
  *    threads) race on the array: serialise them;
+ *  - at most 2^30 cells and 1000 Picard sweeps (picard_iters <= 0: N+1), as the context calls;
  *  - returns ADG_EINVAL for bad arguments, ADG_EUNSUPPORTED when no kernels are built for
  *    (pde, dim, N), ADG_ENONFINITE when a step produced Inf/NaN, ADG_ECUDA on a CUDA error. */
 #define ADG_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)

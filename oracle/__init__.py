@@ -64,6 +64,8 @@ def _load():
             lib.or_destroy.argtypes = [P]
             lib.or_set_ck.argtypes = [P, C.c_int]
             lib.or_set_picard_iters.argtypes = [P, C.c_int]
+            lib.or_set_picard_tol.argtypes = [P, C.c_double]
+            lib.or_predictor_cell.restype = C.c_int
             lib.or_set_storage.argtypes = [P, C.c_int]
             lib.or_round_format.argtypes = [C.c_double, C.c_int]
             lib.or_round_format.restype = C.c_double
@@ -162,6 +164,10 @@ class Mesh:
     def set_picard_iters(self, iters: int):
         _load().or_set_picard_iters(self._h, int(iters))
 
+    def set_picard_tol(self, tol: float):
+        """Stop a cell's Picard sweeps once max |q^(r) - q^(r-1)| <= tol (0: fixed sweeps)."""
+        _load().or_set_picard_tol(self._h, float(tol))
+
     def set_storage(self, fmt):
         """Persistent solution format between the two traversals of a step (Sec. 4.1):
         'fp64', 'fp32', 'bf16' or 'fp16'."""
@@ -240,12 +246,12 @@ class Mesh:
         return out
 
     # -- predictor ----------------------------------------------------------
-    def predictor_cell(self, Qc, dt, iters=None, cell=0):
+    def predictor_cell(self, Qc, dt, iters=None, cell=0, return_sweeps=False):
         Qc = np.ascontiguousarray(Qc, dtype=np.float64).reshape(self.V, self.NS)
         q = np.zeros((self.n, self.V, self.NS))
-        _load().or_predictor_cell(self._h, cell, _dp(Qc), dt,
-                                  self.n if iters is None else int(iters), _dp(q))
-        return q
+        r = _load().or_predictor_cell(self._h, cell, _dp(Qc), dt,
+                                      self.n if iters is None else int(iters), _dp(q))
+        return (q, r) if return_sweeps else q
 
     def ck_cell(self, Qc, dt, cell=0):
         Qc = np.ascontiguousarray(Qc, dtype=np.float64).reshape(self.V, self.NS)

@@ -171,6 +171,7 @@ int or_setup(or_mesh* M, int dim, int N, const int* m, const double* lo, const d
   for (int j = 0; j < nparams && j < 8; ++j) M->pp[j] = params[j];
   M->cfl = cfl;
   M->picard_iters = picard_iters > 0 ? picard_iters : N + 1;
+  M->picard_tol = 0.0;
   M->use_ck = 0;
   M->storage = OR_ST_FP64;
   M->cell_c = NULL;
@@ -595,15 +596,17 @@ static void space_derivative_of_flux(const or_mesh* M, int cell, const double* q
   free(F);
 }
 
-void or_predictor_cell(const or_mesh* M, int cell, const double* Qc, double dt, int iters,
-                       double* q) {
+int or_predictor_cell(const or_mesh* M, int cell, const double* Qc, double dt, int iters,
+                      double* q) {
   const int n = M->n, V = M->nvar, NS = ipow(n, M->dim);
   for (int k = 0; k < n; ++k)
     for (int v = 0; v < V; ++v)
       for (int i = 0; i < NS; ++i) q[(k * V + v) * NS + i] = Qc[v * NS + i];
   double* R = (double*)malloc(sizeof(double) * (size_t)n * V * NS);
-  for (int r = 0; r < iters; ++r) {
+  int r = 0;
+  while (r < iters) {
     space_derivative_of_flux(M, cell, q, n, R);
+    double change = 0.0; /* max |q^(r+1) - q^(r)| over the cell's space-time DOFs */
     for (int v = 0; v < V; ++v)
       for (int i = 0; i < NS; ++i) {
         double rhs[OR_MAXN];
@@ -611,11 +614,16 @@ void or_predictor_cell(const or_mesh* M, int cell, const double* Qc, double dt, 
         for (int k = 0; k < n; ++k) {
           double s = 0.0;
           for (int l = 0; l < n; ++l) s += M->K1inv[k][l] * rhs[l];
+          const double d = fabs(s - q[(k * V + v) * NS + i]);
+          if (d > change) change = d;
           q[(k * V + v) * NS + i] = s;
         }
       }
+    ++r;
+    if (M->picard_tol > 0.0 && change <= M->picard_tol) break;
   }
   free(R);
+  return r;
 }
 
 /* Cauchy-Kowalevskaya predictor for linear PDEs (Sec. 3.1, last paragraph):
@@ -1013,6 +1021,8 @@ void or_destroy(or_mesh* M) { free(M); }
 void or_set_ck(or_mesh* M, int use_ck) { M->use_ck = use_ck; }
 
 void or_set_picard_iters(or_mesh* M, int iters) { M->picard_iters = iters; }
+
+void or_set_picard_tol(or_mesh* M, double tol) { M->picard_tol = tol; }
 
 /* ------------------------------------------------------------------------ */
 /* Receivers and misfit (acoustics).  A receiver samples the pressure of the */

@@ -55,7 +55,8 @@ typedef struct {
   double lo[3], h[3];
   double pp[8];       /* PDE parameters as given by the caller */
   double cfl;         /* C_CFL of eq. (CFL_condition) */
-  int picard_iters;   /* fixed number of Picard sweeps */
+  int picard_iters;   /* number of Picard sweeps (the most, with a stopping tolerance) */
+  double picard_tol;  /* optional stopping tolerance on max |q^(r) - q^(r-1)| per cell; 0 = off */
   int use_ck;         /* 1: Cauchy-Kowalevskaya predictor instead of Picard (linear PDEs) */
   int storage;        /* persistent-solution format (Sec. 4.1 "storage"): OR_ST_* */
   const double* cell_c; /* optional per-cell wave speed for acoustics (rho fixed); NULL = none */
@@ -92,9 +93,10 @@ void or_l2_error(const or_mesh* M, const double* Q, int scen, const double* sp, 
 void or_l2_diff(const or_mesh* M, const double* Qa, const double* Qb, double* out);
 void or_totals(const or_mesh* M, const double* Q, double* tot);
 
-/* one cell's predictor: q[(k*V+v)*NS+i], plus time averages */
-void or_predictor_cell(const or_mesh* M, int cell, const double* Qc, double dt, int iters,
-                       double* q);
+/* one cell's predictor: q[(k*V+v)*NS+i]; at most iters sweeps, fewer when M->picard_tol > 0
+ * and the largest change of a sweep is at most that tolerance.  Returns the sweeps taken. */
+int or_predictor_cell(const or_mesh* M, int cell, const double* Qc, double dt, int iters,
+                      double* q);
 void or_ck_cell(const or_mesh* M, int cell, const double* Qc, double dt, double* q);
 
 /* whole step */
@@ -131,6 +133,9 @@ or_mesh* or_create(int dim, int N, const int* m, const double* lo, const double*
 void or_destroy(or_mesh* M);
 void or_set_ck(or_mesh* M, int use_ck);
 void or_set_picard_iters(or_mesh* M, int iters);
+/* Picard stopping tolerance of the oracle's reading of Sec. 3.1 (the paper fixes none): a cell
+ * stops sweeping once max over k, v, i of |q^(r) - q^(r-1)| is at most tol; 0 turns it off. */
+void or_set_picard_tol(or_mesh* M, double tol);
 /* Persistent solution stored in format fmt (OR_ST_*) between the two grid traversals of a
  * step (Sec. 4.1, Algorithm 1): the step rounds Q after the predictor/volume pass and after
  * the corrector pass. */

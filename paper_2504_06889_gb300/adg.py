@@ -43,7 +43,7 @@ _SIGS = {
     "adg_init_mesh": [_P, C.c_int, C.c_int, _ip, _dp, _dp],
     "adg_set_pde": [_P, C.c_int, _dp, C.c_int],
     "adg_set_kernel_precision": [_P, C.c_int, C.c_int, C.c_int],
-    "adg_set_numerics": [_P, C.c_double, C.c_int],
+    "adg_set_numerics": [_P, C.c_double, C.c_int, C.c_double],
     "adg_set_refinement": [_P, C.c_int],
     "adg_set_predictor": [_P, C.c_int],
     "adg_workspace_bytes": [_P, C.POINTER(C.c_size_t)],
@@ -98,7 +98,7 @@ class Solver:
     """One ADER-DG context with torch-allocated state and workspace on the current device."""
 
     def __init__(self, dim, N, cells, pde, params, lo=None, hi=None, cfl=0.9, picard_iters=0,
-                 precision=None, flags=0, stream=None, scheme=PRED_PICARD, refine=0):
+                 precision=None, flags=0, stream=None, scheme=PRED_PICARD, refine=0, picard_tol=0.0):
         import torch
 
         self._torch = torch
@@ -118,7 +118,7 @@ class Solver:
         self._check(self.lib.adg_init_mesh(self.ctx, dim, N, cl, lo_p, hi_p))
         pa, pp = _d(params)
         self._check(self.lib.adg_set_pde(self.ctx, pde, pp, len(pa)))
-        self._check(self.lib.adg_set_numerics(self.ctx, cfl, picard_iters))
+        self._check(self.lib.adg_set_numerics(self.ctx, cfl, picard_iters, picard_tol))
         if isinstance(scheme, str):
             scheme = {"picard": PRED_PICARD, "ck": PRED_CK}[scheme]
         self._check(self.lib.adg_set_predictor(self.ctx, scheme))

@@ -222,6 +222,39 @@ void finalize_pde_params(PdeParams* p) {
   p->f_c = (float)p->c;
 }
 
+int parse_pde_params(int pde, int dim, const double* params, int nparams, PdeParams* out, const char** why) {
+  auto bad = [&](const char* msg) {
+    if (why) *why = msg;
+    return (int)ADG_EINVAL;
+  };
+  *out = PdeParams{};
+  if (adg_nvar(pde, dim) < 0) return bad("unknown PDE for this dimension");
+  const int need = pde == ADG_ACOUSTIC ? 2 : pde == ADG_ELASTIC ? 3 : 1;
+  if (!params || nparams < need) return bad("missing PDE parameters");
+  PdeParams& p = *out;
+  p.pde = pde;
+  if (pde == ADG_ACOUSTIC) {
+    p.rho = params[0];
+    p.K = params[1];
+    if (!(p.rho > 0 && p.K > 0)) return bad("acoustic: rho, K > 0");
+  } else if (pde == ADG_ELASTIC) {
+    p.rho = params[0];
+    p.cp = params[1];
+    p.cs = params[2];
+    p.mu = p.rho * p.cs * p.cs;
+    p.lam = p.rho * p.cp * p.cp - 2.0 * p.mu;
+    if (!(p.rho > 0 && p.cp > 0 && p.cs > 0)) return bad("elastic: rho, cp, cs > 0");
+  } else if (pde == ADG_EULER) {
+    p.gamma = params[0];
+    if (!(p.gamma > 1)) return bad("euler: gamma > 1");
+  } else {
+    p.g = params[0];
+    if (!(p.g > 0)) return bad("swe: g > 0");
+  }
+  finalize_pde_params(&p);
+  return ADG_OK;
+}
+
 }  // namespace adg
 
 using namespace adg;
@@ -241,6 +274,7 @@ struct adg_ctx {
   int flags = 0;
   double cfl = 0.9;
   int picard_iters = 0;
+  double picard_tol = 0.0;  // optional Picard stopping tolerance (0: fixed sweeps)
   int refine = 0;  // FP64 refinement sweeps (0: off)
   int scheme = ADG_PRED_PICARD;
   double* Q = nullptr;
@@ -330,6 +364,7 @@ static void fill_step_args(const adg_ctx* c, StepArgs* a) {
   a->hmin = hmin;
   a->cfl = c->cfl;
   a->picard_iters = c->picard_iters > 0 ? c->picard_iters : c->N + 1;
+  a->picard_tol = c->picard_tol;
   a->comp_sweeps = (c->flags & ADG_F_COMPENSATED_TWO) ? 2 : (c->flags & ADG_F_COMPENSATED_LAST) ? 1 : 0;
   a->per_cell_scale = (c->flags & ADG_F_PER_CELL_SCALE) ? 1 : 0;
   a->refine_sweeps = c->refine;
@@ -430,35 +465,13 @@ int adg_init_mesh(adg_ctx* c, int dim, int order_N, const int* cells, const doub
 int adg_set_pde(adg_ctx* c, int pde, const double* params, int nparams) {
   if (!c) return ADG_EINVAL;
   if (!c->have_mesh) return fail(c, ADG_ENOTINIT, "adg_init_mesh first");
-  const int V = adg_nvar(pde, c->dim);
-  if (V < 0) return fail(c, ADG_EINVAL, "unknown PDE for this dimension");
-  const int need = pde == ADG_ACOUSTIC ? 2 : pde == ADG_ELASTIC ? 3 : 1;
-  if (!params || nparams < need) return fail(c, ADG_EINVAL, "missing PDE parameters");
   PdeParams p{};
-  p.pde = pde;
-  if (pde == ADG_ACOUSTIC) {
-    p.rho = params[0];
-    p.K = params[1];
-    if (!(p.rho > 0 && p.K > 0)) return fail(c, ADG_EINVAL, "acoustic: rho, K > 0");
-  } else if (pde == ADG_ELASTIC) {
-    p.rho = params[0];
-    p.cp = params[1];
-    p.cs = params[2];
-    p.mu = p.rho * p.cs * p.cs;
-    p.lam = p.rho * p.cp * p.cp - 2.0 * p.mu;
-    if (!(p.rho > 0 && p.cp > 0 && p.cs > 0)) return fail(c, ADG_EINVAL, "elastic: rho, cp, cs > 0");
-  } else if (pde == ADG_EULER) {
-    p.gamma = params[0];
-    if (!(p.gamma > 1)) return fail(c, ADG_EINVAL, "euler: gamma > 1");
-  } else {
-    p.g = params[0];
-    if (!(p.g > 0)) return fail(c, ADG_EINVAL, "swe: g > 0");
-  }
+  const char* why = nullptr;
+  if (parse_pde_params(pde, c->dim, params, nparams, &p, &why) != ADG_OK) return fail(c, ADG_EINVAL, why);
   p.cell_c = c->d_cell_c;
-  finalize_pde_params(&p);
   c->pp = p;
   c->pde = pde;
-  c->V = V;
+  c->V = adg_nvar(pde, c->dim);
   for (int j = 0; j < nparams && j < 8; ++j) c->params[j] = params[j];
   c->have_pde = true;
   c->have_bufs = false;
@@ -488,12 +501,15 @@ int adg_set_kernel_precision(adg_ctx* c, int kernel, int prec, int flags) {
   return ADG_OK;
 }
 
-int adg_set_numerics(adg_ctx* c, double cfl, int picard_iters) {
+int adg_set_numerics(adg_ctx* c, double cfl, int picard_iters, double picard_tol) {
   if (!c) return ADG_EINVAL;
   if (!(cfl > 0.0)) return fail(c, ADG_EINVAL, "cfl must be > 0");
-  if (picard_iters > 1000) return fail(c, ADG_EINVAL, "picard_iters too large");
+  if (picard_iters > kMaxPicardIters) return fail(c, ADG_EINVAL, "picard_iters too large");
+  if (!(picard_tol >= 0.0) || !std::isfinite(picard_tol))
+    return fail(c, ADG_EINVAL, "picard_tol must be finite and >= 0");
   c->cfl = cfl;
   c->picard_iters = picard_iters;
+  c->picard_tol = picard_tol;
   return ADG_OK;
 }
 
@@ -642,6 +658,11 @@ static int select_kernels(adg_ctx* c, StepFn* pred, StepFn* corr) {
   const int rie = c->prec[ADG_K_RIEMANN], cor = c->prec[ADG_K_CORRECTOR];
   if (rie > PBF16 || cor > PBF16) return fail(c, ADG_EUNSUPPORTED, "precision mix not built");
   const int stp = c->prec[ADG_K_STORAGE];
+  if (c->picard_tol > 0.0 &&
+      (c->refine > 0 || c->scheme != ADG_PRED_PICARD || pic != prd || pic > P32))
+    return fail(c, ADG_EUNSUPPORTED,
+                "a Picard stopping tolerance is built for the SIMT Picard predictor with PICARD == PREDICTOR "
+                "in {FP64, FP32}");
   if (stp != P64) {
     const StorageEntry* se = find_storage(c->pde, c->dim, c->N);
     if (!se) return fail(c, ADG_EUNSUPPORTED, "storage below FP64 is not built for this (PDE, d, N)");
@@ -1051,6 +1072,8 @@ int adg_adjoint(adg_ctx* c, int nsteps, int nsnap, const double* xyz, int nrecv,
     return fail(c, ADG_EUNSUPPORTED, "the adjoint is built for the FP64 and FP32 predictors");
   if (c->scheme != ADG_PRED_PICARD)
     return fail(c, ADG_EUNSUPPORTED, "the adjoint transposes the Picard predictor");
+  if (c->picard_tol > 0.0)
+    return fail(c, ADG_EUNSUPPORTED, "the adjoint transposes a fixed number of Picard sweeps");
   if (c->prec[ADG_K_STORAGE] != P64) return fail(c, ADG_EUNSUPPORTED, "the adjoint needs FP64 storage");
   if (!observed || !d_grad_p0 || !d_grad_c) return fail(c, ADG_EINVAL, "null output/observation");
   AdjLayout L;

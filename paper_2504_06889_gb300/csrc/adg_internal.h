@@ -39,6 +39,12 @@ struct PdeParams {
   float f_rho, f_irho, f_K, f_lam, f_mu, f_lam2mu, f_gm1, f_gamma, f_g, f_halfg, f_c;
 };
 void finalize_pde_params(PdeParams* p);
+// The PDE and its parameters as adg_set_pde takes them (acoustic rho, K; elastic rho, c_p, c_s;
+// euler gamma; swe g), checked and finalized; shared by every entry point that takes them.
+// Returns ADG_OK, or ADG_EINVAL with *why (may be null) naming the problem.
+int parse_pde_params(int pde, int dim, const double* params, int nparams, PdeParams* out, const char** why);
+// Largest number of Picard sweeps an entry point accepts.
+constexpr int kMaxPicardIters = 1000;
 
 // Device-resident step scalars (owned by the context).
 struct DevScalars {
@@ -67,6 +73,7 @@ struct StepArgs {
   double hmin;
   double cfl;
   int picard_iters;
+  double picard_tol;   // optional stopping tolerance of the SIMT Picard sweeps (0: off)
   int comp_sweeps;     // tensor-core Picard: number of final sweeps with hi/lo compensation
   int per_cell_scale;  // tensor-core Picard: power-of-two scaling of the flux per cell
   int refine_sweeps;   // refinement predictor: the last sweeps run in FP64

@@ -197,7 +197,7 @@ __device__ __forceinline__ float store_to_float(__half x) { return __half2float(
 // wavefronts per cell and slice, against about 790 for the node-per-thread form.
 
 // Layout constants of the pencil-task form per (d, n, flux components), from the bank model
-// pencil_layout_model.py (beside this file): xpm = 1 stores the x pencils pencil-major (read and
+// tests/pencil_layout_model.py: xpm = 1 stores the x pencils pencil-major (read and
 // written by the tasks with 8-byte accesses), ord1 = 1 numbers the y pencils z + n x instead of
 // x + n z, MS is the stride of the position along a direction, CS the values per component.
 struct PtLayout {
@@ -534,6 +534,44 @@ __device__ __forceinline__ void ncp_at_node(const PP<T>& pp, const T* sF, const 
   }
 }
 
+// Optional stopping rule of the Picard sweeps (the paper fixes none; reading: a cell stops once
+// the largest change of its iterate over a sweep, max over k, v, i of |q^(r) - q^(r-1)|, is at
+// most tol).  One bit per cell of the block in `done`, the same in every thread; a stopped
+// cell's threads keep taking part in the block's barriers but no longer change their iterate.
+// s_diff: [3][CPB] bits of each cell's largest change (non-negative doubles order like their
+// bits); sweep r accumulates into row r % 3 and clears row (r + 1) % 3, which was last read two
+// end-of-sweep barriers earlier.
+template <int CPB> struct PicardStop {
+  unsigned long long* s_diff;
+  double tol;
+  unsigned int done;
+  __device__ __forceinline__ void init(unsigned long long* buf, double t, int first_cell, int ncells) {
+    s_diff = buf;
+    tol = t;
+    done = 0u;
+    for (int c = 0; c < CPB; ++c)
+      if (first_cell + c >= ncells) done |= 1u << c;  // cells past the mesh never hold a block up
+    for (int j = threadIdx.x; j < 3 * CPB; j += blockDim.x) s_diff[j] = 0ull;
+  }
+  __device__ __forceinline__ bool on() const { return tol > 0.0; }
+  __device__ __forceinline__ bool frozen(int lc) const { return (done >> lc) & 1u; }
+  __device__ __forceinline__ void begin(int r) {
+    if (on() && threadIdx.x < CPB) s_diff[((r + 1) % 3) * CPB + threadIdx.x] = 0ull;
+  }
+  __device__ __forceinline__ void record(int r, int lc, double change) {
+    if (on() && !frozen(lc)) atomicMax(&s_diff[(r % 3) * CPB + lc], (unsigned long long)__double_as_longlong(change));
+  }
+  // after sweep r: true once every cell of the block has stopped (block-uniform)
+  __device__ __forceinline__ bool end(int r) {
+    if (!on()) return false;
+    __syncthreads();
+#pragma unroll 1
+    for (int c = 0; c < CPB; ++c)
+      if (__longlong_as_double((long long)s_diff[(r % 3) * CPB + c]) <= tol) done |= 1u << c;
+    return done == (CPB >= 32 ? 0xFFFFFFFFu : ((1u << CPB) - 1u));
+  }
+};
+
 // One Picard sweep of eq. (Picard) in arithmetic T on the node-per-thread layout: q (this
 // node's iterate at every time node) is replaced by Q - dt P R(q), R_k = sum_dir D_dir F_dir(q_k)
 // (plus the non-conservative product B(q_k) grad q_k where the PDE has one).  first: every time
@@ -542,7 +580,8 @@ __device__ __forceinline__ void ncp_at_node(const PP<T>& pp, const T* sF, const 
 template <class C, class T>
 __device__ __forceinline__ void picard_sweep(T (&q)[C::n][C::V], const T (&Qh)[C::V], T* sFbuf, const T* sdtP,
                                              const T* sdtProw, const T (&Dr)[C::D][Pencil<C>::S], const PP<T>& pp,
-                                             const int* pb, const int* idx, int lc, bool first, int& buf) {
+                                             const int* pb, const int* idx, int lc, bool first, int& buf,
+                                             bool frozen = false, T* change = nullptr) {
   using Ph = Phys<C::PDE, C::D>;
   constexpr int n = C::n, V = C::V, D = C::D, VX = C::VX;
   constexpr int S = Pencil<C>::S, PD = Pencil<C>::PER_DIR;
@@ -579,7 +618,11 @@ __device__ __forceinline__ void picard_sweep(T (&q)[C::n][C::V], const T (&Qh)[C
     for (int v = 0; v < V; ++v) {
       const T rv = deriv(sF, ncpv, v);
 #pragma unroll
-      for (int kk = 0; kk < n; ++kk) q[kk][v] = Qh[v] - sdtProw[kk] * rv;
+      for (int kk = 0; kk < n; ++kk) {
+        const T nv = Qh[v] - sdtProw[kk] * rv;
+        if (change) *change = tmax(*change, tabs(nv - q[kk][v]));
+        q[kk][v] = nv;
+      }
     }
     buf ^= 1;
     return;
@@ -604,6 +647,13 @@ __device__ __forceinline__ void picard_sweep(T (&q)[C::n][C::V], const T (&Qh)[C
     }
     buf ^= 1;  // the next slice writes the other buffer
   }
+  if (change) {
+#pragma unroll
+    for (int k = 0; k < n; ++k)
+#pragma unroll
+      for (int v = 0; v < V; ++v) *change = tmax(*change, tabs(qn[k][v] - q[k][v]));
+  }
+  if (frozen) return;
 #pragma unroll
   for (int k = 0; k < n; ++k)
 #pragma unroll
@@ -698,7 +748,8 @@ template <class C, class T>
 __device__ __forceinline__ void picard_pt(T (&q)[C::n][C::V], const T (&Qh)[C::V], T* sbuf, T dtT,
                                           const Tables& tab, const T (&ih)[C::D],
                                           const PP<T>& pp, const int (&off)[C::D], int cF,
-                                          const int (&tb)[PencilTasks<C>::NSLOT], int iters) {
+                                          const int (&tb)[PencilTasks<C>::NSLOT], int iters,
+                                          PicardStop<C::CPB>& stop, int lc) {
   using Ph = Phys<C::PDE, C::D>;
   using L = PencilTasks<C>;
   constexpr int n = C::n, V = C::V, D = C::D, B = C::CPB * L::CELL;
@@ -737,17 +788,25 @@ __device__ __forceinline__ void picard_pt(T (&q)[C::n][C::V], const T (&Qh)[C::V
   };
   if (iters <= 0) return;
   // first sweep: every time node holds Q, so one flux slice serves all of them
+  stop.begin(0);
   write_slice(sF0, Qh);
   __syncthreads();
   pencil_tasks<C, T>(sF0, sR0, tab, tb);
   __syncthreads();
+  T change = T(0);
 #pragma unroll
   for (int v = 0; v < V; ++v) {
     const T drv = dt_deriv(sR0, v);
 #pragma unroll
-    for (int kk = 0; kk < n; ++kk) q[kk][v] = fmaf(-tab.fProw[kk], drv, Qh[v]);
+    for (int kk = 0; kk < n; ++kk) {
+      q[kk][v] = fmaf(-tab.fProw[kk], drv, Qh[v]);
+      if (stop.on()) change = fmaxf(change, fabsf(q[kk][v] - Qh[v]));
+    }
   }
+  if (stop.on()) stop.record(0, lc, (double)change);
+  if (stop.end(0)) return;
   for (int r = 1; r < iters; ++r) {
+    stop.begin(r);
     T qn[n][V];
 #pragma unroll
     for (int k = 0; k < n; ++k)
@@ -763,10 +822,21 @@ __device__ __forceinline__ void picard_pt(T (&q)[C::n][C::V], const T (&Qh)[C::V
       __syncthreads();
     }
     consume((n - 1) % 2 ? sR1 : sR0, n - 1, qn);
+    if (stop.on()) {
+      T ch = T(0);
 #pragma unroll
-    for (int k = 0; k < n; ++k)
+      for (int k = 0; k < n; ++k)
 #pragma unroll
-      for (int v = 0; v < V; ++v) q[k][v] = qn[k][v];
+        for (int v = 0; v < V; ++v) ch = fmaxf(ch, fabsf(qn[k][v] - q[k][v]));
+      stop.record(r, lc, (double)ch);
+    }
+    if (!stop.frozen(lc)) {
+#pragma unroll
+      for (int k = 0; k < n; ++k)
+#pragma unroll
+        for (int v = 0; v < V; ++v) q[k][v] = qn[k][v];
+    }
+    if (stop.end(r)) return;
   }
 }
 
@@ -926,7 +996,10 @@ __global__ void __launch_bounds__(C::THREADS, PredMinBlocks<C, T, CK>::value) k_
   constexpr bool kPT = !CK && UsePencilTasks<C, T>::value;  // pencil-task sweeps
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double s_dt;
+  __shared__ unsigned long long s_change[3 * CPB];
   if (a.sc->bad) return;
+  PicardStop<CPB> stop;
+  stop.init(s_change, CK ? 0.0 : a.picard_tol, blockIdx.x * CPB, a.ncells);
   const double dt = block_dt(a, D, C::N, &s_dt);
 
   // tables: dt P and its row sums (T), then Vm, w, psi0, psi1 (TP)
@@ -1069,7 +1142,7 @@ __global__ void __launch_bounds__(C::THREADS, PredMinBlocks<C, T, CK>::value) k_
 #pragma unroll
     for (int j = 0; j < L::NSLOT; ++j) tb[j] = L::task_base(j);
     const int cF = lc * L::CELL;
-    picard_pt<C, T>(q, Qh, sbuf, dtT, a.tab, ih, pp, off, cF, tb, a.picard_iters);
+    picard_pt<C, T>(q, Qh, sbuf, dtT, a.tab, ih, pp, off, cF, tb, a.picard_iters, stop, lc);
     __syncthreads();
     if constexpr (UseFinalPt<C>::value)
       predictor_final_pt<C, T, TS, TQ>(a, q, sbuf, pp, ih, dt, lc, i, cell, valid, off, cF, tb);
@@ -1077,9 +1150,14 @@ __global__ void __launch_bounds__(C::THREADS, PredMinBlocks<C, T, CK>::value) k_
       predictor_final<C, T, TP, TS, TQ>(a, q, reinterpret_cast<TP*>(smem_raw), sVm, sw, sp0, sp1, dt, lc, i,
                                         cell, valid, cl, idx, pb);
   } else {
-    if (!CK && a.picard_iters > 0) picard_sweep<C, T>(q, Qh, sFbuf, sdtP, sdtProw, Dr, pp, pb, idx, lc, true, buf);
-    for (int r = 1; !CK && r < a.picard_iters; ++r)
-      picard_sweep<C, T>(q, Qh, sFbuf, sdtP, sdtProw, Dr, pp, pb, idx, lc, false, buf);
+    for (int r = 0; !CK && r < a.picard_iters; ++r) {
+      stop.begin(r);
+      T change = T(0);
+      picard_sweep<C, T>(q, Qh, sFbuf, sdtP, sdtProw, Dr, pp, pb, idx, lc, r == 0, buf, stop.frozen(lc),
+                         stop.on() ? &change : nullptr);
+      if (stop.on()) stop.record(r, lc, conv<double>(change));
+      if (stop.end(r)) break;
+    }
     __syncthreads();
     predictor_final<C, T, TP, TS, TQ>(a, q, reinterpret_cast<TP*>(smem_raw), sVm, sw, sp0, sp1, dt, lc, i,
                                       cell, valid, cl, idx, pb);

@@ -9,10 +9,10 @@
 // How: the step's scratch (the step scalars and the face traces written by the predictor and
 // read by the corrector) lives in the file-scope array below instead of a caller-provided
 // workspace.  Every GPU that loads this library holds the array until the process exits.  Host
-// code cannot use the array's name as a device address, so the first call on each device (with
-// that device current) looks the address up once with cudaGetSymbolAddress and keeps it.
+// code cannot use the array's name as a device address, so every call looks the address up on
+// the current device with cudaGetSymbolAddress (cheap next to a step, and never stale: after a
+// device reset the module is loaded again and the lookup sees the new address).
 #include <cstring>
-#include <mutex>
 
 #include "../../include/adg.h"
 #include "adg_internal.h"
@@ -24,23 +24,12 @@ namespace {
 static __device__ __align__(256) unsigned char g_noalloc_scratch[ADG_NOALLOC_SCRATCH_BYTES];
 
 constexpr size_t kScalarBytes = 256;
-constexpr int kMaxDevices = 64;
 
-std::mutex g_mu;
-void* g_scratch_addr[kMaxDevices] = {nullptr};
-
-// Device address of g_noalloc_scratch on the current device, looked up on first use.
+// Device address of g_noalloc_scratch on the current device.
 int scratch_address(void** out) {
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess) return ADG_ECUDA;
-  if (dev < 0 || dev >= kMaxDevices) return ADG_EUNSUPPORTED;
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return ADG_ECUDA;
-    g_scratch_addr[dev] = p;
-  }
-  *out = g_scratch_addr[dev];
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return ADG_ECUDA;
+  *out = p;
   return ADG_OK;
 }
 
@@ -60,33 +49,6 @@ __global__ void k_noalloc_reset(DevScalars* sc, double t) {
   }
 }
 
-int pde_params_from(int pde, int dim, const double* p, int np, PdeParams* out) {
-  std::memset(out, 0, sizeof(*out));
-  out->pde = pde;
-  const int need = pde == ADG_ACOUSTIC ? 2 : pde == ADG_ELASTIC ? 3 : 1;
-  if (adg_nvar(pde, dim) < 0 || !p || np < need) return ADG_EINVAL;
-  if (pde == ADG_ACOUSTIC) {
-    out->rho = p[0];
-    out->K = p[1];
-    if (!(out->rho > 0 && out->K > 0)) return ADG_EINVAL;
-  } else if (pde == ADG_ELASTIC) {
-    out->rho = p[0];
-    out->cp = p[1];
-    out->cs = p[2];
-    out->mu = out->rho * out->cs * out->cs;
-    out->lam = out->rho * out->cp * out->cp - 2.0 * out->mu;
-    if (!(out->rho > 0 && out->cp > 0 && out->cs > 0)) return ADG_EINVAL;
-  } else if (pde == ADG_EULER) {
-    out->gamma = p[0];
-    if (!(out->gamma > 1)) return ADG_EINVAL;
-  } else {
-    out->g = p[0];
-    if (!(out->g > 0)) return ADG_EINVAL;
-  }
-  finalize_pde_params(out);
-  return ADG_OK;
-}
-
 }  // namespace
 }  // namespace adg
 
@@ -104,10 +66,12 @@ extern "C" int adg_step_noalloc(int pde, int dim, int order_N, const int* cells,
   StepFn pred = e->predictor[P64][P64], corr = e->corrector[P64][P64];
   if (!pred || !corr) return ADG_EUNSUPPORTED;
 
+  if (picard_iters > kMaxPicardIters) return ADG_EINVAL;
   StepArgs a;
   std::memset(&a, 0, sizeof(a));
-  if (pde_params_from(pde, dim, pde_params, nparams, &a.pp) != ADG_OK) return ADG_EINVAL;
+  if (parse_pde_params(pde, dim, pde_params, nparams, &a.pp, nullptr) != ADG_OK) return ADG_EINVAL;
   if (!build_tables(order_N + 1, &a.tab)) return ADG_EINVAL;
+  // mesh: at most 2^30 cells (as adg_init_mesh), checked while multiplying so nothing overflows
   long long ncells = 1;
   double hmin = 0.0;
   for (int d = 0; d < 3; ++d) {
@@ -117,14 +81,16 @@ extern "C" int adg_step_noalloc(int pde, int dim, int order_N, const int* cells,
     const double h = d < dim ? (hi[d] - lo[d]) / m : 1.0;
     a.invh[d] = 1.0 / h;
     if (d < dim && (d == 0 || h < hmin)) hmin = h;
+    if (m > (1LL << 30) / ncells) return ADG_EINVAL;
     ncells *= m;
   }
-  // size check: FP64 traces of every cell must fit behind the scalars
+  // size check: the FP64 traces of every cell must fit behind the scalars (compared as a cell
+  // count, so no product can overflow)
   const long long n = order_N + 1;
   long long nf = 1;
   for (int d = 1; d < dim; ++d) nf *= n;
-  const long long trace_bytes = ncells * dim * 2 * 2 * e->V * nf * (long long)sizeof(double);
-  if (trace_bytes > (long long)(ADG_NOALLOC_SCRATCH_BYTES - kScalarBytes)) return ADG_ENOMEM;
+  const long long per_cell = (long long)dim * 2 * 2 * e->V * nf * (long long)sizeof(double);
+  if (ncells > (long long)(ADG_NOALLOC_SCRATCH_BYTES - kScalarBytes) / per_cell) return ADG_ENOMEM;
 
   void* base = nullptr;
   int st = scratch_address(&base);

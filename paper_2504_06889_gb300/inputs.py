@@ -157,7 +157,7 @@ def elastic_pair(seed=3, rho=2.7, cp=6.0, cs=3.464, dim=3):
 
 # C_CFL of eq. (CFL_condition) is a stability factor that depends on N.  r[N] is
 # the linear stability limit of dt = C h / (d (2N+1) lambda) for this scheme,
-# measured with the oracle (oracle/stability_limit.py); workloads run at
+# measured with the oracle (pinned by tests/test_oracle_stability.py); workloads run at
 # C_CFL = 0.9 r[N].
 STABILITY_LIMIT = {0: 1.0, 1: 1.0, 2: 0.84, 3: 0.71, 4: 0.61, 5: 0.53, 6: 0.47}
 

@@ -18,7 +18,7 @@ results for the configurations the library builds; others use xpm = 0, ord1 = 0,
 check() replays the kernel's index arithmetic for a layout (bounds, coverage, alignment),
 check_final() the final stage's trace stores, check_schedule() the double-buffered phases.
 
-    python pencil_layout_model.py
+    python tests/pencil_layout_model.py
 """
 import itertools
 

@@ -4,7 +4,7 @@ central finite differences of the GPU misfit, and across checkpoint counts.
 Tolerances: FP64 adjoint vs the oracle's adjoint 1e-10 relative to the largest gradient entry
 (different but exact formulations: the GPU gets the material derivative by a tangent-linear
 pass, the oracle by reverse mode through stored Picard iterates); central differences 1e-6
-relative (the task's FD tolerance); the FP32-predictor form within 1e-4 of FP64.
+relative (the library's finite-difference tolerance); the FP32-predictor form within 1e-4 of FP64.
 """
 import numpy as np
 import pytest

@@ -4,7 +4,7 @@ Tolerances:
   * FP64 everywhere: elementwise |Q_gpu - Q_oracle| <= 1e-12 max|Q| (rounding-order
     differences only; the only reductions are a max and fixed-order sums).
   * FP32 Picard/predictor (and FP32 Riemann/corrector): relative eq.-(L2gauss) distance
-    <= 1e-5 (the FP32 tolerance of the benchmark spec, relative per eq. L2gauss).
+    <= 1e-5 (the FP32 tolerance this library states, relative per eq. L2gauss).
   * bf16 Riemann/corrector: relative distance <= steps * 2^-8 (one bf16 rounding unit of
     the face data per step bounds the update error; gross mistakes give O(1)).
 """

@@ -63,3 +63,54 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(adg, "_lib", None)
     with pytest.raises(ImportError):
         adg.load()
+
+
+def _noalloc_args(adg, dim, N, cells, pde=None, params=(1.4,)):
+    import ctypes as C
+
+    cl = (C.c_int * dim)(*cells)
+    lo = (C.c_double * dim)(*([0.0] * dim))
+    hi = (C.c_double * dim)(*([1.0] * dim))
+    par = (C.c_double * len(params))(*params)
+    return cl, lo, hi, par
+
+
+def test_noalloc_rejects_bad_sizes_before_touching_the_device(libpath):
+    """adg_step_noalloc checks sizes on the host first: cell counts whose products overflow, more
+    cells than adg_init_mesh allows, meshes whose traces exceed the static scratch, and more
+    Picard sweeps than adg_set_numerics allows.  Here (no GPU) a check that let such a call
+    through would reach the CUDA runtime and return ADG_ECUDA instead.  The state pointer is a
+    dummy that no correct path dereferences, so this runs on CPU-only machines only."""
+    import ctypes as C
+
+    try:
+        import torch
+
+        if torch.cuda.is_available():
+            pytest.skip("host-side checks only: run where no GPU is visible")
+    except ImportError:
+        pass
+    from paper_2504_06889_gb300 import adg
+
+    lib = adg.load()
+    dummy = C.c_void_p(1 << 20)  # 16-byte aligned, never dereferenced
+    t = C.c_double(0.0)
+    cases = [
+        # (cells, picard_iters, expected)
+        ((2**20, 2**20, 2**20), 0, adg.EINVAL),      # 2^60 cells: overflow territory
+        ((2**31 - 1, 2**31 - 1, 3), 0, adg.EINVAL),
+        ((1024, 1024, 1025), 0, adg.EINVAL),          # just above 2^30 cells
+        ((64, 64, 64), 0, adg.ENOMEM),                # traces far beyond 32 MiB
+        ((1, 1, 2**30), 0, adg.ENOMEM),               # exactly 2^30 cells pass the count check
+                                                      # and then exceed the scratch
+        ((2, 2, 2), 1001, adg.EINVAL),                # more sweeps than adg_set_numerics allows
+        ((2, 2, 2), 2**31 - 1, adg.EINVAL),
+        ((0, 2, 2), 0, adg.EINVAL),
+        ((-5, 2, 2), 0, adg.EINVAL),
+    ]
+    for cells, iters, want in cases:
+        cl, lo, hi, par = _noalloc_args(adg, 3, 2, cells)
+        rc = lib.adg_step_noalloc(adg.EULER, 3, 2, cl, lo, hi, par, 1, 0.5, iters, dummy, 1, C.byref(t),
+                                  None, None)
+        assert rc == want, (cells, iters, rc, want)
+    assert t.value == 0.0

@@ -133,3 +133,36 @@ def test_picard_converges_geometrically(oracle_mod):
     ref = M.predictor_cell(Qc, dt, iters=60)
     d = [np.abs(M.predictor_cell(Qc, dt, iters=r) - ref).max() for r in range(1, 7)]
     assert all(d[j + 1] < 0.5 * d[j] for j in range(len(d) - 1)), d
+
+
+@pytest.mark.parametrize("pde,dim,N,params,scen", [
+    (0, 2, 3, [1.0, 1.0], "acoustic"),
+    (2, 3, 2, [1.4], "euler"),
+])
+def test_picard_stopping_tolerance_follows_the_fixed_sweep_iterates(oracle_mod, pde, dim, N, params, scen):
+    """The optional stopping rule (the paper fixes no rule; the oracle's reading: a cell stops
+    once max |q^(r) - q^(r-1)| <= tol): the sweep it stops at, and its result, are fixed by the
+    fixed-sweep iterates q^(1), q^(2), ... computed independently with iters = 1, 2, ..."""
+    from paper_2504_06889_gb300 import inputs as I
+
+    wl = (I.acoustic2d_planar(m=3, N=N) if scen == "acoustic" else I.euler3d_wave(m=2, N=N))
+    M = oracle_mod.Mesh(wl.dim, wl.N, wl.cells, wl.pde, wl.params, cfl=wl.cfl)
+    Q = M.interpolate(wl.scenario, wl.sp)
+    dt = M.dt(Q)
+    Qc = Q[1]
+    iters = 12
+    its = [np.broadcast_to(Qc[None], (M.n,) + Qc.shape).copy()]
+    for r in range(1, iters + 1):
+        its.append(M.predictor_cell(Qc, dt, iters=r, cell=1))
+    change = [np.abs(its[r] - its[r - 1]).max() for r in range(1, iters + 1)]
+    assert all(change[r + 1] < change[r] for r in range(4))  # the map contracts
+    for tol in (0.0, 1e30, change[2] * 1.5, change[4] * 0.5, change[iters - 1] * 0.1):
+        M.set_picard_tol(tol)
+        q, used = M.predictor_cell(Qc, dt, iters=iters, cell=1, return_sweeps=True)
+        if tol == 0.0:
+            expect = iters
+        else:
+            expect = next((r for r in range(1, iters + 1) if change[r - 1] <= tol), iters)
+        assert used == expect, (tol, used, expect)
+        np.testing.assert_array_equal(q, its[used])
+    M.set_picard_tol(0.0)

@@ -16,7 +16,8 @@ CSRC = os.path.join(ROOT, "paper_2504_06889_gb300", "csrc")
 
 
 def model():
-    spec = importlib.util.spec_from_file_location("pencil_layout_model", os.path.join(CSRC, "pencil_layout_model.py"))
+    here = os.path.dirname(os.path.abspath(__file__))
+    spec = importlib.util.spec_from_file_location("pencil_layout_model", os.path.join(here, "pencil_layout_model.py"))
     m = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(m)
     return m
