@@ -149,13 +149,9 @@ def predictor_bytes_per_cell(pde, dim, N, trace_bytes, state_bytes=8):
 
 # DRAM bytes per cell of one predictor launch, from one ncu capture of the same kernel on a
 # 32^3 case of the workload (dram__bytes_read.sum + dram__bytes_write.sum divided by the cells);
-# the traffic of a launch is proportional to its cells.  Only valid while the kernel is
-# unchanged since the capture (the profile named beside it).
-MEASURED_TRAFFIC = {
-    ("euler3d_N5_64^3", "fp32"): (790.026e6 / 32768, "profiles/k_predictor_fp32_euler3d_N5_32cubed.md"),
-    ("euler3d_N5_64^3", "bf16tc"): (796.997e6 / 32768, "profiles/k_predictor_tcs_bf16_euler3d_N5_32cubed.md"),
-    ("euler3d_N5_64^3", "fp8tc"): (792.707e6 / 32768, "profiles/k_predictor_tc_fp8_euler3d_N5_32cubed.md"),
-}
+# the traffic of a launch is proportional to its cells.  Keyed by (workload, mix); an entry holds
+# only while the kernel is unchanged since its capture, and is removed when the kernel changes.
+MEASURED_TRAFFIC = {}
 
 
 def load_peaks():
@@ -168,13 +164,26 @@ def load_peaks():
             "sm_max_mhz": 2070.0}, "fallback"
 
 
-def alu_peak_tflops(kind, sm_mhz):
-    """FP32 (and scalar bf16, which issues at the same rate): 152 SMs x 128 lanes x 2 flop per
-    FMA x SM clock.  FP64: GB300's nominal 1.25 TFLOP/s (FP64 runs at a small fraction of the
-    FP32 rate on this part)."""
-    if kind in ("fp32", "bf16"):
-        return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
-    return 1.25
+def measure_alu_peaks(adg, stream_ptr=None):
+    """FP32 (the better of scalar and packed two-lane FMAs) and FP64 FMA rates of this GPU in
+    TFLOP/s, measured now with the library's FMA-chain kernel (best of 5 launches of ~20 ms)."""
+    import ctypes as C
+
+    from paper_2504_06889_gb300 import adg as A
+
+    lib = A.load()
+    f = lib.adg_measure_fma_peak
+    f.argtypes = [C.c_int, C.c_int, C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    f.restype = C.c_int
+    out = {}
+    for key, prec in (("fp32_scalar", A.FP32), ("fp32_x2", A.MEASURE_FP32X2), ("fp64", A.FP64)):
+        tf, ms = C.c_double(), C.c_double()
+        rc = f(prec, 5, stream_ptr, C.byref(tf), C.byref(ms))
+        if rc != A.OK:
+            raise RuntimeError(f"adg_measure_fma_peak({key}) failed: {rc}")
+        out[key] = tf.value
+    out["fp32"] = max(out["fp32_scalar"], out["fp32_x2"])
+    return out
 
 
 class ClockSampler:
@@ -260,9 +269,27 @@ def max_over_ranks(x, ws):
     return float(t.item())
 
 
-def cpu_oracle_sample(wl, sample_cells, steps=1):
+def wl_label(wl):
+    """Workload name with its actual mesh (the generators' names carry their default sizes)."""
+    base = wl.name.split("_N")[0]
+    cells = wl.cells[0] if len(set(wl.cells)) == 1 else "x".join(map(str, wl.cells))
+    return f"{base}_N{wl.N}_{cells}^{wl.dim}" if len(set(wl.cells)) == 1 else f"{base}_N{wl.N}_{cells}"
+
+
+def cpu_oracle_sample(wl, sample_cells, steps=1, threads=None):
     """Time the FP64 oracle (as it stands) for `steps` steps on a sample mesh of the same
-    workload (same N, PDE, scenario, per-cell work) with all host cores."""
+    workload (same N, PDE, scenario, per-cell work).  threads=None: all host cores in this
+    process; an integer: a child process with that many OpenMP threads (the thread count of a
+    loaded OpenMP runtime cannot be changed)."""
+    if threads is not None:
+        code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+                "from paper_2504_06889_gb300 import inputs as I; "
+                "wl = I.WORKLOADS[%r]().with_cells(%r); "
+                "print(json.dumps(bench.cpu_oracle_sample(wl, %d, %d)))"
+                % (ROOT, wl.name.split("_")[0], tuple(wl.cells), sample_cells, steps))
+        env = dict(os.environ, OMP_NUM_THREADS=str(threads))
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, check=True)
+        return json.loads(out.stdout.strip().splitlines()[-1])
     cores = os.cpu_count() or 1
     os.environ.setdefault("OMP_NUM_THREADS", str(cores))
     import oracle
@@ -276,7 +303,7 @@ def cpu_oracle_sample(wl, sample_cells, steps=1):
     el = time.perf_counter() - t0
     return {"value": sw.dofs * steps / el, "unit": UNIT, "cores": int(os.environ["OMP_NUM_THREADS"]),
             "kind": "oracle",
-            "sample": f"{sw.name}: {steps} step(s) on {sample_cells}^{wl.dim} cells of the same "
+            "sample": f"{wl_label(sw)}: {steps} step(s) on {sample_cells}^{wl.dim} cells of the same "
                       f"workload ({sw.dofs} DOF), {el:.2f} s"}
 
 
@@ -332,58 +359,69 @@ def run_reference(args, wl):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": wl.name, "mix": "fp64 (CPU oracle)", "sample_cells": [sc] * wl.dim},
+        "config": {"workload": wl_label(wl), "mix": "fp64 (CPU oracle)", "sample_cells": [sc] * wl.dim},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": int(os.environ["OMP_NUM_THREADS"]),
                          "kind": "oracle",
-                         "sample": f"each step on {sc}^{wl.dim} cells of {wl.name} ({sw.dofs} DOF)"},
+                         "sample": f"each step on {sc}^{wl.dim} cells of {wl_label(wl)} ({sw.dofs} DOF)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="euler3d", choices=sorted(I.WORKLOADS))
-    ap.add_argument("--cells", type=int, default=0, help="override cells per direction")
-    ap.add_argument("--mixes", default="")
-    ap.add_argument("--sweep", action="store_true", help="per-kernel precision sweep (27 mixes)")
-    ap.add_argument("--adjoint", action="store_true", help="also time the adjoint (acoustics)")
-    ap.add_argument("--nsnap", type=int, default=10)
-    ap.add_argument("--headline", default="fp32")
-    ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--ref-cells", type=int, default=12)
-    ap.add_argument("--cpu-cells", type=int, default=24)
-    args = ap.parse_args()
-    wl = I.WORKLOADS[args.workload]()
-    if args.cells:
-        wl = wl.with_cells((args.cells,) * wl.dim)
-    if args.impl == "reference":
-        return run_reference(args, wl)
+def roofline_of(wl, mix, prec, scheme, ms_pred, alu, peaks):
+    """Roofline of the predictor launch (the dominant kernel) from algorithmic flops and the
+    measured peaks: T_roof = F_tc / P_tc + F_fp32 / P_fp32 + F_fp64 / P_fp64 per cell (one term
+    per pipe the mix uses), achieved = flops / measured time, peak = flops / T_roof (the
+    effective peak of the mix), frac = achieved / peak = T_roof / T_measured.  Tensor-core
+    contractions count their algorithmic flops only (no padding, no compensation passes)."""
+    n, NS = wl.N + 1, (wl.N + 1) ** wl.dim
+    V = I.nvar(wl.pde, wl.dim)
+    nz = NZ[(wl.pde, wl.dim)]
+    f_all = predictor_flops_per_cell(wl.pde, wl.dim, wl.N, scheme=scheme)
+    f64 = 2 * V * NS  # the FP64 volume update of the state: one FMA per DOF
+    f_tc = 0
+    if prec["picard"] == "fp64" and prec["predictor"] == "fp64":
+        f64 = f_all
+    elif mix in MIX_REFINE:
+        first, sweep, final = predictor_flop_parts(wl.pde, wl.dim, wl.N)
+        k = min(MIX_REFINE[mix], n)
+        nlo = n - k
+        f_lo = (first + (nlo - 1) * sweep) if nlo > 0 else 0
+        f64 = f_all - f_lo
+    elif prec["picard"] in ("bf16", "fp16", "fp8") and prec["predictor"] == "fp32":
+        f_tc = NS * nz * 2 * n * (1 + (n - 1) * n)  # contractions of the first and n - 1 further sweeps
+    f32 = f_all - f_tc - f64
+    p_tc = peaks["bf16_tflops"] * (2.0 if prec["picard"] == "fp8" else 1.0)
+    t_roof = f_tc / (p_tc * 1e12) + f32 / (alu["fp32"] * 1e12) + f64 / (alu["fp64"] * 1e12)
+    cells = wl.ncells
+    achieved = f_all * cells / (ms_pred * 1e-3) / 1e12
+    peak = f_all / t_roof / 1e12
+    pipes = [p for p, f in (("tensor", f_tc), ("fp32", f32), ("fp64", f64)) if f > 0]
+    tr = MEASURED_TRAFFIC.get((wl_label(wl), mix))
+    out = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+           "traffic": tr * cells if tr else None,
+           "kernel": ("k_predictor_tcs" if mix in ("bf16tc", "fp16tc") and wl.pde != I.ELASTIC
+                      else "k_predictor_tc" if mix.endswith("tc") else
+                      "k_predictor_refine" if mix in MIX_REFINE else "k_predictor"),
+           "flops_split": {"tensor": f_tc * cells, "fp32": f32 * cells, "fp64": f64 * cells},
+           "peak_source": "composite of " + " + ".join(pipes) + " at peaks measured in this run (FMA-chain "
+                          "kernel: fp32 %.1f, fp64 %.2f TFLOP/s)%s" % (
+                              alu["fp32"], alu["fp64"],
+                              "; tensor: bf16 %.0f TFLOP/s of measured (MEASURED_PEAKS.json)%s" % (
+                                  peaks["bf16_tflops"], ", x2 for E4M3" if prec["picard"] == "fp8" else "")
+                              if f_tc else "")}
+    if tr:
+        out["traffic_source"] = "ncu capture of the same kernel on 32^3 cells, scaled by the cells"
+    return out
 
+
+def run_mixes(adg, wl, mixes, table, args, ws, local, alu, peaks, headline=None, e2e=False):
+    """W untimed and K timed steps of every mix from the same initial state; per mix its
+    DOF-updates/s, kernel times, accuracy and roofline.  Clocks are sampled during the headline
+    mix's timed region."""
     import torch
 
-    from paper_2504_06889_gb300 import adg
-
-    ws, rank, local = dist_setup()
-    adg.load()
-    peaks, peak_src = load_peaks()
-    table = dict(MIXES)
-    if args.sweep:
-        table.update(sweep_mixes())
-        mixes = list(sweep_mixes())
-    else:
-        mixes = [m for m in (args.mixes or DEFAULT_MIXES[args.workload]).split(",") if m]
-    headline = args.headline if args.headline in mixes else (
-        "fp32" if "fp32" in mixes else "pred-fp32_riem-fp32_corr-fp32" if args.sweep else mixes[-1])
-    results = {}
-    ref_state = {}
-    launches = 0
-    clocks = None
+    results, ref_state, clocks = {}, {}, None
     for mix in mixes:
         prec = table[mix]
         scheme = MIX_SCHEME.get(mix, "picard")
@@ -408,8 +446,6 @@ def main():
         if sampler:
             clocks = sampler.stop()
         ms = max_over_ranks(e0.elapsed_time(e1), ws)
-        if mix == headline:
-            launches = 2 * args.steps
         r = {"dof_per_s": ws * wl.dofs * args.steps / (ms * 1e-3), "ms_per_step": ms / args.steps,
              "ms_predictor": ms_pred / args.steps, "ms_corrector": ms_corr / args.steps, "t": t}
         if wl.has_exact:
@@ -421,39 +457,12 @@ def main():
             r["l2_rel_vs_fp64_gpu"] = 0.0
         elif scheme in ref_state:
             r["l2_rel_vs_fp64_gpu"] = s.l2_diff(ref_state[scheme][0])[1] / ref_state[scheme][1]
-        # roofline of the dominant kernel (the predictor)
-        cells = wl.ncells
-        fl = predictor_flops_per_cell(wl.pde, wl.dim, wl.N, scheme=scheme) * cells
-        kind = {"fp64": "fp64", "bf16": "fp32" if prec["predictor"] == "fp32" else "bf16"}.get(
-            prec["picard"], "fp32")
-        sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-        pk = alu_peak_tflops(kind, sm_mhz)
-        ach = fl / (ms_pred / args.steps * 1e-3) / 1e12
-        if mix in MIX_REFINE:
-            # composite bound: the low-precision sweeps at the FP32 peak, the FP64 sweeps and the
-            # final stage at the FP64 peak; the effective peak is flops / that time
-            first, sweep, final = predictor_flop_parts(wl.pde, wl.dim, wl.N)
-            k = min(MIX_REFINE[mix], wl.N + 1)
-            nlo = wl.N + 1 - k
-            f_lo = (first + (nlo - 1) * sweep) if nlo > 0 else 0
-            f_hi = fl / cells - f_lo
-            t_roof = f_lo / (alu_peak_tflops("fp32", sm_mhz) * 1e12) + f_hi / (alu_peak_tflops("fp64", sm_mhz) * 1e12)
-            pk = fl / cells / t_roof / 1e12
-            kind = "fp32+fp64 composite"
-        tr = MEASURED_TRAFFIC.get((wl.name, mix)) if wl.name.endswith(f"{wl.cells[0]}^{wl.dim}") else None
-        r["roofline"] = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
-                         "frac": ach / pk, "traffic": tr[0] * cells if tr else None,
-                         "kernel": "k_predictor_tcs" if mix in ("bf16tc", "fp16tc") and wl.pde != I.ELASTIC
-                         else "k_predictor_tc" if "tc" in mix else "k_predictor",
-                         "peak_source": f"{kind} ALU derived at {sm_mhz:.0f} MHz"}
-        if tr:
-            r["roofline"]["traffic_source"] = f"ncu capture on 32^3 cells scaled by the cells ({tr[1]})"
+        r["roofline"] = roofline_of(wl, mix, prec, scheme, ms_pred / args.steps, alu, peaks)
         tb = {"fp64": 8, "fp32": 4, "bf16": 2}[prec["corrector"]]
         sb = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}[prec.get("storage", "fp64")]
-        bts = predictor_bytes_per_cell(wl.pde, wl.dim, wl.N, tb, sb) * cells
+        bts = predictor_bytes_per_cell(wl.pde, wl.dim, wl.N, tb, sb) * wl.ncells
         r["predictor_gbs"] = bts / (ms_pred / args.steps * 1e-3) / 1e9
-        results[mix] = r
-        if mix == headline and not args.no_e2e:
+        if mix == headline and e2e:
             # end to end through the public API with pinned host buffers, every step
             host = torch.empty(s.Q.shape, dtype=torch.float64, pin_memory=True)
             host.copy_(s.Q)
@@ -470,35 +479,122 @@ def main():
             nb = host.numel() * 8
             r["e2e"] = {"value": ws * wl.dofs * ke / el, "unit": UNIT, "h2d_bytes_per_step": nb,
                         "d2h_bytes_per_step": nb, "steps": ke}
+        results[mix] = r
         s.close()
         del s
         torch.cuda.empty_cache()
+    return results, clocks
 
+
+def compact(results):
+    """Per mix: DOF-updates/s, ms per step (predictor, corrector), L2 vs exact, relative L2 vs the
+    FP64 GPU path and the predictor's roofline fraction (short enough to stay in the line)."""
+    out = {}
+    for mix, r in results.items():
+        out[mix] = {"value": float("%.4g" % r["dof_per_s"]), "ms": round(r["ms_per_step"], 3),
+                    "pred_ms": round(r["ms_predictor"], 3), "corr_ms": round(r["ms_corrector"], 3),
+                    "l2_exact": float("%.3g" % r["l2_vs_exact"]) if "l2_vs_exact" in r else None,
+                    "rel_fp64": float("%.3g" % r["l2_rel_vs_fp64_gpu"]) if "l2_rel_vs_fp64_gpu" in r else None,
+                    "frac": round(r["roofline"]["frac"], 3)}
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="euler3d", choices=sorted(I.WORKLOADS))
+    ap.add_argument("--cells", type=int, default=0, help="override cells per direction")
+    ap.add_argument("--mixes", default="")
+    ap.add_argument("--sweep", action="store_true", help="per-kernel precision sweep (27 mixes)")
+    ap.add_argument("--adjoint", action="store_true", help="also time the adjoint (acoustics)")
+    ap.add_argument("--nsnap", type=int, default=10)
+    ap.add_argument("--headline", default="fp32")
+    ap.add_argument("--second", default="elastic3d",
+                    help="second workload block of the default run ('' for none)")
+    ap.add_argument("--second-mixes", default="fp64,fp32,fp16tc,fp8tc")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--ref-cells", type=int, default=12)
+    ap.add_argument("--cpu-cells", type=int, default=24)
+    ap.add_argument("--cpu1-cells", type=int, default=10)
+    args = ap.parse_args()
+    wl = I.WORKLOADS[args.workload]()
+    if args.cells:
+        wl = wl.with_cells((args.cells,) * wl.dim)
+    if args.impl == "reference":
+        return run_reference(args, wl)
+
+    import torch
+
+    from paper_2504_06889_gb300 import adg
+
+    ws, rank, local = dist_setup()
+    adg.load()
+    peaks, peak_src = load_peaks()
+    alu = measure_alu_peaks(adg)
+    table = dict(MIXES)
+    if args.sweep:
+        table.update(sweep_mixes())
+        mixes = list(sweep_mixes())
+    else:
+        mixes = [m for m in (args.mixes or DEFAULT_MIXES[args.workload]).split(",") if m]
+    headline = args.headline if args.headline in mixes else (
+        "fp32" if "fp32" in mixes else "pred-fp32_riem-fp32_corr-fp32" if args.sweep else mixes[-1])
+    results, clocks = run_mixes(adg, wl, mixes, table, args, ws, local, alu, peaks, headline=headline,
+                                e2e=not args.no_e2e)
+    second = None
+    run_second = (args.second and not args.mixes and not args.sweep and not args.cells
+                  and args.workload == "euler3d" and args.second in I.WORKLOADS)
+    if run_second:
+        wl2 = I.WORKLOADS[args.second]()
+        mixes2 = [m for m in args.second_mixes.split(",") if m]
+        res2, _ = run_mixes(adg, wl2, mixes2, table, args, ws, local, alu, peaks)
+        second = {"workload": wl_label(wl2), "dof": wl2.dofs,
+                  "fp64_gpu_value": res2["fp64"]["dof_per_s"] if "fp64" in res2 else None,
+                  "mixes": compact(res2)}
     adjoint = None
     if args.adjoint and wl.pde == I.ACOUSTIC and wl.dim == 3:
         adjoint = time_adjoint(adg, wl, args.nsnap)
     if rank != 0:
         return
     h = results[headline]
-    cpu = None if args.no_cpu else cpu_oracle_sample(wl, args.cpu_cells)
+    cpu = cpu1 = None
+    if not args.no_cpu:
+        cpu = cpu_oracle_sample(wl, args.cpu_cells)
+        cpu1 = cpu_oracle_sample(wl, args.cpu1_cells, threads=1)
+    fp64v = results["fp64"]["dof_per_s"] if "fp64" in results else None
     line = {
         "metric": METRIC, "value": h["dof_per_s"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": h["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": DTYPE.get(headline, headline),
         "data": "synthetic",
-        "config": {"workload": wl.name, "pde": I.PDE_NAMES[wl.pde], "dim": wl.dim, "N": wl.N,
+        "config": {"workload": wl_label(wl), "pde": I.PDE_NAMES[wl.pde], "dim": wl.dim, "N": wl.N,
                    "cells": list(wl.cells), "dof": wl.dofs, "mix": headline, "cfl": wl.cfl,
                    "parallelism": "replicas" if ws > 1 else "single",
                    "l2_flush": "inputs larger than L2 (FP64 state %.2f GB)" % (wl.dofs * 8 / 1e9)},
-        "mixes": results,
-        "roofline": dict(h["roofline"], peak_source=h["roofline"]["peak_source"] + f" ({peak_src} peaks file)"),
+        "fp64_gpu_value": fp64v,
+        "vs_fp64_gpu": h["dof_per_s"] / fp64v if fp64v else None,
+        "l2_vs_exact": h.get("l2_vs_exact"),
+        "l2_rel_vs_fp64_gpu": h.get("l2_rel_vs_fp64_gpu"),
+        "mixes": compact(results),
+        "roofline": h["roofline"],
+        "alu_peaks_measured": {k: round(v, 3) for k, v in alu.items()},
         "cpu_baseline": cpu,
+        "cpu_baseline_1thread": cpu1,
         "e2e": h.get("e2e"),
-        "gpu_launches": launches,
+        "gpu_launches": 2 * args.steps,
         "clocks": clocks,
     }
+    if second is not None:
+        line["second_workload"] = second
     if adjoint is not None:
         line["adjoint"] = adjoint
+    # the full per-mix records (per-variable errors, kernel names, bandwidths) go to stderr, so
+    # that stdout carries the one result line
+    print(json.dumps({"detail": {wl_label(wl): results}, "peaks_file": peak_src}), file=sys.stderr, flush=True)
     print(json.dumps(line), flush=True)
 
 

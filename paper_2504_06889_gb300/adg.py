@@ -20,6 +20,7 @@ FP64, FP32, BF16, FP16, FP8E4M3 = 0, 1, 2, 3, 4
 F_COMPENSATED_LAST, F_PER_CELL_SCALE, F_COMPENSATED_TWO = 1, 2, 4
 F_TEST_SKIP_MMA = 256  # testing aid: the tensor-core predictors' first MMA round is skipped
 PRED_PICARD, PRED_CK = 0, 1
+MEASURE_FP32X2 = 101  # adg_measure_fma_peak: packed two-lane FP32 FMAs
 SC_PLANAR, SC_EULER_WAVE, SC_SWE_MODES, SC_GAUSS_PULSE, SC_LAKE = 0, 1, 2, 3, 4
 SC_EULER_BELL, SC_EULER_VORTEX = 5, 6
 PREC_NAMES = {"fp64": FP64, "fp32": FP32, "bf16": BF16, "fp16": FP16, "fp8": FP8E4M3, "fp8e4m3": FP8E4M3}
@@ -64,6 +65,7 @@ _SIGS = {
     "adg_adjoint_workspace_bytes": [_P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_size_t)],
     "adg_misfit": [_P, C.c_int, _dp, C.c_int, _dp, _dp, _dp, _P, C.c_size_t],
     "adg_adjoint": [_P, C.c_int, C.c_int, _dp, C.c_int, _dp, _dp, _P, _P, _P, C.c_size_t],
+    "adg_measure_fma_peak": [C.c_int, C.c_int, _P, _dp, _dp],
     "adg_step_noalloc": [C.c_int, C.c_int, C.c_int, _ip, _dp, _dp, _dp, C.c_int, C.c_double, C.c_int,
                          _P, C.c_int, _dp, _dp, _P],
 }
