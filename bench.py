@@ -57,6 +57,9 @@ MIXES = {
     # E4M3 inputs (kind::f8f6f4, K = 32 per instruction: four pencils per accumulator row)
     "fp8tc": {"picard": "fp8", "predictor": "fp32", "riemann": "fp32", "corrector": "fp32"},
 }
+# bf16 tensor-core sweeps (flux offset, compensated last sweep) with the final stage, the Riemann
+# solver and the corrector in FP64
+MIXES["bf16tc64"] = {"picard": "bf16", "predictor": "fp64", "riemann": "fp64", "corrector": "fp64"}
 # Cauchy-Kowalevskaya predictor (linear PDEs) in place of the Picard sweeps
 MIXES["fp64ck"] = dict(MIXES["fp64"])
 MIXES["fp32ck"] = dict(MIXES["fp32"])
@@ -66,7 +69,7 @@ MIX_SCHEME = {"fp64ck": "ck", "fp32ck": "ck"}
 for _k in ("fp64", "fp32"):
     for _s, _n in (("fp32", "32"), ("fp16", "16"), ("bf16", "bf16")):
         MIXES[f"{_k}s{_n}"] = dict(MIXES[_k], storage=_s)
-MIX_FLAGS = {"bf16tc": 1 | 2, "fp16tc": 1 | 2, "fp8tc": 1 | 2}
+MIX_FLAGS = {"bf16tc": 1 | 2, "fp16tc": 1 | 2, "fp8tc": 1 | 2, "bf16tc64": 1}
 # iterative refinement: the first Picard sweeps in FP32 (or bf16) arithmetic, the last k sweeps,
 # the final stage, the Riemann solver and the corrector in FP64
 MIX_REFINE = {}
@@ -97,6 +100,7 @@ def sweep_mixes():
                                                     "corrector": c}
     return out
 DTYPE = {"fp64": "f64", "fp32pred": "f32+f64", "fp32": "f32+f64", "bf16tc": "bf16+f32+f64",
+         "bf16tc64": "bf16+f32+f64",
          "fp16tc": "f16+f32+f64", "fp8tc": "e4m3+f32+f64", "fp64ck": "f64", "fp32ck": "f32+f64",
          "fp64s32": "f64", "fp64s16": "f64", "fp64sbf16": "f64",
          "fp32s32": "f32+f64", "fp32s16": "f32+f64", "fp32sbf16": "f32+f64",
@@ -388,8 +392,11 @@ def roofline_of(wl, mix, prec, scheme, ms_pred, alu, peaks):
         nlo = n - k
         f_lo = (first + (nlo - 1) * sweep) if nlo > 0 else 0
         f64 = f_all - f_lo
-    elif prec["picard"] in ("bf16", "fp16", "fp8") and prec["predictor"] == "fp32":
+    elif prec["picard"] in ("bf16", "fp16", "fp8") and prec["predictor"] in ("fp32", "fp64"):
         f_tc = NS * nz * 2 * n * (1 + (n - 1) * n)  # contractions of the first and n - 1 further sweeps
+        if prec["predictor"] == "fp64":  # the final stage in FP64
+            first, sweep, final = predictor_flop_parts(wl.pde, wl.dim, wl.N)
+            f64 = final
     f32 = f_all - f_tc - f64
     p_tc = peaks["bf16_tflops"] * (2.0 if prec["picard"] == "fp8" else 1.0)
     t_roof = f_tc / (p_tc * 1e12) + f32 / (alu["fp32"] * 1e12) + f64 / (alu["fp64"] * 1e12)
@@ -400,8 +407,9 @@ def roofline_of(wl, mix, prec, scheme, ms_pred, alu, peaks):
     tr = MEASURED_TRAFFIC.get((wl_label(wl), mix))
     out = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
            "traffic": tr * cells if tr else None,
-           "kernel": ("k_predictor_tcs" if mix in ("bf16tc", "fp16tc") and wl.pde != I.ELASTIC
-                      else "k_predictor_tc" if mix.endswith("tc") else
+           "kernel": ("k_predictor_tcp" if mix in ("bf16tc", "bf16tc64") and wl.pde == I.EULER
+                      else "k_predictor_tcs" if mix == "fp16tc" and wl.pde != I.ELASTIC
+                      else "k_predictor_tc" if "tc" in mix else
                       "k_predictor_refine" if mix in MIX_REFINE else "k_predictor"),
            "flops_split": {"tensor": f_tc * cells, "fp32": f32 * cells, "fp64": f64 * cells},
            "peak_source": "composite of " + " + ".join(pipes) + " at peaks measured in this run (FMA-chain "

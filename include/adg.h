@@ -151,6 +151,10 @@ ADG_API int adg_set_pde(adg_ctx* c, int pde, const double* params, int nparams);
  *              the operands hold F - F_c, F_c the flux at the cell's first node, which the
  *              derivative annihilates; 3D Euler runs whole sweeps per MMA round, the other
  *              PDEs and E4M3 one round per time slice);
+ *              BF16 with PREDICTOR FP64 (3D Euler N = 5, no refinement): the bf16 tensor-core
+ *              sweeps as above, then the final stage (last fluxes, time averages, volume integral,
+ *              face traces) in FP64 from q_k = Q - (dt P R)_k, the FP64 state minus the sweeps'
+ *              FP32 correction;
  *              BF16 with PREDICTOR BF16: the whole predictor in bf16 arithmetic (SIMT, built
  *              for shallow water); FP32 or BF16 with PREDICTOR FP64 and adg_set_refinement:
  *              low-precision sweeps refined by FP64 sweeps
@@ -180,8 +184,9 @@ ADG_API int adg_set_kernel_precision(adg_ctx* c, int kernel, int prec, int flags
  * change of its space-time iterate over a sweep, max over time nodes, variables and nodes of
  * |q^(r) - q^(r-1)|, is at most picard_tol (picard_iters stays the most).  picard_tol = 0 (the
  * default) turns it off; negative or non-finite values return ADG_EINVAL.  It is built for the
- * SIMT Picard predictor with PICARD == PREDICTOR in {FP64, FP32}; other mixes, the refinement
- * predictor, the Cauchy-Kowalevskaya scheme and adg_adjoint return ADG_EUNSUPPORTED with it. */
+ * SIMT Picard predictor with PICARD == PREDICTOR in {FP64, FP32} and FP64 storage; other mixes, the
+ * refinement predictor, the Cauchy-Kowalevskaya scheme and adg_adjoint return ADG_EUNSUPPORTED
+ * with it. */
 ADG_API int adg_set_numerics(adg_ctx* c, double cfl, int picard_iters, double picard_tol);
 
 /* Predictor scheme (Sec. 3.1).  ADG_PRED_PICARD (default): the Picard sweeps of eq. (Picard),

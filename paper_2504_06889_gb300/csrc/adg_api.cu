@@ -659,10 +659,10 @@ static int select_kernels(adg_ctx* c, StepFn* pred, StepFn* corr) {
   if (rie > PBF16 || cor > PBF16) return fail(c, ADG_EUNSUPPORTED, "precision mix not built");
   const int stp = c->prec[ADG_K_STORAGE];
   if (c->picard_tol > 0.0 &&
-      (c->refine > 0 || c->scheme != ADG_PRED_PICARD || pic != prd || pic > P32))
+      (c->refine > 0 || c->scheme != ADG_PRED_PICARD || pic != prd || pic > P32 || stp != P64))
     return fail(c, ADG_EUNSUPPORTED,
                 "a Picard stopping tolerance is built for the SIMT Picard predictor with PICARD == PREDICTOR "
-                "in {FP64, FP32}");
+                "in {FP64, FP32} and FP64 storage");
   if (stp != P64) {
     const StorageEntry* se = find_storage(c->pde, c->dim, c->N);
     if (!se) return fail(c, ADG_EUNSUPPORTED, "storage below FP64 is not built for this (PDE, d, N)");
@@ -686,6 +686,9 @@ static int select_kernels(adg_ctx* c, StepFn* pred, StepFn* corr) {
     if (pic != prd || pic > P32)
       return fail(c, ADG_EUNSUPPORTED, "Cauchy-Kowalevskaya predictor: PICARD == PREDICTOR in {FP64, FP32}");
     *pred = c->entry->predictor_ck[pic][cor];
+  } else if (pic == PBF16 && prd == P64 && c->entry->predictor_tc_f64[cor]) {
+    // bf16 tensor-core sweeps, the final stage in FP64 from the FP64 state and the correction
+    *pred = c->entry->predictor_tc_f64[cor];
   } else if ((pic == PBF16 && prd == P32) || pic == PF16 || pic == PF8) {
     if (prd != P32) return fail(c, ADG_EUNSUPPORTED, "tensor-core Picard needs an FP32 predictor stage");
     if (cor > P32) return fail(c, ADG_EUNSUPPORTED, "tensor-core Picard writes FP32 or FP64 traces");

@@ -130,6 +130,9 @@ struct Entry {
   StepFn corrector[3][3];
   // tensor-core Picard with FP32 final stage: [0 = bf16, 1 = fp16, 2 = fp8 E4M3][trace prec]
   StepFn predictor_tc[3][3];
+  // bf16 tensor-core Picard sweeps with an FP64 final stage (PICARD BF16, PREDICTOR FP64)
+  // [trace prec]
+  StepFn predictor_tc_f64[3];
   // Cauchy-Kowalevskaya predictor (linear PDEs): [P64 / P32 arithmetic][trace prec]
   StepFn predictor_ck[2][3];
   // refinement predictor (low-precision sweeps, then FP64 sweeps and final stage):

@@ -347,14 +347,18 @@ template <class C, class T, class TP, bool PT = false> struct PredSmem {
 // last iterate, time averages Qbar = sum_k w_k q_k and Fbar = sum_k w_k F(q_k), the volume
 // integral added to Q in FP64 and the face traces of Qbar and Fbar.n written in TS.
 // smem_fin: CPB * (D V PD + V NS) values of TP; must not alias the tables.
-template <class C, class T, class TP, class TS, class TQ = double>
+// DELTA: q holds the iterate's correction, q_k = Q64 - q[k] (formed in FP64 from the node's FP64
+// state Q64), for a final stage in higher precision than the sweeps.
+template <class C, class T, class TP, class TS, class TQ = double, bool DELTA = false>
 __device__ __forceinline__ void predictor_final(const StepArgs& a, const T (*q)[C::V], TP* smem_fin,
                                                 const TP* sVm, const TP* sw, const TP* sp0, const TP* sp1,
                                                 double dt, int lc, int i, int cell, bool valid, int cl,
-                                                const int* idx, const int* pb, bool owner = true) {
+                                                const int* idx, const int* pb, bool owner = true,
+                                                const double* Q64 = nullptr) {
   using Ph = Phys<C::PDE, C::D>;
   constexpr int n = C::n, V = C::V, D = C::D, NS = C::NS, NF = C::NF;
   constexpr int S = Pencil<C>::S, PD = Pencil<C>::PER_DIR;
+  static_assert(!DELTA || C::NG == 0, "the correction form serves conservative PDEs");
   // ---- final flux, time averages (Qbar = sum_k w_k q_k, Fbar = sum_k w_k F(q_k)) ---------------
   const PP<TP> ppP = make_pp<TP>(a.pp, cl);
   TP Fb[D][V], Qb[V];
@@ -368,7 +372,12 @@ __device__ __forceinline__ void predictor_final(const StepArgs& a, const T (*q)[
   for (int k = 0; k < n; ++k) {
     TP qk[V];
 #pragma unroll
-    for (int v = 0; v < V; ++v) qk[v] = conv<TP>(q[k][v]);
+    for (int v = 0; v < V; ++v) {
+      if constexpr (DELTA)
+        qk[v] = conv<TP>(Q64[v] - (double)q[k][v]);
+      else
+        qk[v] = conv<TP>(q[k][v]);
+    }
     TP F[D][V];
     Ph::flux(ppP, qk, F);
     const TP wk = sw[k];
@@ -538,32 +547,43 @@ __device__ __forceinline__ void ncp_at_node(const PP<T>& pp, const T* sF, const 
 // the largest change of its iterate over a sweep, max over k, v, i of |q^(r) - q^(r-1)|, is at
 // most tol).  One bit per cell of the block in `done`, the same in every thread; a stopped
 // cell's threads keep taking part in the block's barriers but no longer change their iterate.
+// ON = false compiles every member to nothing (the kernels without a tolerance).
 // s_diff: [3][CPB] bits of each cell's largest change (non-negative doubles order like their
 // bits); sweep r accumulates into row r % 3 and clears row (r + 1) % 3, which was last read two
 // end-of-sweep barriers earlier.
-template <int CPB> struct PicardStop {
+template <int CPB, bool ON> struct PicardStop {
   unsigned long long* s_diff;
   double tol;
   unsigned int done;
   __device__ __forceinline__ void init(unsigned long long* buf, double t, int first_cell, int ncells) {
-    s_diff = buf;
-    tol = t;
     done = 0u;
-    for (int c = 0; c < CPB; ++c)
-      if (first_cell + c >= ncells) done |= 1u << c;  // cells past the mesh never hold a block up
-    for (int j = threadIdx.x; j < 3 * CPB; j += blockDim.x) s_diff[j] = 0ull;
+    if constexpr (ON) {
+      s_diff = buf;
+      tol = t;
+      for (int c = 0; c < CPB; ++c)
+        if (first_cell + c >= ncells) done |= 1u << c;  // cells past the mesh never hold a block up
+      for (int j = threadIdx.x; j < 3 * CPB; j += blockDim.x) s_diff[j] = 0ull;
+    }
   }
-  __device__ __forceinline__ bool on() const { return tol > 0.0; }
-  __device__ __forceinline__ bool frozen(int lc) const { return (done >> lc) & 1u; }
+  __device__ __forceinline__ bool on() const {
+    if constexpr (ON) return tol > 0.0;
+    return false;
+  }
+  __device__ __forceinline__ bool frozen(int lc) const {
+    if constexpr (ON) return (done >> lc) & 1u;
+    return false;
+  }
   __device__ __forceinline__ void begin(int r) {
-    if (on() && threadIdx.x < CPB) s_diff[((r + 1) % 3) * CPB + threadIdx.x] = 0ull;
+    if constexpr (ON)
+      if (threadIdx.x < CPB) s_diff[((r + 1) % 3) * CPB + threadIdx.x] = 0ull;
   }
   __device__ __forceinline__ void record(int r, int lc, double change) {
-    if (on() && !frozen(lc)) atomicMax(&s_diff[(r % 3) * CPB + lc], (unsigned long long)__double_as_longlong(change));
+    if constexpr (ON)
+      if (!frozen(lc)) atomicMax(&s_diff[(r % 3) * CPB + lc], (unsigned long long)__double_as_longlong(change));
   }
   // after sweep r: true once every cell of the block has stopped (block-uniform)
   __device__ __forceinline__ bool end(int r) {
-    if (!on()) return false;
+    if constexpr (!ON) return false;
     __syncthreads();
 #pragma unroll 1
     for (int c = 0; c < CPB; ++c)
@@ -744,12 +764,12 @@ __device__ __forceinline__ void pencil_tasks(const T* sF, T* sR, const Tables& t
 // time operator dt P takes P and its row sums from the kernel parameters and multiplies the
 // derivative by dt once); off: this node's offset inside a combo's region, per direction; cF: this
 // node's cell region (lc * CELL); tb: this thread's task offsets (see pencil_tasks).
-template <class C, class T>
+template <class C, class T, class STOPT>
 __device__ __forceinline__ void picard_pt(T (&q)[C::n][C::V], const T (&Qh)[C::V], T* sbuf, T dtT,
                                           const Tables& tab, const T (&ih)[C::D],
                                           const PP<T>& pp, const int (&off)[C::D], int cF,
                                           const int (&tb)[PencilTasks<C>::NSLOT], int iters,
-                                          PicardStop<C::CPB>& stop, int lc) {
+                                          STOPT& stop, int lc) {
   using Ph = Phys<C::PDE, C::D>;
   using L = PencilTasks<C>;
   constexpr int n = C::n, V = C::V, D = C::D, B = C::CPB * L::CELL;
@@ -988,7 +1008,7 @@ __device__ __forceinline__ void predictor_final_pt(const StepArgs& a, const T (*
 // m < N, q_k = sum_m (xi_k dt)^m / m! d_t^m Q at the time nodes; N derivative evaluations per
 // cell instead of about (N+1)^2 flux slices.  Both end in the same final stage.
 // ------------------------------------------------------------------------------------------------
-template <class C, class T, class TP, class TS, bool CK = false, class TQ = double>
+template <class C, class T, class TP, class TS, bool CK = false, class TQ = double, bool STOP = false>
 __global__ void __launch_bounds__(C::THREADS, PredMinBlocks<C, T, CK>::value) k_predictor(const __grid_constant__ StepArgs a) {
   using Ph = Phys<C::PDE, C::D>;
   constexpr int n = C::n, V = C::V, D = C::D, NS = C::NS, CPB = C::CPB, VX = C::VX;
@@ -996,9 +1016,9 @@ __global__ void __launch_bounds__(C::THREADS, PredMinBlocks<C, T, CK>::value) k_
   constexpr bool kPT = !CK && UsePencilTasks<C, T>::value;  // pencil-task sweeps
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double s_dt;
-  __shared__ unsigned long long s_change[3 * CPB];
+  __shared__ unsigned long long s_change[STOP ? 3 * CPB : 1];
   if (a.sc->bad) return;
-  PicardStop<CPB> stop;
+  PicardStop<CPB, STOP> stop;
   stop.init(s_change, CK ? 0.0 : a.picard_tol, blockIdx.x * CPB, a.ncells);
   const double dt = block_dt(a, D, C::N, &s_dt);
 
@@ -1142,7 +1162,7 @@ __global__ void __launch_bounds__(C::THREADS, PredMinBlocks<C, T, CK>::value) k_
 #pragma unroll
     for (int j = 0; j < L::NSLOT; ++j) tb[j] = L::task_base(j);
     const int cF = lc * L::CELL;
-    picard_pt<C, T>(q, Qh, sbuf, dtT, a.tab, ih, pp, off, cF, tb, a.picard_iters, stop, lc);
+    picard_pt<C, T, PicardStop<CPB, STOP>>(q, Qh, sbuf, dtT, a.tab, ih, pp, off, cF, tb, a.picard_iters, stop, lc);
     __syncthreads();
     if constexpr (UseFinalPt<C>::value)
       predictor_final_pt<C, T, TS, TQ>(a, q, sbuf, pp, ih, dt, lc, i, cell, valid, off, cF, tb);
@@ -1659,21 +1679,37 @@ __global__ void k_l2_final(const double* partial, int nblocks, double* out) {
 // ------------------------------------------------------------------------------------------------
 // launchers
 // ------------------------------------------------------------------------------------------------
-template <class C, class T, class TP, class TS, bool CK = false, class TQ = double>
-cudaError_t launch_predictor(const StepArgs& a, cudaStream_t s) {
+// The kernel with the Picard stopping tolerance is a separate instantiation (STOP), built for the
+// FP64 and FP32 Picard predictors with FP64 storage, so that the kernels without one carry none
+// of its state.
+template <class C, class T, class TP, class TS, bool CK, class TQ> struct HasStopKernel {
+  static constexpr bool value = !CK && std::is_same<TQ, double>::value &&
+                                (std::is_same<T, double>::value || std::is_same<T, float>::value);
+};
+
+template <class C, class T, class TP, class TS, bool CK = false, class TQ = double, bool STOP = false>
+cudaError_t launch_predictor_variant(const StepArgs& a, cudaStream_t s) {
   constexpr bool kPT = !CK && UsePencilTasks<C, T>::value;
   static_assert(PredSmem<C, T, TP, kPT>::total <= 227 * 1024, "predictor shared memory above the per-block limit");
   const size_t smem = PredSmem<C, T, TP, kPT>::total;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_predictor<C, T, TP, TS, CK, TQ>,
+    cudaError_t e = cudaFuncSetAttribute(k_predictor<C, T, TP, TS, CK, TQ, STOP>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   const int blocks = (a.ncells + C::CPB - 1) / C::CPB;
-  k_predictor<C, T, TP, TS, CK, TQ><<<blocks, C::THREADS, smem, s>>>(a);
+  k_predictor<C, T, TP, TS, CK, TQ, STOP><<<blocks, C::THREADS, smem, s>>>(a);
   return cudaGetLastError();
+}
+
+template <class C, class T, class TP, class TS, bool CK = false, class TQ = double>
+cudaError_t launch_predictor(const StepArgs& a, cudaStream_t s) {
+  if constexpr (HasStopKernel<C, T, TP, TS, CK, TQ>::value) {
+    if (a.picard_tol > 0.0) return launch_predictor_variant<C, T, TP, TS, CK, TQ, true>(a, s);
+  }
+  return launch_predictor_variant<C, T, TP, TS, CK, TQ, false>(a, s);
 }
 
 template <class C, class TR, class TC, class TS, class TQ = double>
