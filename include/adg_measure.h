@@ -29,6 +29,16 @@ extern "C" {
  * the stream.  ADG_ECUDA on a CUDA error. */
 ADG_API int adg_measure_fma_peak(int prec, int repeats, void* cuda_stream, double* tflops, double* ms_best);
 
+/* Self-check of the conversions the FP32 kernels make by integer operations instead of the FP64
+ * unit (binary64 -> binary32 round to nearest with ties to even, binary32 -> binary64, and the
+ * finiteness test of a binary64): each of `count` values (>= 1) is compared bit for bit with the
+ * hardware conversion (__double2float_rn, the float -> double conversion, isfinite).  The values
+ * are seeded patterns (a counter-based hash of seed and index): a quarter uniform 64-bit
+ * patterns, a quarter with exponents around the FP32 range, a quarter exact ties, a quarter next
+ * to ties and with all-ones significands (carries into the exponent).  *mismatches (host) gets
+ * the number of differing results.  Allocates 8 bytes of device memory; waits for the stream. */
+ADG_API int adg_check_conversions(long long count, unsigned long long seed, void* cuda_stream, long long* mismatches);
+
 #ifdef __cplusplus
 }
 #endif

@@ -66,6 +66,7 @@ _SIGS = {
     "adg_misfit": [_P, C.c_int, _dp, C.c_int, _dp, _dp, _dp, _P, C.c_size_t],
     "adg_adjoint": [_P, C.c_int, C.c_int, _dp, C.c_int, _dp, _dp, _P, _P, _P, C.c_size_t],
     "adg_measure_fma_peak": [C.c_int, C.c_int, _P, _dp, _dp],
+    "adg_check_conversions": [C.c_longlong, C.c_ulonglong, _P, C.POINTER(C.c_longlong)],
     "adg_step_noalloc": [C.c_int, C.c_int, C.c_int, _ip, _dp, _dp, _dp, C.c_int, C.c_double, C.c_int,
                          _P, C.c_int, _dp, _dp, _P],
 }

@@ -326,6 +326,20 @@ static void* storage_ptr(const adg_ctx* c) {
   if (c->prec[ADG_K_STORAGE] == P64 || !c->ws) return nullptr;
   return (char*)c->ws + align256(traces_bytes(c)) + align256(l2_partial_bytes(c));
 }
+// FP32 predictor and corrector with FP64 storage: the predictor's volume term goes through an FP32
+// buffer, and the corrector accumulates dt (vol - surf) into the FP64 state once per DOF
+static bool uses_volbuf(const adg_ctx* c) {
+  return c->prec[ADG_K_PREDICTOR] == P32 && c->prec[ADG_K_CORRECTOR] == P32 && c->prec[ADG_K_STORAGE] == P64 &&
+         c->refine == 0;
+}
+static size_t volbuf_bytes(const adg_ctx* c) {
+  return uses_volbuf(c) ? (size_t)c->ncells * c->V * c->NS * sizeof(float) : 0;
+}
+static float* volbuf_ptr(const adg_ctx* c) {
+  if (!uses_volbuf(c) || !c->ws) return nullptr;
+  return reinterpret_cast<float*>((char*)c->ws + align256(traces_bytes(c)) + align256(l2_partial_bytes(c)) +
+                                  align256(storage_bytes(c)));
+}
 
 // FP64 state -> storage format (and the FP64 copy rounded), or storage -> FP64 copy
 static cudaError_t storage_sync(const adg_ctx* c, bool in) {
@@ -353,6 +367,7 @@ static void fill_step_args(const adg_ctx* c, StepArgs* a) {
   a->Q = c->Q;
   a->Qs = storage_ptr(c);
   a->traces = c->ws;
+  a->volbuf = volbuf_ptr(c);
   a->sc = c->sc;
   for (int d = 0; d < 3; ++d) {
     a->m[d] = c->m[d];
@@ -494,7 +509,7 @@ int adg_set_kernel_precision(adg_ctx* c, int kernel, int prec, int flags) {
     return fail(c, ADG_EUNSUPPORTED, "the predictor's final stage runs in FP64, FP32 or bf16");
   if ((kernel == ADG_K_RIEMANN || kernel == ADG_K_CORRECTOR) && prec == ADG_FP16)
     return fail(c, ADG_EUNSUPPORTED, "fp16 Riemann/corrector not built");
-  if ((kernel == ADG_K_CORRECTOR || kernel == ADG_K_STORAGE) && prec != c->prec[kernel])
+  if ((kernel == ADG_K_PREDICTOR || kernel == ADG_K_CORRECTOR || kernel == ADG_K_STORAGE) && prec != c->prec[kernel])
     c->have_bufs = false;  // the workspace size changes
   c->prec[kernel] = prec;
   if (kernel == ADG_K_PICARD) c->flags = flags;
@@ -516,6 +531,7 @@ int adg_set_numerics(adg_ctx* c, double cfl, int picard_iters, double picard_tol
 int adg_set_refinement(adg_ctx* c, int fp64_sweeps) {
   if (!c) return ADG_EINVAL;
   if (fp64_sweeps < 0 || fp64_sweeps > 1000) return fail(c, ADG_EINVAL, "fp64_sweeps must be in [0, 1000]");
+  if ((fp64_sweeps > 0) != (c->refine > 0)) c->have_bufs = false;  // the workspace size can change
   c->refine = fp64_sweeps;
   return ADG_OK;
 }
@@ -538,7 +554,8 @@ int adg_state_size(const adg_ctx* c, size_t* ndouble, int* nvar) {
 int adg_workspace_bytes(const adg_ctx* c, size_t* bytes) {
   if (!c || !bytes) return ADG_EINVAL;
   if (!c->have_mesh || !c->have_pde) return ADG_ENOTINIT;
-  *bytes = align256(traces_bytes(c)) + align256(l2_partial_bytes(c)) + align256(storage_bytes(c));
+  *bytes = align256(traces_bytes(c)) + align256(l2_partial_bytes(c)) + align256(storage_bytes(c)) +
+           align256(volbuf_bytes(c));
   return ADG_OK;
 }
 

@@ -66,6 +66,10 @@ struct StepArgs {
   double* Q;          // state [cells][V][NS]
   void* Qs;           // the state in the storage precision when it is not FP64 (else null)
   void* traces;       // [cells][D][2 sides][2 (Qbar, Fbar.n)][V][NF] in the corrector precision
+  // FP32 predictor and corrector with FP64 storage: the predictor stores its volume term here
+  // ([cells][V][NS]) instead of adding it to Q, and the corrector adds dt (vol - surf), formed in
+  // FP32, to Q in one FP64 operation per DOF (null: each kernel updates Q itself)
+  float* volbuf;
   DevScalars* sc;
   int m[3];
   int ncells;

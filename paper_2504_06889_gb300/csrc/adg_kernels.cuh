@@ -462,6 +462,8 @@ __device__ __forceinline__ void predictor_final(const StepArgs& a, const T (*q)[
       if constexpr (std::is_same<TQ, double>::value) {
         if constexpr (NG > 0)
           Qw[v * NS + i] = (Qw[v * NS + i] + dt * conv<double>(vol)) - dt * conv<double>(nc[v]);
+        else if (a.volbuf)  // the corrector adds dt (vol - surf)
+          a.volbuf[(size_t)cell * V * NS + v * NS + i] = conv<float>(vol);
         else
           Qw[v * NS + i] += dt * conv<double>(vol);
       } else {
@@ -990,8 +992,12 @@ __device__ __forceinline__ void predictor_final_pt(const StepArgs& a, const T (*
       for (int d = 0; d < D; ++d)
         if (Ph::nz(d, v)) vol = fmaf(ih[d], sVo[cF + L::cidx(d, v) * L::CS + off[d]], vol);
       if constexpr (std::is_same<TQ, double>::value) {
-        double* Qw = a.Q + (size_t)cell * V * NS;
-        Qw[v * NS + i] += dt * (double)vol;
+        if (a.volbuf) {  // the corrector adds dt (vol - surf)
+          a.volbuf[(size_t)cell * V * NS + v * NS + i] = vol;
+        } else {
+          double* Qw = a.Q + (size_t)cell * V * NS;
+          Qw[v * NS + i] += dt * (double)vol;
+        }
       } else {
         TQ* Qsw = static_cast<TQ*>(a.Qs) + (size_t)cell * V * NS;
         const double qv = store_widen(Qsw[v * NS + i]) + dt * (double)vol;
@@ -1085,7 +1091,12 @@ __global__ void __launch_bounds__(C::THREADS, PredMinBlocks<C, T, CK>::value) k_
   if constexpr (std::is_same<TQ, double>::value) {
     const double* Qc = a.Q + (size_t)cl * V * NS;
 #pragma unroll
-    for (int v = 0; v < V; ++v) Qh[v] = conv<T>(Qc[v * NS + i]);
+    for (int v = 0; v < V; ++v) {
+      if constexpr (std::is_same<T, float>::value)
+        Qh[v] = f64_to_f32_rn(Qc[v * NS + i]);
+      else
+        Qh[v] = conv<T>(Qc[v * NS + i]);
+    }
   } else {
     const TQ* Qc = static_cast<const TQ*>(a.Qs) + (size_t)cl * V * NS;
 #pragma unroll
@@ -1355,11 +1366,21 @@ __global__ void __launch_bounds__(C::THREADS) k_corrector(const __grid_constant_
         surf += sCoef[(D + dir) * n + id] * gp - sCoef[dir * n + id] * gm;
       }
       if constexpr (std::is_same<TQ, double>::value) {
-        const double qv = Qw[v * NS + i] - dt * todouble(surf);
+        double qv;
+        if constexpr (std::is_same<TC, float>::value) {
+          if (a.volbuf) {  // Q + dt (vol - surf): the difference in FP32, one FP64 operation
+            const float inc = a.volbuf[(size_t)cell * V * NS + v * NS + i] - surf;
+            qv = fma(dt, f32_to_f64(inc), Qw[v * NS + i]);
+          } else {
+            qv = Qw[v * NS + i] - dt * f32_to_f64(surf);
+          }
+        } else {
+          qv = Qw[v * NS + i] - dt * todouble(surf);
+        }
         Qw[v * NS + i] = qv;
         qnew_keep[v] = qv;
-        qf[v] = (float)qv;
-        bad |= !isfinite(qv);
+        qf[v] = f64_to_f32_rn(qv);
+        bad |= !f64_is_finite(qv);
       } else {
         // stored in the storage format; the next dt follows the stored values (their FP32
         // copy is exact, the FP64 one is made only for the lambda candidates below)

@@ -4,6 +4,8 @@
 
 #include <cuda_runtime.h>
 
+#include "adg_physics.cuh"
+
 namespace adg {
 namespace {
 
@@ -85,8 +87,68 @@ int measure(int repeats, cudaStream_t st, int iters, double* tflops, double* ms_
   return ADG_OK;
 }
 
+// splitmix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number generators", OOPSLA
+// 2014): the value of a counter under a seed
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__global__ void k_check_conversions(long long count, unsigned long long seed, unsigned long long* bad) {
+  unsigned long long local = 0;
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < count;
+       j += (long long)gridDim.x * blockDim.x) {
+    const unsigned long long h = mix64(seed ^ mix64((unsigned long long)j));
+    unsigned long long b = h;
+    const int kind = (int)(j & 3);
+    if (kind > 0) {
+      // exponent within 140 of the FP32 range's centre, random sign and significand
+      const unsigned long long e = 1023ull - 140ull + (mix64(h) % 281ull);
+      b = (h & 0x800FFFFFFFFFFFFFull) | (e << 52);
+      if (kind == 2) b = (b & ~0x1FFFFFFFull) | 0x10000000ull;  // exactly half way
+      if (kind == 3) {
+        const unsigned long long low[4] = {0x0FFFFFFFull, 0x10000001ull, 0x1FFFFFFFull, 0x0ull};
+        b = (b & ~0x1FFFFFFFull) | low[(h >> 7) & 3];
+        if ((h >> 9) & 1) b |= 0x000FFFFFE0000000ull;  // all-ones kept significand: carries
+      }
+    }
+    const double x = __longlong_as_double((long long)b);
+    const float f = f64_to_f32_rn(x), g = __double2float_rn(x);
+    const bool both_nan = (f != f) && (g != g);
+    if (!both_nan && __float_as_uint(f) != __float_as_uint(g)) ++local;
+    if (f64_is_finite(x) != (bool)isfinite(x)) ++local;
+    const float y = __uint_as_float((unsigned)(h >> 32));
+    const double d1 = f32_to_f64(y), d2 = (double)y;
+    const bool both_nan2 = (d1 != d1) && (d2 != d2);
+    if (!both_nan2 && __double_as_longlong(d1) != __double_as_longlong(d2)) ++local;
+  }
+  if (local) atomicAdd(bad, local);
+}
+
 }  // namespace
 }  // namespace adg
+
+extern "C" int adg_check_conversions(long long count, unsigned long long seed, void* cuda_stream,
+                                     long long* mismatches) {
+  if (count < 1 || !mismatches) return ADG_EINVAL;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  unsigned long long* d = nullptr;
+  if (cudaMalloc(&d, sizeof(*d)) != cudaSuccess) return ADG_ECUDA;
+  unsigned long long h = 0;
+  int rc = ADG_OK;
+  if (cudaMemsetAsync(d, 0, sizeof(*d), st) != cudaSuccess) rc = ADG_ECUDA;
+  if (rc == ADG_OK) {
+    adg::k_check_conversions<<<152 * 8, 256, 0, st>>>(count, seed, d);
+    if (cudaGetLastError() != cudaSuccess) rc = ADG_ECUDA;
+  }
+  if (rc == ADG_OK && cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess) rc = ADG_ECUDA;
+  if (rc == ADG_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = ADG_ECUDA;
+  cudaFree(d);
+  if (rc == ADG_OK) *mismatches = (long long)h;
+  return rc;
+}
 
 extern "C" int adg_measure_fma_peak(int prec, int repeats, void* cuda_stream, double* tflops, double* ms_best) {
   if (!tflops || repeats < 1 || repeats > 100) return ADG_EINVAL;

@@ -45,6 +45,37 @@ __device__ __forceinline__ __nv_bfloat16 conv<__nv_bfloat16, __nv_bfloat16>(__nv
   return x;
 }
 
+// Conversions between FP64 and FP32 by integer operations.  On this part the FP64 unit, which also
+// converts, retires about 1/64 of the FP32 rate, so the hot kernels avoid it.  Both follow the
+// IEEE 754 definitions (binary64 -> binary32 round to nearest, ties to even; binary32 -> binary64
+// exact); zeros, subnormals, non-finite values and results outside the normal FP32 range take the
+// hardware conversion.
+__device__ __forceinline__ float f64_to_f32_rn(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32);
+  const int e = (int)((hi >> 20) & 0x7FFu) - 1023;
+  if (e < -126 || e > 127) return __double2float_rn(x);
+  const unsigned m = (unsigned)((b >> 29) & 0x7FFFFFull);  // the 23 kept significand bits
+  const unsigned rest = (unsigned)(b & 0x1FFFFFFFull);      // the 29 dropped ones
+  unsigned r = ((unsigned)(e + 127) << 23) | m;
+  // round up above the half-way point, or at it when the kept part is odd; a carry out of the
+  // significand steps the exponent, which is the rounded value (2^128 becomes infinity)
+  r += (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ? 1u : 0u;
+  return __uint_as_float((hi & 0x80000000u) | r);
+}
+__device__ __forceinline__ double f32_to_f64(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned e = (u >> 23) & 0xFFu;
+  if (e == 0u || e == 0xFFu) return (double)x;
+  const unsigned long long b = ((unsigned long long)(u >> 31) << 63) | ((unsigned long long)(e + 896u) << 52) |
+                               ((unsigned long long)(u & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)b);
+}
+// x is finite (not an infinity or a NaN): the exponent field is not all ones
+__device__ __forceinline__ bool f64_is_finite(double x) {
+  return ((unsigned)((unsigned long long)__double_as_longlong(x) >> 52) & 0x7FFu) != 0x7FFu;
+}
+
 template <class T> __device__ __forceinline__ T tsqrt(T x) { return sqrt(x); }
 template <> __device__ __forceinline__ float tsqrt<float>(float x) { return sqrtf(x); }
 template <> __device__ __forceinline__ __nv_bfloat16 tsqrt<__nv_bfloat16>(__nv_bfloat16 x) {

@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(TcCfg<C, TIN>::THREADS)
   T Qh[V];
   const double* Qc = a.Q + (size_t)cl * V * NS;
 #pragma unroll
-  for (int v = 0; v < V; ++v) Qh[v] = owner ? (T)Qc[v * NS + (owner ? i : 0)] : T(0);
+  for (int v = 0; v < V; ++v) Qh[v] = owner ? f64_to_f32_rn(Qc[v * NS + (owner ? i : 0)]) : T(0);
 
   // scale of the first sweep: all time nodes start at Q, so F(q_k) = F(Q)
   auto fmax_of = [&](const T (*F)[V]) {

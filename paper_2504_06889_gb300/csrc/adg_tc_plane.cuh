@@ -63,10 +63,12 @@ template <class C> struct TpCfg {
   static constexpr int R_OFF = (A_BYTES + 127) / 128 * 128;
   static constexpr int R_BYTES = NP * PS * 4;
   static constexpr int LOW_END = R_OFF + R_BYTES;       // A_xy + R_s (the final stage reuses it)
-  // B_z: MN-major; position groups LBO_Z apart, 8-row K groups SBO_Z apart
-  static constexpr int LBO_Z = 144;
-  static constexpr int SBO_Z = (NCOL / 8) * LBO_Z;
-  static constexpr int Z_TILE = (KZ / 8) * SBO_Z;
+  // B_z: MN-major; groups of 8 plane positions NG_Z apart, 8-row K groups KG_Z apart.  For an
+  // MN-major operand without swizzle the descriptor's leading byte offset is the K-group stride and
+  // its stride byte offset the MN-group stride (measured on this part)
+  static constexpr int NG_Z = 144;
+  static constexpr int KG_Z = (NCOL / 8) * NG_Z;
+  static constexpr int Z_TILE = (KZ / 8) * KG_Z;
   static constexpr int BZ_OFF = (LOW_END + 127) / 128 * 128;
   // B_xy hi and lo: K-major, core LBO 128, SBO (KXY / 8) * 128
   static constexpr int BXY_BYTES = NCOL * KXY * 2;
@@ -95,7 +97,7 @@ template <class G> __device__ __forceinline__ int aoff(int r, int c) {
 }
 // B_z byte offset of (K row kr, plane position p) in a tile (MN-major)
 template <class G> __device__ __forceinline__ int zoff(int kr, int p) {
-  return (kr >> 3) * G::SBO_Z + (kr & 7) * 16 + (p >> 3) * G::LBO_Z + (p & 7) * 2;
+  return (kr >> 3) * G::KG_Z + (kr & 7) * 16 + (p >> 3) * G::NG_Z + (p & 7) * 2;
 }
 // B_xy byte offset of (output position p, column c)
 template <class G> __device__ __forceinline__ int boff(int p, int c) {
@@ -259,7 +261,7 @@ __global__ void __launch_bounds__(TpCfg<C>::THREADS, 2) k_predictor_tcp(const __
 #pragma unroll
       for (int v = 0; v < V; ++v) {
         const double x = Qc[v * NS + i];
-        Qh[v] = (float)x;
+        Qh[v] = f64_to_f32_rn(x);
         if constexpr (F64) Q64[v] = x;
       }
     }
@@ -342,7 +344,7 @@ __global__ void __launch_bounds__(TpCfg<C>::THREADS, 2) k_predictor_tcp(const __
             const int kz = first ? 2 : (tile == TILES - 1 ? G::KZ_LAST / 16 : G::KZ / 16);
 #pragma unroll 1
             for (int ks = 0; ks < kz; ++ks) {
-              const uint64_t zd = tc::sdesc(zb + (uint32_t)(ks * 2 * G::SBO_Z), G::LBO_Z, G::SBO_Z);
+              const uint64_t zd = tc::sdesc(zb + (uint32_t)(ks * 2 * G::KG_Z), G::KG_Z, G::NG_Z);
               tcp::mma_ts(d, tmem + (uint32_t)(G::AZ_HI + ks * 8), zd, idesc_z, 1u);
               if (comp && pass == 0) tcp::mma_ts(d, tmem + (uint32_t)(G::AZ_LO + ks * 8), zd, idesc_z, 1u);
             }

@@ -292,7 +292,7 @@ __global__ void __launch_bounds__(TsCfg<C>::THREADS, TsCfg<C>::THREADS > 128 ? 2
     {
       const double* Qc = a.Q + (size_t)cell * V * NS;
 #pragma unroll
-      for (int v = 0; v < V; ++v) Qh[v] = (float)Qc[v * NS + i];
+      for (int v = 0; v < V; ++v) Qh[v] = f64_to_f32_rn(Qc[v * NS + i]);
     }
     if (tid == 0) {
       float F[3][V];
