@@ -57,7 +57,7 @@ MIXES = {
     # E4M3 inputs (kind::f8f6f4, K = 32 per instruction: four pencils per accumulator row)
     "fp8tc": {"picard": "fp8", "predictor": "fp32", "riemann": "fp32", "corrector": "fp32"},
 }
-# bf16 tensor-core sweeps (flux offset, compensated last sweep) with the final stage, the Riemann
+# bf16 tensor-core sweeps (flux offset, last two sweeps compensated) with the final stage, the Riemann
 # solver and the corrector in FP64
 MIXES["bf16tc64"] = {"picard": "bf16", "predictor": "fp64", "riemann": "fp64", "corrector": "fp64"}
 # Cauchy-Kowalevskaya predictor (linear PDEs) in place of the Picard sweeps
@@ -69,7 +69,7 @@ MIX_SCHEME = {"fp64ck": "ck", "fp32ck": "ck"}
 for _k in ("fp64", "fp32"):
     for _s, _n in (("fp32", "32"), ("fp16", "16"), ("bf16", "bf16")):
         MIXES[f"{_k}s{_n}"] = dict(MIXES[_k], storage=_s)
-MIX_FLAGS = {"bf16tc": 1 | 2, "fp16tc": 1 | 2, "fp8tc": 1 | 2, "bf16tc64": 1}
+MIX_FLAGS = {"bf16tc": 1 | 2, "fp16tc": 1 | 2, "fp8tc": 1 | 2, "bf16tc64": 4}
 # iterative refinement: the first Picard sweeps in FP32 (or bf16) arithmetic, the last k sweeps,
 # the final stage, the Riemann solver and the corrector in FP64
 MIX_REFINE = {}

@@ -460,10 +460,10 @@ __device__ __forceinline__ void predictor_final(const StepArgs& a, const T (*q)[
         vol += s * ihp[dir];
       }
       if constexpr (std::is_same<TQ, double>::value) {
-        if constexpr (NG > 0)
+        if (a.volbuf)  // the corrector adds dt (vol - surf) (vol with the non-conservative term)
+          a.volbuf[(size_t)cell * V * NS + v * NS + i] = conv<float>(NG > 0 ? vol - nc[v] : vol);
+        else if constexpr (NG > 0)
           Qw[v * NS + i] = (Qw[v * NS + i] + dt * conv<double>(vol)) - dt * conv<double>(nc[v]);
-        else if (a.volbuf)  // the corrector adds dt (vol - surf)
-          a.volbuf[(size_t)cell * V * NS + v * NS + i] = conv<float>(vol);
         else
           Qw[v * NS + i] += dt * conv<double>(vol);
       } else {
@@ -893,12 +893,13 @@ __device__ __forceinline__ void final_task(const T* f, T* o, const Tables& tab, 
 // direction), and each Qbar pencil times psi(0), psi(1) (its traces); the nodes add dt times the
 // volume integral to Q in FP64.  The Fbar tasks are the sweeps' (tb); the Qbar tasks are numbered
 // by face node, so their trace stores are contiguous.  sbuf: the pencil-task regions (Fbar in
-// the first, Qbar [cell][v][node] in the second, Vm Fbar in the third).
+// the first, Qbar [cell][v][node] in the second, Vm Fbar in the third); cell0: the mesh cell of
+// the block's first cell slot (lc = 0).
 template <class C, class T, class TS, class TQ>
 __device__ __forceinline__ void predictor_final_pt(const StepArgs& a, const T (*q)[C::V], T* sbuf, const PP<T>& pp,
                                                    const T (&ih)[C::D], double dt, int lc, int i, int cell,
                                                    bool valid, const int (&off)[C::D], int cF,
-                                                   const int (&tb)[PencilTasks<C>::NSLOT]) {
+                                                   const int (&tb)[PencilTasks<C>::NSLOT], int cell0) {
   using Ph = Phys<C::PDE, C::D>;
   using L = PencilTasks<C>;
   constexpr int n = C::n, V = C::V, D = C::D, NS = C::NS, NF = C::NF, B = C::CPB * L::CELL;
@@ -945,7 +946,7 @@ __device__ __forceinline__ void predictor_final_pt(const StepArgs& a, const T (*
       final_task<n, 1>(sFb + tb[j], sVo + tb[j], a.tab, &s0, &s1);
     else
       final_task<n, L::MS>(sFb + tb[j], sVo + tb[j], a.tab, &s0, &s1);
-    const int tcell = blockIdx.x * C::CPB + tcl;
+    const int tcell = cell0 + tcl;
     if (tcell < a.ncells) {
       int d = 0, v = 0;
       L::combo_dv(c, &d, &v);
@@ -962,7 +963,7 @@ __device__ __forceinline__ void predictor_final_pt(const StepArgs& a, const T (*
     if (t >= NQ) break;
     const int tcl = t / (D * V * NF), r = t - tcl * (D * V * NF);
     const int d = r / (V * NF), v = (r / NF) % V, jf = r % NF;
-    const int tcell = blockIdx.x * C::CPB + tcl;
+    const int tcell = cell0 + tcl;
     if (tcell >= a.ncells) continue;
     const T* qb = sQb + tcl * L::CELL + v * NS;
     T s0 = T(0), s1 = T(0);
@@ -1176,7 +1177,7 @@ __global__ void __launch_bounds__(C::THREADS, PredMinBlocks<C, T, CK>::value) k_
     picard_pt<C, T, PicardStop<CPB, STOP>>(q, Qh, sbuf, dtT, a.tab, ih, pp, off, cF, tb, a.picard_iters, stop, lc);
     __syncthreads();
     if constexpr (UseFinalPt<C>::value)
-      predictor_final_pt<C, T, TS, TQ>(a, q, sbuf, pp, ih, dt, lc, i, cell, valid, off, cF, tb);
+      predictor_final_pt<C, T, TS, TQ>(a, q, sbuf, pp, ih, dt, lc, i, cell, valid, off, cF, tb, blockIdx.x * CPB);
     else
       predictor_final<C, T, TP, TS, TQ>(a, q, reinterpret_cast<TP*>(smem_raw), sVm, sw, sp0, sp1, dt, lc, i,
                                         cell, valid, cl, idx, pb);

@@ -429,7 +429,7 @@ __global__ void __launch_bounds__(TpCfg<C>::THREADS, 2) k_predictor_tcp(const __
       }
     } else {
       predictor_final_pt<C, float, TS, double>(a, q, reinterpret_cast<float*>(tp_smem), pp, ih, dt, 0, i, cell,
-                                               true, off, 0, tb);
+                                               true, off, 0, tb, cell);
     }
   }  // cells
   tc::fence_before();

@@ -286,35 +286,43 @@ def test_nonfinite_state_is_reported_and_time_stops(adg, oracle_mod):
 
 # ---- full size, in the benchmark's launch configuration: sampled cells ----------------------------
 
+P64 = {"picard": "fp64", "predictor": "fp64"}
+P32 = {"picard": "fp32", "predictor": "fp32"}
+# the benchmark's headline mix: every kernel outside the FP64 state, accumulation and CFL in FP32
+ALL32 = {"picard": "fp32", "predictor": "fp32", "riemann": "fp32", "corrector": "fp32"}
+# bf16 tensor-core sweeps (two compensated), FP32 final stage, Riemann and corrector
+TC16 = {"picard": "bf16", "predictor": "fp32", "riemann": "fp32", "corrector": "fp32"}
 FULL = [
-    (I.euler3d_wave(), [("fp64", 1e-12), ("fp32", 1e-5)]),
-    (I.elastic3d_planar(), [("fp32", 1e-5)]),
-    (I.swe2d_modes(), [("fp64", 1e-12), ("fp32", 1e-5)]),
-    (I.acoustic3d_pulse(), [("fp64", 1e-12)]),
+    (I.euler3d_wave(), [("fp64", P64, 0, 1e-12), ("fp32", P32, 0, 1e-5), ("fp32 all", ALL32, 0, 1e-5),
+                        ("bf16tc", TC16, 4, 1e-5)]),
+    (I.elastic3d_planar(), [("fp32", P32, 0, 1e-5), ("fp32 all", ALL32, 0, 1e-5)]),
+    (I.swe2d_modes(), [("fp64", P64, 0, 1e-12), ("fp32", P32, 0, 1e-5), ("fp32 all", ALL32, 0, 1e-5)]),
+    (I.acoustic3d_pulse(), [("fp64", P64, 0, 1e-12)]),
 ]
 
 
 @pytest.mark.parametrize("wl,precs", FULL, ids=[w.name for w, _ in FULL])
 def test_full_size_sampled_cells_match_oracle(adg, oracle_mod, wl, precs):
+    """One step at the benchmark's full size and launch configuration; 16 sampled cells (the first,
+    the last and 14 seeded ones) against the oracle's step of those cells."""
     M = oracle_mod.Mesh(wl.dim, wl.N, wl.cells, wl.pde, wl.params, cfl=wl.cfl)
     Q0 = M.interpolate(wl.scenario, wl.sp)
     dt = M.dt(Q0)
     rng = np.random.default_rng(11)
     ids = np.unique(np.concatenate([[0, M.ncells - 1], rng.integers(0, M.ncells, size=14)]))
     ref = M.step_cells(Q0, dt, ids)
-    for prec, tol in precs:
-        s = adg.Solver(wl.dim, wl.N, wl.cells, wl.pde, wl.params, cfl=wl.cfl,
-                       precision={"picard": prec, "predictor": prec})
+    for name, prec, flags, tol in precs:
+        s = adg.Solver(wl.dim, wl.N, wl.cells, wl.pde, wl.params, cfl=wl.cfl, precision=prec, flags=flags)
         s.set_state(Q0, 0.0)
         t, dtg = s.step(1)
         assert abs(dtg - dt) <= 1e-15 * dt
         Qg = s.Q[torch.from_numpy(ids).cuda()].cpu().numpy()
         for j in range(len(ids)):
             err = np.sqrt(np.sum((Qg[j] - ref[j]) ** 2)) / np.sqrt(np.sum(ref[j] ** 2))
-            if prec == "fp64":
+            if name == "fp64":
                 assert np.abs(Qg[j] - ref[j]).max() <= tol * np.abs(ref[j]).max(), (ids[j], err)
             else:
-                assert err <= tol, (ids[j], err)
+                assert err <= tol, (name, ids[j], err)
         s.close()
         del s
         torch.cuda.empty_cache()

@@ -1,0 +1,139 @@
+"""Accuracy targets of the low-precision mixes at the configurations' orders, on the GPU.
+
+Two targets, both against the analytic solutions (eq. L2gauss):
+  * the bf16 tensor-core predictor (flux offset, compensated sweeps) stays within 2x the FP64
+    path's discretisation error at the order of the configuration: 3D Euler at N = 5 (the
+    benchmark's density wave) and 3D elasticity at N = 6 (one P and one S wave);
+  * every mix's observed convergence order under h-refinement lies within 0.3 of the FP64
+    path's, 3D Euler N = 5, 3D elasticity N = 6 and 3D acoustics N = 4 (plane waves).
+
+The FP64 error must sit above a mix's rounding floor for either statement to hold.  The meshes
+are therefore coarse (2^3 to 6^3 cells at these orders), run for 2 m steps on the m^3 mesh (dt is
+proportional to h, so every run ends near the same time).  Where the FP64 error falls below the
+floor, the mixes stop converging: the floor itself is asserted (below the FP32 tolerance for the
+16-bit mixes, near 1e-4 for E4M3), and the mesh where the 2x target stops holding is checked, so
+that the statement above has its stated range.
+
+Mixes: "bf16" = bf16 tensor-core sweeps with the last two compensated and the final stage, Riemann
+and corrector in FP32 (the north-star mix); "bf16f64" the same sweeps with the final stage,
+Riemann and corrector in FP64; "fp16" = fp16 tensor-core sweeps with per-cell scaling and a
+compensated last sweep; "fp32" = every kernel in FP32.
+"""
+import numpy as np
+import pytest
+
+from paper_2504_06889_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def adg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2504_06889_gb300 import adg as A
+    from paper_2504_06889_gb300 import build
+
+    build.build()
+    A.load()
+    return A
+
+
+def mix_table(adg):
+    f32 = {"predictor": "fp32", "riemann": "fp32", "corrector": "fp32"}
+    f64 = {"predictor": "fp64", "riemann": "fp64", "corrector": "fp64"}
+    two = adg.F_COMPENSATED_TWO | adg.F_PER_CELL_SCALE
+    return {
+        "fp64": (dict(f64, picard="fp64"), 0),
+        "fp32": (dict(f32, picard="fp32"), 0),
+        "bf16": (dict(f32, picard="bf16"), two),
+        "bf16f64": (dict(f64, picard="bf16"), two),
+        "fp16": (dict(f32, picard="fp16"), adg.F_COMPENSATED_LAST | adg.F_PER_CELL_SCALE),
+        "fp8": (dict(f32, picard="fp8"), adg.F_COMPENSATED_LAST | adg.F_PER_CELL_SCALE),
+    }
+
+
+def euler(m):
+    return I.euler3d_wave(m=m, N=5)
+
+
+def elastic(m):
+    return I.elastic3d_planar(m=m, N=6)
+
+
+def acoustic(m):
+    w = I.acoustic_wave((2 * np.pi, -2 * np.pi, 4 * np.pi), 1.0, 1.0)
+    return I.Workload("ac3", 3, 4, (m, m, m), I.ACOUSTIC, (1.0, 1.0), I.SC_PLANAR, I.planar(4, [w]), 2 * m)
+
+
+_cache = {}
+
+
+def error(adg, make, m, mix):
+    key = (make.__name__, m, mix)
+    if key not in _cache:
+        prec, flags = mix_table(adg)[mix]
+        wl = make(m)
+        s = adg.Solver(wl.dim, wl.N, wl.cells, wl.pde, wl.params, cfl=wl.cfl, precision=prec, flags=flags)
+        s.set_initial(wl.scenario, wl.sp)
+        s.step(2 * m)
+        _cache[key] = s.error_vs_exact()[1]
+        s.close()
+    return _cache[key]
+
+
+# ---- bf16 within 2x of the FP64 discretisation error -------------------------------------------
+
+@pytest.mark.parametrize("make,meshes,mixes", [
+    (euler, (2, 3, 4), ("bf16", "bf16f64")),
+    (elastic, (3, 4, 6, 8), ("bf16",)),
+], ids=["euler3d_N5", "elastic3d_N6"])
+def test_bf16_within_twice_the_fp64_error(adg, make, meshes, mixes):
+    for m in meshes:
+        e64 = error(adg, make, m, "fp64")
+        for mix in mixes:
+            e = error(adg, make, m, mix)
+            assert e <= 2.0 * e64, (make.__name__, m, mix, e, e64)
+
+
+def test_bf16_target_range_ends_at_the_rounding_floor(adg):
+    """On finer Euler meshes the FP64 error (3.5e-8 at 8^3) falls below the bf16 mix's floor, which
+    stays below the FP32 tolerance: the 2x target holds only while the FP64 error is above it."""
+    e64 = error(adg, euler, 8, "fp64")
+    e16 = error(adg, euler, 8, "bf16")
+    assert e16 > 2.0 * e64
+    assert e16 < 1e-5
+
+
+# ---- convergence order within 0.3 of the FP64 path -----------------------------------------------
+
+ORDER_CASES = [
+    (euler, (2, 3, 4), ("fp32", "bf16", "bf16f64", "fp16")),
+    (elastic, (3, 4, 6), ("fp32", "bf16", "fp16")),
+    (acoustic, (2, 3, 4), ("fp32", "fp16")),
+]
+
+
+def orders(adg, make, meshes, mix):
+    e = np.array([error(adg, make, m, mix) for m in meshes])
+    h = 1.0 / np.array(meshes, dtype=float)
+    return e, np.log(e[:-1] / e[1:]) / np.log(h[:-1] / h[1:])
+
+
+@pytest.mark.parametrize("make,meshes,mixes", ORDER_CASES, ids=["euler3d_N5", "elastic3d_N6", "acoustic3d_N4"])
+def test_order_within_0_3_of_fp64(adg, make, meshes, mixes):
+    e64, o64 = orders(adg, make, meshes, "fp64")
+    N = make(2).N
+    # the FP64 path converges at about N + 1 on these meshes
+    assert np.all(o64 > N + 1 - 1.0), (e64, o64)
+    for mix in mixes:
+        e, o = orders(adg, make, meshes, mix)
+        assert np.all(np.abs(o - o64) <= 0.3), (make.__name__, mix, e, o, o64)
+
+
+def test_e4m3_stops_at_its_floor(adg):
+    """E4M3 keeps three mantissa bits: on the Euler wave its error stays near 1e-4 from 3^3 on,
+    so it has no convergence order to compare at N = 5 (the floor is the statement)."""
+    e = [error(adg, euler, m, "fp8") for m in (3, 4)]
+    assert all(1e-5 < x < 1e-3 for x in e), e
