@@ -45,53 +45,31 @@ __device__ __forceinline__ __nv_bfloat16 conv<__nv_bfloat16, __nv_bfloat16>(__nv
   return x;
 }
 
-// Conversions between FP64 and FP32 by integer operations only.  On this part the FP64 unit, which
-// also converts, retires about 1/64 of the FP32 rate, so the hot kernels avoid it.  Both follow the
-// IEEE 754 definitions: binary64 -> binary32 rounds to nearest with ties to even (including
-// results that are subnormal, zero or overflow to infinity), binary32 -> binary64 is exact
-// (subnormal inputs are normalised); infinities stay infinities and NaNs stay NaNs.
+// Conversions between FP64 and FP32 by integer operations.  On this part the FP64 unit, which also
+// converts, retires about 1/64 of the FP32 rate, so the hot kernels avoid it.  Both follow the
+// IEEE 754 definitions (binary64 -> binary32 round to nearest, ties to even; binary32 -> binary64
+// exact); zeros, subnormals, non-finite values and results outside the normal FP32 range take the
+// hardware conversion.
 __device__ __forceinline__ float f64_to_f32_rn(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned hi = (unsigned)(b >> 32), sign = hi & 0x80000000u;
-  const int e64 = (int)((hi >> 20) & 0x7FFu);
-  const unsigned long long frac = b & 0xFFFFFFFFFFFFFull;  // 52 bits
-  if (e64 == 0x7FF) return __uint_as_float(sign | 0x7F800000u | (frac ? 0x00400000u : 0u));
-  const int e = e64 - 1023;
-  if (e > 127) return __uint_as_float(sign | 0x7F800000u);
-  if (e >= -126) {
-    const unsigned m = (unsigned)(frac >> 29);              // the 23 kept significand bits
-    const unsigned rest = (unsigned)(frac & 0x1FFFFFFFull);  // the 29 dropped ones
-    unsigned r = ((unsigned)(e + 127) << 23) | m;
-    // round up above the half-way point, or at it when the kept part is odd; a carry out of the
-    // significand steps the exponent, which is the rounded value (2^128 becomes infinity)
-    r += (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ? 1u : 0u;
-    return __uint_as_float(sign | r);
-  }
-  // below the normal range: the result is a multiple of 2^-149.  x = sig 2^(e - 52), so
-  // x / 2^-149 = sig 2^-(s) with s = -e - 97 >= 30
-  if (e64 == 0) return __uint_as_float(sign);  // a binary64 subnormal is far below 2^-150
-  const int s = -e - 97;
-  if (s >= 54) return __uint_as_float(sign);  // below half the smallest subnormal
-  const unsigned long long sig = frac | (1ull << 52);
-  const unsigned long long q = sig >> s, rem = sig & ((1ull << s) - 1ull), half = 1ull << (s - 1);
-  const unsigned long long r = q + ((rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull);
-  return __uint_as_float(sign | (unsigned)r);  // 2^23 here is the smallest normal, as it should be
+  const unsigned hi = (unsigned)(b >> 32);
+  const int e = (int)((hi >> 20) & 0x7FFu) - 1023;
+  if (e < -126 || e > 127) return __double2float_rn(x);
+  const unsigned m = (unsigned)((b >> 29) & 0x7FFFFFull);  // the 23 kept significand bits
+  const unsigned rest = (unsigned)(b & 0x1FFFFFFFull);      // the 29 dropped ones
+  unsigned r = ((unsigned)(e + 127) << 23) | m;
+  // round up above the half-way point, or at it when the kept part is odd; a carry out of the
+  // significand steps the exponent, which is the rounded value (2^128 becomes infinity)
+  r += (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ? 1u : 0u;
+  return __uint_as_float((hi & 0x80000000u) | r);
 }
 __device__ __forceinline__ double f32_to_f64(float x) {
   const unsigned u = __float_as_uint(x);
-  const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
-  const unsigned e = (u >> 23) & 0xFFu, m = u & 0x7FFFFFu;
-  if (e == 0xFFu)
-    return __longlong_as_double((long long)(sign | (0x7FFull << 52) | ((unsigned long long)m << 29)));
-  if (e == 0u) {
-    if (m == 0u) return __longlong_as_double((long long)sign);
-    // subnormal: m 2^-149 with the leading one of m at bit p
-    const int p = 31 - __clz(m);
-    const unsigned long long mant = ((unsigned long long)m << (52 - p)) & 0xFFFFFFFFFFFFFull;
-    return __longlong_as_double((long long)(sign | ((unsigned long long)(p - 149 + 1023) << 52) | mant));
-  }
-  return __longlong_as_double(
-      (long long)(sign | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)m << 29)));
+  const unsigned e = (u >> 23) & 0xFFu;
+  if (e == 0u || e == 0xFFu) return (double)x;
+  const unsigned long long b = ((unsigned long long)(u >> 31) << 63) | ((unsigned long long)(e + 896u) << 52) |
+                               ((unsigned long long)(u & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)b);
 }
 // x is finite (not an infinity or a NaN): the exponent field is not all ones
 __device__ __forceinline__ bool f64_is_finite(double x) {
