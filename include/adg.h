@@ -173,9 +173,9 @@ ADG_API int adg_set_pde(adg_ctx* c, int pde, const double* params, int nparams);
  *              rounded values back), and every step call ends by widening the stored state
  *              into it.  adg_misfit and adg_adjoint need FP64 storage.
  * Others return ADG_EUNSUPPORTED (at the call, or at the first step for mixes that depend on
- * the mesh and PDE).  With PREDICTOR and CORRECTOR FP32 and FP64 storage the workspace also holds
- * the predictor's FP32 volume term (4 bytes per DOF): the corrector then forms dt (volume -
- * surface) in FP32 and adds it to the FP64 state in one FP64 operation per DOF (eq.
+ * the mesh and PDE).  For Euler with PREDICTOR and CORRECTOR FP32 and FP64 storage the workspace
+ * also holds the predictor's FP32 volume term (4 bytes per DOF): the corrector then forms dt
+ * (volume - surface) in FP32 and adds it to the FP64 state in one FP64 operation per DOF (eq.
  * weak_form_volume_surface).  Changing PREDICTOR, CORRECTOR or STORAGE, or switching refinement on
  * or off, can change the workspace size: bind the buffers again. */
 ADG_API int adg_set_kernel_precision(adg_ctx* c, int kernel, int prec, int flags);

@@ -327,10 +327,13 @@ static void* storage_ptr(const adg_ctx* c) {
   return (char*)c->ws + align256(traces_bytes(c)) + align256(l2_partial_bytes(c));
 }
 // FP32 predictor and corrector with FP64 storage: the predictor's volume term goes through an FP32
-// buffer, and the corrector accumulates dt (vol - surf) into the FP64 state once per DOF
+// buffer, and the corrector accumulates dt (vol - surf) into the FP64 state once per DOF.  Used for
+// Euler, where it measured faster (3D N = 5: corrector 3.33 -> 3.21 ms at 64^3); for 3D elasticity
+// the 4 extra bytes per DOF the corrector reads cost more than the FP64 work they save (2.56 ->
+// 3.01 ms at 48^3), and the other PDEs keep the two FP64 updates as well.
 static bool uses_volbuf(const adg_ctx* c) {
-  return c->prec[ADG_K_PREDICTOR] == P32 && c->prec[ADG_K_CORRECTOR] == P32 && c->prec[ADG_K_STORAGE] == P64 &&
-         c->refine == 0;
+  return c->pde == ADG_EULER && c->prec[ADG_K_PREDICTOR] == P32 && c->prec[ADG_K_CORRECTOR] == P32 &&
+         c->prec[ADG_K_STORAGE] == P64 && c->refine == 0;
 }
 static size_t volbuf_bytes(const adg_ctx* c) {
   return uses_volbuf(c) ? (size_t)c->ncells * c->V * c->NS * sizeof(float) : 0;
