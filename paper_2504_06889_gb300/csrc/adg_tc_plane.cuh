@@ -26,10 +26,11 @@
 // lo hi accumulate in the same tile.  The first sweep starts from q = Q at every time node: only
 // the k = 0 groups are contracted and multiplied by the row sums of dt P.
 //
-// Operand layouts (no swizzle, 8-row core matrices of 16 bytes): A_xy and B_xy K-major, A_xy's
-// K cores 144 bytes apart so that a warp's stores of consecutive plane positions hit distinct
-// banks; B_z MN-major (8 plane positions per 16-byte core row), its position groups 144 bytes
-// apart for the same reason.  Waits are bounded: a wait that runs out sets DevScalars::timeout,
+// Operand layouts (no swizzle, 8-row core matrices of 16 bytes): A_xy and B_xy K-major, B_z
+// MN-major (8 plane positions per 16-byte core row).  In A_xy and B_z the core matrices of one K
+// core (A_xy) or one position group (B_z) are contiguous over all 128 rows, so that a node's store
+// address is one base plus a compile-time offset, and those 2 KB blocks sit 16 bytes more than
+// their size apart, so that a warp's stores of consecutive plane positions hit distinct banks.  Waits are bounded: a wait that runs out sets DevScalars::timeout,
 // the kernel stops at its next barrier and frees its tensor memory.
 #pragma once
 
@@ -49,26 +50,27 @@ template <class C> struct TpCfg {
   static constexpr int KXY = (2 * NP + 15) / 16 * 16;   // K of the x-y contraction
   static constexpr int KZ = (RT + 15) / 16 * 16;        // K of the z contraction of a full tile
   static constexpr int KZ_LAST = (GLAST * n + 15) / 16 * 16;
-  // A_xy: K-major; K cores LBO_A apart, 8-row groups SBO_A apart
-  static constexpr int LBO_A = 144;
-  static constexpr int SBO_A = (KXY / 8) * LBO_A;
-  static constexpr int A_TILE = 16 * SBO_A;
-  static constexpr int RG_LAST = (GLAST * n + 7) / 8;   // 8-row groups written in the last tile
-  // rows of the last tile past its groups are read by the MMA (their products land in rows that
-  // nobody reads): they overlap the exchange buffer that follows
-  static constexpr int A_BYTES = (TILES - 1) * A_TILE + RG_LAST * SBO_A;
+  // A_xy: K-major; the 8-row groups of a K core contiguous (SBO 128 bytes), so that a row's
+  // address is linear in the row and a node's stores are one base plus compile-time offsets; K
+  // cores LBO_A apart, 128 rows of 16 bytes plus 16 bytes, so that a warp's stores of consecutive
+  // plane positions fall in distinct banks
+  static constexpr int SBO_A = 128;
+  static constexpr int LBO_A = 128 * 16 + 16;
+  static constexpr int A_TILE = (KXY / 8) * LBO_A;
+  static constexpr int A_BYTES = TILES * A_TILE;
   // the exchange buffer R_s[p][r] (FP32), row stride PS odd: stores by row and loads by position
   // are conflict-free
   static constexpr int PS = ROWS | 1;
   static constexpr int R_OFF = (A_BYTES + 127) / 128 * 128;
   static constexpr int R_BYTES = NP * PS * 4;
   static constexpr int LOW_END = R_OFF + R_BYTES;       // A_xy + R_s (the final stage reuses it)
-  // B_z: MN-major; groups of 8 plane positions NG_Z apart, 8-row K groups KG_Z apart.  For an
-  // MN-major operand without swizzle the descriptor's leading byte offset is the K-group stride and
-  // its stride byte offset the MN-group stride (measured on this part)
-  static constexpr int NG_Z = 144;
-  static constexpr int KG_Z = (NCOL / 8) * NG_Z;
-  static constexpr int Z_TILE = (KZ / 8) * KG_Z;
+  // B_z: MN-major; 8-row K groups contiguous (128 bytes), groups of 8 plane positions NG_Z apart
+  // (128 K rows plus 16 bytes).  For an MN-major operand without swizzle the descriptor's leading
+  // byte offset is the K-group stride and its stride byte offset the MN-group stride (measured on
+  // this part)
+  static constexpr int KG_Z = 128;
+  static constexpr int NG_Z = KZ * 16 + 16;
+  static constexpr int Z_TILE = (NCOL / 8) * NG_Z;
   static constexpr int BZ_OFF = (LOW_END + 127) / 128 * 128;
   // B_xy hi and lo: K-major, core LBO 128, SBO (KXY / 8) * 128
   static constexpr int BXY_BYTES = NCOL * KXY * 2;
@@ -84,7 +86,6 @@ template <class C> struct TpCfg {
   static_assert(C::NG == 0, "plane-form tensor-core predictor: conservative PDEs");
   static_assert(NCOL <= 256 && NCOL % 16 == 0, "MMA N");
   static_assert(TCOLS <= 256, "two CTAs per SM share the 512 tensor-memory columns");
-  static_assert((TILES - 1) * A_TILE + A_TILE <= BXY_OFF, "the last tile's MMA reads stay in the buffers");
   // the reader warps of a tile's lane quarters must be full warps
   static_assert((TILES - 1) * 4 * 32 + ((GLAST * n + 31) / 32) * 32 <= (THREADS / 32) * 32,
                 "every accumulator row needs a full reader warp");
@@ -93,11 +94,11 @@ template <class C> struct TpCfg {
 namespace tcp {
 // A_xy byte offset of (row r, column c) in a tile
 template <class G> __device__ __forceinline__ int aoff(int r, int c) {
-  return (r >> 3) * G::SBO_A + (r & 7) * 16 + (c >> 3) * G::LBO_A + (c & 7) * 2;
+  return r * 16 + (c >> 3) * G::LBO_A + (c & 7) * 2;
 }
 // B_z byte offset of (K row kr, plane position p) in a tile (MN-major)
 template <class G> __device__ __forceinline__ int zoff(int kr, int p) {
-  return (kr >> 3) * G::KG_Z + (kr & 7) * 16 + (p >> 3) * G::NG_Z + (p & 7) * 2;
+  return kr * 16 + (p >> 3) * G::NG_Z + (p & 7) * 2;
 }
 // B_xy byte offset of (output position p, column c)
 template <class G> __device__ __forceinline__ int boff(int p, int c) {
@@ -287,14 +288,11 @@ __global__ void __launch_bounds__(TpCfg<C>::THREADS, 2) k_predictor_tcp(const __
         // ---- fluxes into the operands: A_xy word (F_x, F_y) and B_z value F_z per (k, v) ------
         // the final stage and the exchange buffer overwrite the zero columns of A_xy's K padding:
         // clear them (every row the MMAs read for live accumulator rows)
-        if constexpr (G::KXY > 2 * NP) {
-          constexpr int RG = (TILES - 1) * 16 + G::RG_LAST;
-          for (int t = tid; t < RG * 8; t += blockDim.x) {
-            const int rg = t >> 3, rr = t & 7;
-            const int tile = rg / 16, rgl = rg % 16;
-            *reinterpret_cast<uint4*>(Abuf + tile * G::A_TILE + rgl * G::SBO_A + rr * 16 +
-                                      (2 * NP / 8) * G::LBO_A) = make_uint4(0u, 0u, 0u, 0u);
-          }
+        if constexpr (G::KXY > 2 * NP) {  // the last K core holds the padding: 128 rows per tile
+          static_assert(G::KXY - 2 * NP <= 8 && (2 * NP) % 8 == 0, "padding fills the last K core");
+          for (int t = tid; t < TILES * 128; t += blockDim.x)
+            *reinterpret_cast<uint4*>(Abuf + (t >> 7) * G::A_TILE + (G::KXY / 8 - 1) * G::LBO_A + (t & 127) * 16) =
+                make_uint4(0u, 0u, 0u, 0u);
         }
 #pragma unroll
         for (int k = 0; k < n; ++k) {
@@ -344,7 +342,7 @@ __global__ void __launch_bounds__(TpCfg<C>::THREADS, 2) k_predictor_tcp(const __
             const int kz = first ? 2 : (tile == TILES - 1 ? G::KZ_LAST / 16 : G::KZ / 16);
 #pragma unroll 1
             for (int ks = 0; ks < kz; ++ks) {
-              const uint64_t zd = tc::sdesc(zb + (uint32_t)(ks * 2 * G::KG_Z), G::KG_Z, G::NG_Z);
+              const uint64_t zd = tc::sdesc(zb + (uint32_t)(ks * 2 * G::KG_Z), G::KG_Z, G::NG_Z);  // 16 K rows a step
               tcp::mma_ts(d, tmem + (uint32_t)(G::AZ_HI + ks * 8), zd, idesc_z, 1u);
               if (comp && pass == 0) tcp::mma_ts(d, tmem + (uint32_t)(G::AZ_LO + ks * 8), zd, idesc_z, 1u);
             }
