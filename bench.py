@@ -81,7 +81,7 @@ MIXES["bf16ref3"] = {"picard": "bf16", "predictor": "fp64", "riemann": "fp64", "
 
 # default mixes per workload (the tensor-core predictor is built for the 3D meshes)
 DEFAULT_MIXES = {
-    "euler3d": "fp64,fp32pred,fp32,bf16tc,fp16tc,fp8tc,fp32ref3",
+    "euler3d": "fp64,fp32pred,fp32,bf16tc,bf16tc64,fp16tc,fp8tc,fp32ref3",
     "elastic3d": "fp64,fp32,fp16tc,bf16tc,fp8tc,fp64ck,fp32ck",
     "acoustic3d": "fp64,fp32,fp16tc,fp64ck,fp32ck",
     "acoustic2d": "fp64,fp32,fp64ck,fp32ck",
