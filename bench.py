@@ -142,20 +142,25 @@ def predictor_flops_per_cell(pde, dim, N, iters=None, scheme="picard"):
     return (first + (it - 1) * sweep if it > 0 else 0) + final + vol + traces
 
 
-def predictor_bytes_per_cell(pde, dim, N, trace_bytes, state_bytes=8):
-    """Algorithmic HBM bytes of the predictor for one cell: read and write the state (FP64, or
-    the storage format), write the face traces (Qbar and Fbar.n, both sides of every
+def predictor_bytes_per_cell(pde, dim, N, trace_bytes, state_bytes=8, write_bytes=None):
+    """Algorithmic HBM bytes of the predictor for one cell: read the state (FP64, or the storage
+    format), write it back (or, where the volume term goes through the FP32 volume buffer, write
+    that: write_bytes = 4), write the face traces (Qbar and Fbar.n, both sides of every
     direction)."""
     n = N + 1
     V = I.nvar(pde, dim)
-    return 2 * state_bytes * n ** dim * V + 2 * dim * 2 * V * n ** (dim - 1) * trace_bytes
+    wb = state_bytes if write_bytes is None else write_bytes
+    return (state_bytes + wb) * n ** dim * V + 2 * dim * 2 * V * n ** (dim - 1) * trace_bytes
 
 
 # DRAM bytes per cell of one predictor launch, from one ncu capture of the same kernel on a
 # 32^3 case of the workload (dram__bytes_read.sum + dram__bytes_write.sum divided by the cells);
 # the traffic of a launch is proportional to its cells.  Keyed by (workload, mix); an entry holds
 # only while the kernel is unchanged since its capture, and is removed when the kernel changes.
-MEASURED_TRAFFIC = {}
+MEASURED_TRAFFIC = {
+    ("euler3d_N5_64^3", "fp32"): 653.399e6 / 32768,
+    ("euler3d_N5_64^3", "bf16tc"): 654.879e6 / 32768,
+}
 
 
 def load_peaks():
@@ -468,7 +473,9 @@ def run_mixes(adg, wl, mixes, table, args, ws, local, alu, peaks, headline=None,
         r["roofline"] = roofline_of(wl, mix, prec, scheme, ms_pred / args.steps, alu, peaks)
         tb = {"fp64": 8, "fp32": 4, "bf16": 2}[prec["corrector"]]
         sb = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}[prec.get("storage", "fp64")]
-        bts = predictor_bytes_per_cell(wl.pde, wl.dim, wl.N, tb, sb) * wl.ncells
+        volbuf = (wl.pde == I.EULER and prec["predictor"] == "fp32" and prec["corrector"] == "fp32"
+                  and prec.get("storage", "fp64") == "fp64" and mix not in MIX_REFINE)
+        bts = predictor_bytes_per_cell(wl.pde, wl.dim, wl.N, tb, sb, 4 if volbuf else None) * wl.ncells
         r["predictor_gbs"] = bts / (ms_pred / args.steps * 1e-3) / 1e9
         if mix == headline and e2e:
             # end to end through the public API with pinned host buffers, every step
