@@ -527,9 +527,8 @@ def main():
     ap.add_argument("--adjoint", action="store_true", help="also time the adjoint (acoustics)")
     ap.add_argument("--nsnap", type=int, default=10)
     ap.add_argument("--headline", default="fp32")
-    ap.add_argument("--second", default="elastic3d",
-                    help="second workload block of the default run ('' for none)")
-    ap.add_argument("--second-mixes", default="fp64,fp32,fp16tc,fp8tc")
+    ap.add_argument("--second", default="elastic3d:fp64,fp32,fp16tc,fp8tc;swe2d:fp64,fp32;acoustic3d:fp64,fp32,fp32ck",
+                    help="further workload blocks of the default run, 'name:mix,mix;...' ('' for none)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--ref-cells", type=int, default=12)
@@ -560,16 +559,18 @@ def main():
         "fp32" if "fp32" in mixes else "pred-fp32_riem-fp32_corr-fp32" if args.sweep else mixes[-1])
     results, clocks = run_mixes(adg, wl, mixes, table, args, ws, local, alu, peaks, headline=headline,
                                 e2e=not args.no_e2e)
-    second = None
-    run_second = (args.second and not args.mixes and not args.sweep and not args.cells
-                  and args.workload == "euler3d" and args.second in I.WORKLOADS)
-    if run_second:
-        wl2 = I.WORKLOADS[args.second]()
-        mixes2 = [m for m in args.second_mixes.split(",") if m]
+    others = []
+    run_others = args.second and not args.mixes and not args.sweep and not args.cells and args.workload == "euler3d"
+    for block in (args.second.split(";") if run_others else []):
+        name, _, ms2 = block.partition(":")
+        if name not in I.WORKLOADS:
+            continue
+        wl2 = I.WORKLOADS[name]()
+        mixes2 = [m for m in ms2.split(",") if m]
         res2, _ = run_mixes(adg, wl2, mixes2, table, args, ws, local, alu, peaks)
-        second = {"workload": wl_label(wl2), "dof": wl2.dofs,
-                  "fp64_gpu_value": res2["fp64"]["dof_per_s"] if "fp64" in res2 else None,
-                  "mixes": compact(res2)}
+        others.append({"workload": wl_label(wl2), "dof": wl2.dofs,
+                       "fp64_gpu_value": res2["fp64"]["dof_per_s"] if "fp64" in res2 else None,
+                       "mixes": compact(res2)})
     adjoint = None
     if args.adjoint and wl.pde == I.ACOUSTIC and wl.dim == 3:
         adjoint = time_adjoint(adg, wl, args.nsnap)
@@ -603,8 +604,8 @@ def main():
         "gpu_launches": 2 * args.steps,
         "clocks": clocks,
     }
-    if second is not None:
-        line["second_workload"] = second
+    if others:
+        line["other_workloads"] = others
     if adjoint is not None:
         line["adjoint"] = adjoint
     # the full per-mix records (per-variable errors, kernel names, bandwidths) go to stderr, so

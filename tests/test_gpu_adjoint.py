@@ -195,3 +195,29 @@ def test_full_size_adjoint_finite_differences(adg):
     cm[k] -= eps
     fd = (misfit(Q0, cp) - misfit(Q0, cm)) / (2 * eps)
     assert abs(fd - gc2[k]) <= 1e-6 * abs(fd), (fd, gc2[k])
+
+
+@pytest.mark.parametrize("dim,N,m", [(3, 4, 3), (3, 2, 4), (2, 3, 5)])
+def test_adjoint_dot_product_identity(adg, oracle_mod, dim, N, m):
+    """For a fixed wave speed the receiver samples are a linear map L of the initial pressure (the
+    pulse starts at rest), so with zero data J = 1/2 |L p0|^2 and the adjoint gradient is
+    g = L^T L p0.  Hence <g, w> = <L p0, L w> for every pressure field w: one identity that
+    involves every entry of g, with L w from a forward run that starts from w."""
+    M, c, Q0, xyz, _ = setup_case(oracle_mod, dim, N, m, seed=2)
+    nsteps = 7
+    zero = np.zeros((nsteps, len(xyz)))
+    s = gpu_solver(adg, M, c)
+    s.set_state(Q0, 0.0)
+    _, gq, _ = s.adjoint(nsteps, 3, xyz, zero)
+    g = gq.cpu().numpy()
+    s.set_state(Q0, 0.0)
+    _, r0 = s.misfit(nsteps, xyz)
+    rng = np.random.default_rng(7)
+    for _ in range(2):
+        Qw = np.zeros_like(Q0)
+        Qw[:, 0, :] = rng.normal(size=Qw[:, 0, :].shape)
+        s.set_state(Qw, 0.0)
+        _, rw = s.misfit(nsteps, xyz)
+        lhs = float(np.sum(g * Qw[:, 0, :]))
+        rhs = float(np.sum(r0 * rw))
+        assert abs(lhs - rhs) <= 1e-10 * max(abs(rhs), np.linalg.norm(r0) * np.linalg.norm(rw)), (lhs, rhs)
