@@ -15,7 +15,7 @@ floor, the mixes stop converging: the floor itself is asserted (below the FP32 t
 that the statement above has its stated range.
 
 Mixes: "bf16" = bf16 tensor-core sweeps with the last two compensated and the final stage, Riemann
-and corrector in FP32 (the north-star mix); "bf16f64" the same sweeps with the final stage,
+and corrector in FP32; "bf16f64" the same sweeps with the final stage,
 Riemann and corrector in FP64; "fp16" = fp16 tensor-core sweeps with per-cell scaling and a
 compensated last sweep; "fp32" = every kernel in FP32.
 """
