@@ -3,6 +3,7 @@
 #include "adg_tc.cuh"
 #include "adg_adjoint.cuh"
 #include "adg_refine.cuh"
+#include "adg_corrector_bulk.cuh"
 
 namespace adg {
 template <int D, int N>
@@ -26,6 +27,7 @@ void register_acoustic() {
     add_refine<0, 3, 4>(e);
     add_ck<0, 3, 4>(e);
     add_adjoint<3, 4>(e);
+    add_corrector_bulk<0, 3, 4>(e);
     register_entry(e);
   }  // 3D, N = 4 (pulse / adjoint workload)
   {

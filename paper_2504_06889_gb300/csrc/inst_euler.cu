@@ -4,6 +4,7 @@
 #include "adg_tc_sweep.cuh"
 #include "adg_tc_plane.cuh"
 #include "adg_refine.cuh"
+#include "adg_corrector_bulk.cuh"
 
 namespace adg {
 void register_euler() {
@@ -18,6 +19,7 @@ void register_euler() {
     e.predictor_tc_f64[P64] = launch_predictor_tcp<Cfg<2, 3, 5>, double, true>;
     e.predictor_tc_f64[P32] = launch_predictor_tcp<Cfg<2, 3, 5>, float, true>;
     add_refine<2, 3, 5>(e);
+    add_corrector_bulk<2, 3, 5>(e);
     register_entry(e);
   }  // 3D, N = 5 (density-wave workload)
   {
