@@ -189,6 +189,7 @@ bool build_tables(int n, Tables* T) {
     for (int m = 0; m < n / 2; ++m) {
       T->fDe[i][m] = (float)((D[i][m] + D[i][n - 1 - m]) / 2);
       T->fDo[i][m] = (float)((D[i][m] - D[i][n - 1 - m]) / 2);
+      T->fDoe[i][m] = make_float2(T->fDo[i][m], T->fDe[i][m]);
     }
   return true;
 }

@@ -25,6 +25,8 @@ struct Tables {
   // even and odd parts of D for the FP32 pencil contractions, i, m < n/2:
   // fDe[i][m] = (D[i][m] + D[i][n-1-m]) / 2, fDo[i][m] = (D[i][m] - D[i][n-1-m]) / 2
   float fDe[kMaxN1 / 2][kMaxN1 / 2], fDo[kMaxN1 / 2][kMaxN1 / 2];
+  // the same pairs interleaved, {fDo[i][m], fDe[i][m]}, for two-lane FMAs
+  float2 fDoe[kMaxN1 / 2][kMaxN1 / 2];
   // row sums of P (the first Picard sweep, every time node at Q), summed in FP64
   float fProw[kMaxN1];
 };

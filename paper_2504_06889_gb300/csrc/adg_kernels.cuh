@@ -705,29 +705,26 @@ __device__ __forceinline__ void pencil_task(const T* f, T* o, const Tables& tab)
 #pragma unroll
     for (int m = 0; m < n; ++m) fv[m] = f[m * S];
   }
-  T fe[h], fo[h];
+  // (fo_m, fe_m) pairs: a_i and b_i accumulate side by side in the two lanes of one FMA, each
+  // lane in the order of the scalar sums (product, then FMAs in m)
+  float2 oe[h];
 #pragma unroll
-  for (int m = 0; m < h; ++m) {
-    fe[m] = fv[m] + fv[n - 1 - m];
-    fo[m] = fv[m] - fv[n - 1 - m];
-  }
+  for (int m = 0; m < h; ++m) oe[m] = make_float2(fv[m] - fv[n - 1 - m], fv[m] + fv[n - 1 - m]);
   T out[n];
 #pragma unroll
   for (int i = 0; i < h; ++i) {
-    T ai = tab.fDo[i][0] * fo[0], bi = tab.fDe[i][0] * fe[0];
+    float2 ab = __fmul2_rn(tab.fDoe[i][0], oe[0]);
 #pragma unroll
-    for (int m = 1; m < h; ++m) {
-      ai = fmaf(tab.fDo[i][m], fo[m], ai);
-      bi = fmaf(tab.fDe[i][m], fe[m], bi);
-    }
+    for (int m = 1; m < h; ++m) ab = __ffma2_rn(tab.fDoe[i][m], oe[m], ab);
+    T ai = ab.x, bi = ab.y;
     if constexpr (n % 2 == 1) bi = fmaf(tab.fD[i][h], fv[h], bi);
     out[i] = ai + bi;
     out[n - 1 - i] = ai - bi;
   }
   if constexpr (n % 2 == 1) {
-    T c = tab.fD[h][0] * fo[0];
+    T c = tab.fD[h][0] * oe[0].x;
 #pragma unroll
-    for (int m = 1; m < h; ++m) c = fmaf(tab.fD[h][m], fo[m], c);
+    for (int m = 1; m < h; ++m) c = fmaf(tab.fD[h][m], oe[m].x, c);
     out[h] = c;
   }
   if constexpr (S == 1 && n % 2 == 0) {
@@ -1449,12 +1446,14 @@ __global__ void __launch_bounds__(C::THREADS) k_corrector(const __grid_constant_
 // ------------------------------------------------------------------------------------------------
 template <class C>
 __global__ void k_lambda(const __grid_constant__ StepArgs a) {
-  // lambda_max(Q) exactly in FP64, with the FP64 spectral radius (FP64 division and square
-  // root, slow on this part) evaluated only where it can matter: a first pass takes the FP32
-  // estimate of every node of this block's share and their maximum; a second pass evaluates
-  // FP64 only on the nodes whose estimate is within 1e-4 (relative) of that maximum, or whose
-  // estimate is unreliable.  The FP32 relative error is far below 1e-4 for well-conditioned
-  // states, so the block's FP64 maximum is among them.
+  // lambda_max(Q) exactly in FP64 in one pass over the state, with the FP64 spectral radius
+  // (FP64 division and square root, slow on this part) evaluated only where it can matter: every
+  // node takes its FP32 estimate (the state converted by integer operations), the block keeps the
+  // running maximum of the estimates (a warp maximum, then one shared atomic per warp), and a node
+  // evaluates FP64 only if its estimate is within 1e-4 (relative) of that running maximum, or
+  // unreliable.  The running maximum never exceeds the block's final one and the FP32 relative
+  // error is far below 1e-4 for well-conditioned states, so the block's FP64 maximum is among the
+  // nodes evaluated.
   using Ph = Phys<C::PDE, C::D>;
   constexpr int V = C::V, NS = C::NS;
   __shared__ unsigned long long s_lam;
@@ -1466,40 +1465,42 @@ __global__ void k_lambda(const __grid_constant__ StepArgs a) {
   }
   __syncthreads();
   const size_t total = (size_t)a.ncells * NS;
-  const size_t first = blockIdx.x * (size_t)blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
-  auto load = [&](size_t g, double* q, float* qf, int& cell) {
-    cell = (int)(g / NS);
-    const int i = (int)(g % NS);
-#pragma unroll
-    for (int v = 0; v < V; ++v) {
-      q[v] = a.Q[((size_t)cell * V + v) * NS + i];
-      qf[v] = (float)q[v];
-    }
-  };
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  const int lane = threadIdx.x & 31;
   bool bad = false;
-  float est = 0.0f;
-  for (size_t g = first; g < total; g += stride) {
-    double q[V];
-    float qf[V];
-    int cell;
-    load(g, q, qf, cell);
-#pragma unroll
-    for (int v = 0; v < V; ++v) bad |= !isfinite(q[v]);
-    const float l32 = Ph::maxspeed(make_pp<float>(a.pp, cell), qf);
-    if (l32 < 3.0e38f && !Ph::speed_is_ill_conditioned(qf)) est = fmaxf(est, l32);
-  }
-  atomicMax(&s_l32, __float_as_uint(est));
-  __syncthreads();
-  const float thr = __uint_as_float(s_l32) * (1.0f - 1.0e-4f);
   double lam = 0.0;
-  for (size_t g = first; g < total; g += stride) {
+  // (blockDim.x is a multiple of 32 and every lane runs every round, so the warp operations see
+  // full warps)
+  for (size_t base = blockIdx.x * (size_t)blockDim.x; base < total; base += stride) {
+    const size_t g = base + threadIdx.x;
+    const bool valid = g < total;
     double q[V];
     float qf[V];
-    int cell;
-    load(g, q, qf, cell);
-    const float l32 = Ph::maxspeed(make_pp<float>(a.pp, cell), qf);
-    const bool risky = !(l32 < 3.0e38f) || Ph::speed_is_ill_conditioned(qf);
-    if (risky || l32 >= thr) lam = fmax(lam, Ph::maxspeed(make_pp<double>(a.pp, cell), q));
+    int cell = 0;
+    bool risky = false, node_bad = false;
+    float l32 = 0.0f;
+    unsigned key = 0u;
+    if (valid) {
+      cell = (int)(g / NS);
+      const int i = (int)(g % NS);
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        q[v] = a.Q[((size_t)cell * V + v) * NS + i];
+        qf[v] = f64_to_f32_rn(q[v]);
+        node_bad |= !f64_is_finite(q[v]);
+      }
+      l32 = Ph::maxspeed(make_pp<float>(a.pp, cell), qf);
+      risky = !(l32 < 3.0e38f) || Ph::speed_is_ill_conditioned(qf);
+      if (!risky) key = __float_as_uint(l32);
+    }
+    const unsigned wmax = __reduce_max_sync(0xffffffffu, key);
+    unsigned old = 0u;
+    if (lane == 0) old = atomicMax(&s_l32, wmax);
+    old = __shfl_sync(0xffffffffu, old, 0);
+    const float run = fmaxf(__uint_as_float(old), __uint_as_float(wmax));
+    bad |= node_bad;
+    if (valid && !node_bad && (risky || l32 >= run * (1.0f - 1.0e-4f)))
+      lam = fmax(lam, Ph::maxspeed(make_pp<double>(a.pp, cell), q));
   }
   bad |= !isfinite(lam);
   if (!bad) atomicMax(&s_lam, (unsigned long long)__double_as_longlong(lam));

@@ -49,12 +49,15 @@ __device__ __forceinline__ __nv_bfloat16 conv<__nv_bfloat16, __nv_bfloat16>(__nv
 // converts, retires about 1/64 of the FP32 rate, so the hot kernels avoid it.  Both follow the
 // IEEE 754 definitions (binary64 -> binary32 round to nearest, ties to even; binary32 -> binary64
 // exact); zeros, subnormals, non-finite values and results outside the normal FP32 range take the
-// hardware conversion.
+// hardware conversion, in a function of its own: called, it is a branch that the common case skips,
+// where an inlined one can be turned into a conversion that every thread executes.
+static __device__ __noinline__ float f64_to_f32_hw(double x) { return __double2float_rn(x); }
+static __device__ __noinline__ double f32_to_f64_hw(float x) { return (double)x; }
 __device__ __forceinline__ float f64_to_f32_rn(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const unsigned hi = (unsigned)(b >> 32);
   const int e = (int)((hi >> 20) & 0x7FFu) - 1023;
-  if (e < -126 || e > 127) return __double2float_rn(x);
+  if (e < -126 || e > 127) return f64_to_f32_hw(x);
   const unsigned m = (unsigned)((b >> 29) & 0x7FFFFFull);  // the 23 kept significand bits
   const unsigned rest = (unsigned)(b & 0x1FFFFFFFull);      // the 29 dropped ones
   unsigned r = ((unsigned)(e + 127) << 23) | m;
@@ -66,7 +69,7 @@ __device__ __forceinline__ float f64_to_f32_rn(double x) {
 __device__ __forceinline__ double f32_to_f64(float x) {
   const unsigned u = __float_as_uint(x);
   const unsigned e = (u >> 23) & 0xFFu;
-  if (e == 0u || e == 0xFFu) return (double)x;
+  if (e == 0u || e == 0xFFu) return f32_to_f64_hw(x);
   const unsigned long long b = ((unsigned long long)(u >> 31) << 63) | ((unsigned long long)(e + 896u) << 52) |
                                ((unsigned long long)(u & 0x7FFFFFu) << 29);
   return __longlong_as_double((long long)b);
