@@ -50,7 +50,7 @@ template <class C, class TC, class TS, int NT, int NQ> struct CorrBulkSmem {
   static constexpr int Q_OFF = NT * T_STAGE;
   static constexpr int G_OFF = Q_OFF + NQ * Q_STAGE;              // Rusanov fluxes [2d][V][NF] (TC)
   static constexpr int SMAX_OFF = G_OFF + (2 * D * V * NF * (int)sizeof(TC) + 15) / 16 * 16;  // [2d] (bits)
-  static constexpr int COEF_OFF = SMAX_OFF + 32;
+  static constexpr int COEF_OFF = SMAX_OFF + (2 * D * (int)sizeof(TS) + 15) / 16 * 16;
   static constexpr int TOTAL = COEF_OFF + 2 * D * n * (int)sizeof(TC);
 };
 
@@ -77,7 +77,9 @@ __global__ void __launch_bounds__(C::THREADS, MINB) k_corrector_bulk(const __gri
   using TR = TS;  // the Riemann solve runs in the trace precision, on the staged traces
   constexpr int n = C::n, V = C::V, D = C::D, NS = C::NS, NF = C::NF;
   static_assert(S::ok, "bulk corrector: 3D, one cell per block, copied blocks in 16-byte units");
-  static_assert(std::is_same<TS, float>::value, "bulk corrector: FP32 traces (the face maxima reduce 32-bit keys)");
+  static_assert(std::is_same<TS, float>::value || std::is_same<TS, double>::value, "bulk corrector: FP32 or FP64 traces");
+  // face speeds are non-negative, so their bit patterns order like their values
+  using Key = typename std::conditional<std::is_same<TS, double>::value, unsigned long long, unsigned>::type;
   extern __shared__ __align__(128) unsigned char cb_smem[];
   __shared__ __align__(8) uint64_t s_tbar[NT], s_qbar[NQ];
   __shared__ unsigned long long s_lam;
@@ -85,7 +87,7 @@ __global__ void __launch_bounds__(C::THREADS, MINB) k_corrector_bulk(const __gri
   __shared__ double s_dt;
   if (a.sc->bad) return;
   const int tid = threadIdx.x, i = tid, warp = tid >> 5, lane = tid & 31;
-  unsigned* const sSmax = reinterpret_cast<unsigned*>(cb_smem + L::SMAX_OFF);  // face speeds (FP32 bits)
+  Key* const sSmax = reinterpret_cast<Key*>(cb_smem + L::SMAX_OFF);  // face speeds (bit patterns)
   if (tid == 0) {
     s_lam = 0ull;
     s_bad = 0u;
@@ -95,7 +97,7 @@ __global__ void __launch_bounds__(C::THREADS, MINB) k_corrector_bulk(const __gri
     for (int s = 0; s < NQ; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(&s_qbar[s])));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
-  if (tid < 2 * D) sSmax[tid] = 0u;
+  if (tid < 2 * D) sSmax[tid] = 0;
   TC* sG = reinterpret_cast<TC*>(cb_smem + L::G_OFF);
   TC* sCoef = reinterpret_cast<TC*>(cb_smem + L::COEF_OFF);
   for (int t = tid; t < 2 * D * n; t += blockDim.x) {
@@ -179,7 +181,7 @@ __global__ void __launch_bounds__(C::THREADS, MINB) k_corrector_bulk(const __gri
     for (int base = 0; base < 2 * D * NF; base += NS) {
       const int it = base + i;
       int f = 2 * D;  // (no face)
-      unsigned sbits = 0u;
+      Key sbits = 0;
       if (it < 2 * D * NF) {
         const int j = it % NF;
         f = it / NF;
@@ -195,10 +197,26 @@ __global__ void __launch_bounds__(C::THREADS, MINB) k_corrector_bulk(const __gri
         const PP<TR> ppN = make_pp<TR>(a.pp, neighbour(a, cell, dir, side));
         const TR sm = side ? Ph::speed(ppL, qm, dir) : Ph::speed(ppN, qm, dir);
         const TR sp = side ? Ph::speed(ppN, qp, dir) : Ph::speed(ppL, qp, dir);
-        sbits = __float_as_uint(tmax(sm, sp));
+        const TR smax = tmax(sm, sp);
+        if constexpr (std::is_same<TS, double>::value)
+          sbits = (Key)__double_as_longlong(smax);
+        else
+          sbits = __float_as_uint(smax);
       }
+      // the lanes of one face are consecutive: reduce over them, the lowest lane holds the result
       const unsigned same = __match_any_sync(wmask, f);
-      const unsigned m = __reduce_max_sync(same, sbits);
+      Key m;
+      if constexpr (std::is_same<TS, double>::value) {
+        const int last = 31 - __clz(same);
+        m = sbits;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+          const Key o = __shfl_down_sync(wmask, m, off);
+          if (lane + off <= last) m = o > m ? o : m;
+        }
+      } else {
+        m = __reduce_max_sync(same, sbits);
+      }
       if (f < 2 * D && lane == __ffs(same) - 1) atomicMax(&sSmax[f], m);
     }
     __syncthreads();  // B2: the face speeds are complete
@@ -208,7 +226,11 @@ __global__ void __launch_bounds__(C::THREADS, MINB) k_corrector_bulk(const __gri
       for (int e = i; e < V * NF; e += NS) {
 #pragma unroll
         for (int f = 0; f < 2 * D; ++f) {
-          const TR s = __uint_as_float(sSmax[f]);
+          TR s;
+          if constexpr (std::is_same<TS, double>::value)
+            s = __longlong_as_double((long long)sSmax[f]);
+          else
+            s = __uint_as_float(sSmax[f]);
           const TR qm = tr(f, 0, 0)[e], qp = tr(f, 1, 0)[e];
           const TR Fm = tr(f, 0, 1)[e], Fp = tr(f, 1, 1)[e];
           const TR G = half * (Fm + Fp) + half * s * (qm - qp);
@@ -218,7 +240,7 @@ __global__ void __launch_bounds__(C::THREADS, MINB) k_corrector_bulk(const __gri
     }
     __syncthreads();  // B3: sG is complete; the trace stage and the face speeds are free
     if (tid == 0) {
-      for (int f = 0; f < 2 * D; ++f) sSmax[f] = 0u;
+      for (int f = 0; f < 2 * D; ++f) sSmax[f] = 0;
       issue_t(k + NT);
     }
     // surface integral and update: Q_i -= dt sum_dir (1/h)(psi1[i_dir] G+ - psi0[i_dir] G-)/w[i_dir]
@@ -354,14 +376,14 @@ cudaError_t launch_corrector_bulk(const StepArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// Replace the FP32 corrector (FP32 traces, Riemann and surface arithmetic) of an Entry by the bulk
-// form.  (For the FP64 corrector the bulk form measured slower: that kernel is bound by the FP64
-// pipe, and the staging halves the blocks an SM holds.)
+// Replace the FP32 corrector (FP32 traces, Riemann and surface arithmetic) and the FP64 one of an
+// Entry by the bulk form.
 template <int PDE, int D, int N>
 void add_corrector_bulk(Entry& e) {
   using C = Cfg<PDE, D, N>;
-  static_assert(CorrBulkShape<C, float>::ok, "configuration without the bulk form");
+  static_assert(CorrBulkShape<C, float>::ok && CorrBulkShape<C, double>::ok, "configuration without the bulk form");
   e.corrector[P32][P32] = launch_corrector_bulk<C, float, float, 1, 1, 6>;
+  e.corrector[P64][P64] = launch_corrector_bulk<C, double, double, 1, 1, 4>;
 }
 
 }  // namespace adg
