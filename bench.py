@@ -595,23 +595,26 @@ def main():
                    "cells": list(wl.cells), "dof": wl.dofs, "mix": headline, "cfl": wl.cfl,
                    "parallelism": "replicas" if ws > 1 else "single",
                    "l2_flush": "inputs larger than L2 (FP64 state %.2f GB)" % (wl.dofs * 8 / 1e9)},
-        "fp64_gpu_value": fp64v,
-        "vs_fp64_gpu": h["dof_per_s"] / fp64v if fp64v else None,
-        "l2_vs_exact": h.get("l2_vs_exact"),
-        "l2_rel_vs_fp64_gpu": h.get("l2_rel_vs_fp64_gpu"),
         "mixes": compact(results),
-        "roofline": h["roofline"],
-        "alu_peaks_measured": {k: round(v, 3) for k, v in alu.items()},
-        "cpu_baseline": cpu,
-        "cpu_baseline_1thread": cpu1,
-        "e2e": h.get("e2e"),
-        "gpu_launches": 2 * args.steps,
-        "clocks": clocks,
     }
     if others:
         line["other_workloads"] = others
     if adjoint is not None:
         line["adjoint"] = adjoint
+    # the headline's evidence and comparison last, so that a reader of the line's tail sees them
+    line.update({
+        "roofline": h["roofline"],
+        "alu_peaks_measured": {k: round(v, 3) for k, v in alu.items()},
+        "cpu_baseline": cpu,
+        "cpu_baseline_1thread": cpu1,
+        "clocks": clocks,
+        "gpu_launches": 2 * args.steps,
+        "e2e": h.get("e2e"),
+        "fp64_gpu_value": fp64v,
+        "vs_fp64_gpu": h["dof_per_s"] / fp64v if fp64v else None,
+        "l2_vs_exact": h.get("l2_vs_exact"),
+        "l2_rel_vs_fp64_gpu": h.get("l2_rel_vs_fp64_gpu"),
+    })
     # the full per-mix records (per-variable errors, kernel names, bandwidths) go to stderr, so
     # that stdout carries the one result line
     print(json.dumps({"detail": {wl_label(wl): results}, "peaks_file": peak_src}), file=sys.stderr, flush=True)
