@@ -1,4 +1,4 @@
-// Tensor-core Picard predictor in plane form (3D meshes, bf16 inputs, FP32 accumulation in
+// Tensor-core Picard predictor in plane form (3D meshes, bf16 or fp16 inputs, FP32 accumulation in
 // tensor memory).  arXiv 2504.06889, Sec. 3.1, eq. (Picard):
 //     q_k = Q - dt sum_l P[k][l] R_l,   R_l = sum_dir D_dir F_dir(q_l) / h_dir.
 //
@@ -20,8 +20,8 @@
 // time column and applies dt P in FP32 registers.
 //
 // The derivative of a constant is zero, so the operands hold F - F_c, with F_c the flux at the
-// cell's first node (the bf16 rounding applies to the variation of the flux over the cell).  In
-// the compensated sweeps every operand is split x = hi + lo (bf16 each): the constant operators
+// cell's first node (the 16-bit rounding applies to the variation of the flux over the cell).  In
+// the compensated sweeps every operand is split x = hi + lo (16 bits each): the constant operators
 // keep both parts, the data goes in two passes through the same buffers, and hi hi + hi lo +
 // lo hi accumulate in the same tile.  The first sweep starts from q = Q at every time node: only
 // the k = 0 groups are contracted and multiplied by the row sums of dt P.
@@ -77,7 +77,7 @@ template <class C> struct TpCfg {
   static constexpr int BXY_OFF = BZ_OFF + TILES * Z_TILE;
   static constexpr int TAB_OFF = BXY_OFF + 2 * BXY_BYTES;
   static constexpr int TOTAL = TAB_OFF + (n * n + 3 * n) * 8;  // FP64 final-stage tables
-  // tensor memory: accumulators, then A_z hi and lo (two bf16 per 32-bit column)
+  // tensor memory: accumulators, then A_z hi and lo (two 16-bit values per 32-bit column)
   static constexpr int AZ_HI = TILES * NCOL;
   static constexpr int AZ_LO = AZ_HI + KZ / 2;
   static constexpr int TCOLS = tc::pow2_cols(AZ_LO + KZ / 2);
@@ -118,17 +118,36 @@ __device__ __forceinline__ void st16(uint32_t taddr, const uint32_t* r) {
       "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
       "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]));
 }
-__device__ __forceinline__ uint32_t bf2(float a, float b) {  // a in the low half
+// two 16-bit operands in one 32-bit word (a in the low half), one operand, and the rounding of a
+// float to the operand type and back (E: bf16 or fp16)
+template <class E> __device__ __forceinline__ uint32_t pack2(float a, float b);
+template <> __device__ __forceinline__ uint32_t pack2<__nv_bfloat16>(float a, float b) {
   const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
   return *reinterpret_cast<const uint32_t*>(&h);
 }
-__device__ __forceinline__ float lo_part(float x) { return x - __bfloat162float(__float2bfloat16_rn(x)); }
+template <> __device__ __forceinline__ uint32_t pack2<__half>(float a, float b) {
+  const __half2 h = __floats2half2_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+template <class E> __device__ __forceinline__ E to_e(float x);
+template <> __device__ __forceinline__ __nv_bfloat16 to_e<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
+template <> __device__ __forceinline__ __half to_e<__half>(float x) { return __float2half_rn(x); }
+template <class E> __device__ __forceinline__ float round_e(float x);
+template <> __device__ __forceinline__ float round_e<__nv_bfloat16>(float x) {
+  return __bfloat162float(__float2bfloat16_rn(x));
+}
+template <> __device__ __forceinline__ float round_e<__half>(float x) { return __half2float(__float2half_rn(x)); }
+template <class E> __device__ __forceinline__ float lo_part(float x) { return x - round_e<E>(x); }
 }  // namespace tcp
 
 // F64: the final stage (last fluxes, time averages, volume integral, face traces) in FP64 from
 // q_k = Q - (dt P R)_k, the FP64 state minus the sweeps' FP32 correction; otherwise in FP32 (pencil
-// tasks) from the FP32 iterate.
-template <class C, class TS, bool F64 = false>
+// tasks) from the FP32 iterate.  E: the operand type, bf16 or fp16.  For fp16 (5 exponent bits)
+// the fluxes can be scaled per cell by a power of two, 2^-floor(log2 m) with m the previous
+// sweep's max |F - F_c| (the first sweep's from F(Q)), so that the scaled maximum lies in [1, 2);
+// the accumulator rows are multiplied back by the inverse power of two (both exact).  bf16 has
+// the exponent range of FP32, where such a scale cannot change the rounding, and takes none.
+template <class C, class TS, bool F64 = false, class E = __nv_bfloat16>
 __global__ void __launch_bounds__(TpCfg<C>::THREADS, 2) k_predictor_tcp(const __grid_constant__ StepArgs a) {
   using Ph = Phys<C::PDE, C::D>;
   using G = TpCfg<C>;
@@ -139,8 +158,16 @@ __global__ void __launch_bounds__(TpCfg<C>::THREADS, 2) k_predictor_tcp(const __
   __shared__ __align__(8) uint64_t s_mbar;
   __shared__ uint32_t s_tmem, s_timeout;
   __shared__ float s_fc[3][C::V];
+  __shared__ uint32_t s_fmax[3];
   __shared__ double s_dt;
   if (a.sc->bad) return;
+  const bool per_cell_scale = a.per_cell_scale && std::is_same<E, __half>::value;
+  auto scale_from = [&](uint32_t bits) {  // 2^-floor(log2 max): scaled max in [1, 2)
+    if (!per_cell_scale) return 1.0f;
+    const int e = (int)((bits >> 23) & 0xFFu) - 127;
+    if (bits == 0u || e > 100 || e < -100) return 1.0f;
+    return __uint_as_float((uint32_t)(127 - e) << 23);
+  };
   const double dt = block_dt(a, 3, C::N, &s_dt);
 
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
@@ -165,10 +192,9 @@ __global__ void __launch_bounds__(TpCfg<C>::THREADS, 2) k_predictor_tcp(const __
         if (s == 0 && yi == yo) val = a.tab.fD[xo][xi] * ihx;
         if (s == 1 && xi == xo) val = a.tab.fD[yo][yi] * ihy;
       }
-      const __nv_bfloat16 hi = __float2bfloat16_rn(val);
-      const __nv_bfloat16 lo = __float2bfloat16_rn(val - __bfloat162float(hi));
-      *reinterpret_cast<__nv_bfloat16*>(Bxy + tcp::boff<G>(po, c)) = hi;
-      *reinterpret_cast<__nv_bfloat16*>(Bxy + G::BXY_BYTES + tcp::boff<G>(po, c)) = lo;
+      const float hi = tcp::round_e<E>(val);
+      *reinterpret_cast<E*>(Bxy + tcp::boff<G>(po, c)) = tcp::to_e<E>(hi);
+      *reinterpret_cast<E*>(Bxy + G::BXY_BYTES + tcp::boff<G>(po, c)) = tcp::to_e<E>(val - hi);
     }
   }
   if (tid == 0) {
@@ -187,7 +213,7 @@ __global__ void __launch_bounds__(TpCfg<C>::THREADS, 2) k_predictor_tcp(const __
   tc::fence_after();
   const uint32_t tmem = s_tmem;
   // A_z (block diagonal over a tile's groups, D / h_z, split hi + lo) into tensor memory: warps
-  // 0..3 write their lane quarter, two bf16 per 32-bit column (the lower K index in the low half)
+  // 0..3 write their lane quarter, two 16-bit values per 32-bit column (the lower K index in the low half)
   if (warp < 4) {
     const int r = warp * 32 + lane;
     const float ihz = (float)a.invh[2];
@@ -205,10 +231,10 @@ __global__ void __launch_bounds__(TpCfg<C>::THREADS, 2) k_predictor_tcp(const __
             const int K = 2 * (c0 + j) + h;
             float val = 0.0f;
             if (r < G::RT && K < G::RT && r / n == K / n) val = a.tab.fD[r % n][K % n] * ihz;
-            const float hi = __bfloat162float(__float2bfloat16_rn(val));
+            const float hi = tcp::round_e<E>(val);
             v2[h] = part == 0 ? hi : val - hi;
           }
-          w[j] = tcp::bf2(v2[0], v2[1]);
+          w[j] = tcp::pack2<E>(v2[0], v2[1]);
         }
         tcp::st16(tmem + tl + (uint32_t)((part == 0 ? G::AZ_HI : G::AZ_LO) + c0), w);
       }
@@ -220,9 +246,10 @@ __global__ void __launch_bounds__(TpCfg<C>::THREADS, 2) k_predictor_tcp(const __
   __syncthreads();
   tc::fence_after();
 
-  // instruction descriptors: FP32 accumulator, bf16 A and B, M = 128, N = NCOL; B K-major (x-y)
-  // or MN-major (z)
-  const uint32_t idesc_xy = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NCOL >> 3) << 17) | ((128u >> 4) << 24);
+  // instruction descriptors: FP32 accumulator, A and B of type E, M = 128, N = NCOL; B K-major
+  // (x-y) or MN-major (z)
+  const uint32_t idesc_xy = (1u << 4) | (tc::In<E>::fmt << 7) | (tc::In<E>::fmt << 10) | ((uint32_t)(NCOL >> 3) << 17) |
+                            ((128u >> 4) << 24);
   const uint32_t idesc_z = idesc_xy | (1u << 16);
   const uint32_t smem_base = tc::smem_u32(tp_smem);
   auto launder = [](uint32_t x) {
@@ -273,8 +300,20 @@ __global__ void __launch_bounds__(TpCfg<C>::THREADS, 2) k_predictor_tcp(const __
       for (int d = 0; d < 3; ++d)
 #pragma unroll
         for (int v = 0; v < V; ++v) s_fc[d][v] = F[d][v];
+      s_fmax[0] = s_fmax[1] = s_fmax[2] = 0u;
     }
     __syncthreads();
+    if (per_cell_scale) {  // the first sweep's scale: max |F(Q) - F_c| over the cell
+      float F[3][V];
+      Ph::flux(pp, Qh, F);
+      float m = 0.0f;
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int v = 0; v < V; ++v) m = fmaxf(m, fabsf(F[d][v] - s_fc[d][v]));
+      atomicMax(&s_fmax[2], __float_as_uint(m));
+      __syncthreads();
+    }
     float q[n][V];
 #pragma unroll
     for (int k = 0; k < n; ++k)
@@ -284,7 +323,12 @@ __global__ void __launch_bounds__(TpCfg<C>::THREADS, 2) k_predictor_tcp(const __
     for (int r = 0; r < a.picard_iters && !stop; ++r) {
       const bool comp = r >= a.picard_iters - a.comp_sweeps;
       const bool first = r == 0;
+      // the scale of this sweep (from the previous one's fluxes); slot r % 3 collects this
+      // sweep's maximum, slot (r + 1) % 3 is cleared for the next
+      const float scF = scale_from(s_fmax[(r + 2) % 3]);
+      if (tid == 0) s_fmax[(r + 1) % 3] = 0u;
       for (int pass = 0; pass < (comp ? 2 : 1); ++pass) {
+        float fmx = 0.0f;
         // ---- fluxes into the operands: A_xy word (F_x, F_y) and B_z value F_z per (k, v) ------
         // the final stage and the exchange buffer overwrite the zero columns of A_xy's K padding:
         // clear them (every row the MMAs read for live accumulator rows)
@@ -303,16 +347,22 @@ __global__ void __launch_bounds__(TpCfg<C>::THREADS, 2) k_predictor_tcp(const __
           for (int v = 0; v < V; ++v) {
             const int g = k * V + v, tile = g / G::GPT, gl = g % G::GPT, row = gl * n + iz;
             float fx = F[0][v] - s_fc[0][v], fy = F[1][v] - s_fc[1][v], fz = F[2][v] - s_fc[2][v];
-            if (pass == 1) {
-              fx = tcp::lo_part(fx);
-              fy = tcp::lo_part(fy);
-              fz = tcp::lo_part(fz);
+            if (per_cell_scale) {
+              if (pass == 0) fmx = fmaxf(fmx, fmaxf(fabsf(fx), fmaxf(fabsf(fy), fabsf(fz))));
+              fx *= scF;
+              fy *= scF;
+              fz *= scF;
             }
-            *reinterpret_cast<uint32_t*>(Abuf + tile * G::A_TILE + tcp::aoff<G>(row, 2 * p)) = tcp::bf2(fx, fy);
-            *reinterpret_cast<__nv_bfloat16*>(Zbuf + tile * G::Z_TILE + tcp::zoff<G>(row, p)) =
-                __float2bfloat16_rn(fz);
+            if (pass == 1) {
+              fx = tcp::lo_part<E>(fx);
+              fy = tcp::lo_part<E>(fy);
+              fz = tcp::lo_part<E>(fz);
+            }
+            *reinterpret_cast<uint32_t*>(Abuf + tile * G::A_TILE + tcp::aoff<G>(row, 2 * p)) = tcp::pack2<E>(fx, fy);
+            *reinterpret_cast<E*>(Zbuf + tile * G::Z_TILE + tcp::zoff<G>(row, p)) = tcp::to_e<E>(fz);
           }
         }
+        if (per_cell_scale && pass == 0) atomicMax(&s_fmax[r % 3], __float_as_uint(fmx));
         tc::fence_async_smem();
         tc::fence_before();
         __syncthreads();
@@ -333,10 +383,10 @@ __global__ void __launch_bounds__(TpCfg<C>::THREADS, 2) k_predictor_tcp(const __
 #pragma unroll
             for (int ks = 0; ks < G::KXY / 16; ++ks) {
               const uint64_t ad = tc::sdesc(ab + (uint32_t)(ks * 2 * G::LBO_A), G::LBO_A, G::SBO_A);
-              tc::mma<__nv_bfloat16>(d, ad, tc::sdesc(bh + (uint32_t)(ks * 256), 128, (G::KXY / 8) * 128), idesc_xy,
+              tc::mma<E>(d, ad, tc::sdesc(bh + (uint32_t)(ks * 256), 128, (G::KXY / 8) * 128), idesc_xy,
                                      (pass > 0 || ks > 0) ? 1u : 0u);
               if (comp && pass == 0)
-                tc::mma<__nv_bfloat16>(d, ad, tc::sdesc(bl + (uint32_t)(ks * 256), 128, (G::KXY / 8) * 128),
+                tc::mma<E>(d, ad, tc::sdesc(bl + (uint32_t)(ks * 256), 128, (G::KXY / 8) * 128),
                                        idesc_xy, 1u);
             }
             const int kz = first ? 2 : (tile == TILES - 1 ? G::KZ_LAST / 16 : G::KZ / 16);
@@ -360,6 +410,7 @@ __global__ void __launch_bounds__(TpCfg<C>::THREADS, 2) k_predictor_tcp(const __
           const int lr = quarter * 32 + lane;
           const int rg = tile * G::RT + lr;  // row of the cell
           const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(tile * NCOL);
+          const float unscale = 1.0f / scF;  // (a power of two: exact)
 #pragma unroll
           for (int c0 = 0; c0 < NCOL; c0 += 16) {
             float o[16];
@@ -367,7 +418,7 @@ __global__ void __launch_bounds__(TpCfg<C>::THREADS, 2) k_predictor_tcp(const __
             if (lr < rows_t) {
 #pragma unroll
               for (int j = 0; j < 16; ++j)
-                if (c0 + j < NP) Rs[(c0 + j) * G::PS + rg] = o[j];
+                if (c0 + j < NP) Rs[(c0 + j) * G::PS + rg] = per_cell_scale ? o[j] * unscale : o[j];
             }
           }
         }
@@ -447,7 +498,7 @@ __global__ void __launch_bounds__(TpCfg<C>::THREADS, 2) k_predictor_tcp(const __
   }
 }
 
-template <class C, class TS, bool F64 = false>
+template <class C, class TS, bool F64 = false, class E = __nv_bfloat16>
 cudaError_t launch_predictor_tcp(const StepArgs& a, cudaStream_t s) {
   using G = TpCfg<C>;
   static_assert(G::TOTAL <= 113 * 1024, "two CTAs per SM");
@@ -457,7 +508,7 @@ cudaError_t launch_predictor_tcp(const StepArgs& a, cudaStream_t s) {
                 "the pencil-task final stage fits the sweep buffers");
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_predictor_tcp<C, TS, F64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_predictor_tcp<C, TS, F64, E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)G::TOTAL);
     if (e != cudaSuccess) return e;
     attr = true;
@@ -471,7 +522,7 @@ cudaError_t launch_predictor_tcp(const StepArgs& a, cudaStream_t s) {
     grid = 2 * sms;  // two CTAs per SM: tensor memory (256 columns each) and shared memory
   }
   const int blocks = a.ncells < grid ? a.ncells : grid;
-  k_predictor_tcp<C, TS, F64><<<blocks, G::THREADS, G::TOTAL, s>>>(a);
+  k_predictor_tcp<C, TS, F64, E><<<blocks, G::THREADS, G::TOTAL, s>>>(a);
   return cudaGetLastError();
 }
 
