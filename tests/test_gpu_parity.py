@@ -292,12 +292,16 @@ P32 = {"picard": "fp32", "predictor": "fp32"}
 ALL32 = {"picard": "fp32", "predictor": "fp32", "riemann": "fp32", "corrector": "fp32"}
 # bf16 tensor-core sweeps (two compensated), FP32 final stage, Riemann and corrector
 TC16 = {"picard": "bf16", "predictor": "fp32", "riemann": "fp32", "corrector": "fp32"}
+# fp16 tensor-core sweeps (per-cell scale, compensated last sweep)
+TCH = {"picard": "fp16", "predictor": "fp32", "riemann": "fp32", "corrector": "fp32"}
+# bf16 tensor-core sweeps with the final stage, Riemann and corrector in FP64
+TC16F64 = {"picard": "bf16", "predictor": "fp64", "riemann": "fp64", "corrector": "fp64"}
 FULL = [
     (I.euler3d_wave(), [("fp64", P64, 0, 1e-12), ("fp32", P32, 0, 1e-5), ("fp32 all", ALL32, 0, 1e-5),
-                        ("bf16tc", TC16, 4, 1e-5)]),
+                        ("bf16tc", TC16, 4, 1e-5), ("fp16tc", TCH, 3, 1e-5), ("bf16tc64", TC16F64, 4, 1e-5)]),
     (I.elastic3d_planar(), [("fp32", P32, 0, 1e-5), ("fp32 all", ALL32, 0, 1e-5)]),
     (I.swe2d_modes(), [("fp64", P64, 0, 1e-12), ("fp32", P32, 0, 1e-5), ("fp32 all", ALL32, 0, 1e-5)]),
-    (I.acoustic3d_pulse(), [("fp64", P64, 0, 1e-12)]),
+    (I.acoustic3d_pulse(), [("fp64", P64, 0, 1e-12), ("fp32 all", ALL32, 0, 1e-5)]),
 ]
 
 
