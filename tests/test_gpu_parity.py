@@ -307,14 +307,23 @@ FULL = [
 
 @pytest.mark.parametrize("wl,precs", FULL, ids=[w.name for w, _ in FULL])
 def test_full_size_sampled_cells_match_oracle(adg, oracle_mod, wl, precs):
-    """One step at the benchmark's full size and launch configuration; 16 sampled cells (the first,
-    the last and 14 seeded ones) against the oracle's step of those cells."""
+    """One step at the benchmark's full size and launch configuration; up to 20 sampled cells (the
+    first, the last, 14 seeded ones and the 4 of largest norm) against the oracle's step of those
+    cells."""
     M = oracle_mod.Mesh(wl.dim, wl.N, wl.cells, wl.pde, wl.params, cfl=wl.cfl)
     Q0 = M.interpolate(wl.scenario, wl.sp)
     dt = M.dt(Q0)
     rng = np.random.default_rng(11)
-    ids = np.unique(np.concatenate([[0, M.ncells - 1], rng.integers(0, M.ncells, size=14)]))
+    norms = np.sqrt(np.sum(Q0 ** 2, axis=(1, 2)))
+    ids = np.unique(np.concatenate([[0, M.ncells - 1], rng.integers(0, M.ncells, size=14),
+                                    np.argsort(norms)[-4:]]))
     ref = M.step_cells(Q0, dt, ids)
+    # The low-precision mixes are held to a relative tolerance of the solution, not of a cell far
+    # out in a decaying tail: a cell is measured against the larger of its own norm and 1e-3 of
+    # the largest cell norm of the state (the pulse's tail falls by orders of magnitude across one
+    # cell, so that rounding there is relative to the larger values of the cell's stencil, and far
+    # out its values lie below the normal range of FP32)
+    floor = 1e-3 * norms.max()
     for name, prec, flags, tol in precs:
         s = adg.Solver(wl.dim, wl.N, wl.cells, wl.pde, wl.params, cfl=wl.cfl, precision=prec, flags=flags)
         s.set_state(Q0, 0.0)
@@ -322,7 +331,7 @@ def test_full_size_sampled_cells_match_oracle(adg, oracle_mod, wl, precs):
         assert abs(dtg - dt) <= 1e-15 * dt
         Qg = s.Q[torch.from_numpy(ids).cuda()].cpu().numpy()
         for j in range(len(ids)):
-            err = np.sqrt(np.sum((Qg[j] - ref[j]) ** 2)) / np.sqrt(np.sum(ref[j] ** 2))
+            err = np.sqrt(np.sum((Qg[j] - ref[j]) ** 2)) / max(np.sqrt(np.sum(ref[j] ** 2)), floor)
             if name == "fp64":
                 assert np.abs(Qg[j] - ref[j]).max() <= tol * np.abs(ref[j]).max(), (ids[j], err)
             else:
