@@ -317,6 +317,14 @@ template <class C> struct UseFinalPt {
   static constexpr bool value = !(C::PDE == 1 && C::D == 3);
 };
 
+// The Cauchy-Kowalevskaya levels in pencil-task form (FP32, where the two task regions fit the
+// node-by-node form's sweep buffers, so that the shared memory size stays that form's).
+template <class C, class T> struct UseCkPt {
+  static constexpr bool value =
+      UsePencilTasks<C, T>::value &&
+      (size_t)C::CPB * PencilTasks<C>::CELL <= (size_t)C::CPB * C::D * C::VX * Pencil<C>::PER_DIR;
+};
+
 // Blocks per SM the predictor asks the register allocator for (0: the compiler's own choice, as
 // without the bound; an explicit 1 made it take more registers).  The direction-slot tasks of the
 // x pencil-major layout (3D Euler N=5) take 109 registers unconstrained (2 blocks of 216 threads
@@ -1120,7 +1128,54 @@ __global__ void __launch_bounds__(C::THREADS, PredMinBlocks<C, T, CK>::value) k_
 
   __syncthreads();
   int buf = 0;
-  if constexpr (CK) {
+  if constexpr (CK && UseCkPt<C, T>::value) {
+    // d_t^m Q of this node, and q_k += (xi_k dt)^m / m! d_t^m Q for m = 1..N, the spatial
+    // derivatives of each level in the pencil-task form of the Picard sweeps (the node writes its
+    // fluxes, the tasks differentiate whole pencils, the node reads its derivatives back): two
+    // barriers per level, the levels being sequential
+    using L = PencilTasks<C>;
+    T* const sF = reinterpret_cast<T*>(smem_raw);
+    T* const sR = sF + (size_t)CPB * L::CELL;
+    int off[D], tb[L::NSLOT];
+    T ih[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      off[d] = L::node_off(idx, d);
+      ih[d] = conv<T>(a.invh[d]);
+    }
+#pragma unroll
+    for (int j = 0; j < L::NSLOT; ++j) tb[j] = L::task_base(j);
+    const int cF = lc * L::CELL;
+    T dq[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) dq[v] = Qh[v];
+#pragma unroll 1
+    for (int m = 1; m <= C::N; ++m) {
+      {
+        T F[D][V];
+        Ph::flux(pp, dq, F);
+#pragma unroll
+        for (int d = 0; d < D; ++d)
+#pragma unroll
+          for (int v = 0; v < V; ++v)
+            if (Ph::nz(d, v)) sF[cF + L::cidx(d, v) * L::CS + off[d]] = F[d][v];
+      }
+      __syncthreads();
+      pencil_tasks<C, T>(sF, sR, a.tab, tb);
+      __syncthreads();
+      const T* fac = sdtP + m * n;
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        T rv = T(0);
+#pragma unroll
+        for (int d = 0; d < D; ++d)
+          if (Ph::nz(d, v)) rv = fmaf(ih[d], sR[cF + L::cidx(d, v) * L::CS + off[d]], rv);
+        dq[v] = -rv;
+#pragma unroll
+        for (int k = 0; k < n; ++k) q[k][v] += fac[k] * dq[v];
+      }
+    }
+  } else if constexpr (CK) {
     // d_t^m Q of this node, and q_k += (xi_k dt)^m / m! d_t^m Q for m = 1..N
     T dq[V];
 #pragma unroll
