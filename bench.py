@@ -531,7 +531,7 @@ def main():
     ap.add_argument("--adjoint", action="store_true", help="also time the adjoint (acoustics)")
     ap.add_argument("--nsnap", type=int, default=10)
     ap.add_argument("--headline", default="fp32")
-    ap.add_argument("--second", default="elastic3d:fp64,fp32,fp16tc,fp8tc;swe2d:fp64,fp32;acoustic3d:fp64,fp32,fp32ck",
+    ap.add_argument("--second", default="elastic3d:fp64,fp32,fp16tc,fp8tc,fp64ck,fp32ck;swe2d:fp64,fp32;acoustic3d:fp64,fp32,fp32ck",
                     help="further workload blocks of the default run, 'name:mix,mix;...' ('' for none)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
