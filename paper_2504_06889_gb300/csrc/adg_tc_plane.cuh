@@ -259,11 +259,12 @@ __global__ void __launch_bounds__(TpCfg<C>::THREADS, 2) k_predictor_tcp(const __
   };
   uint32_t phase = 0;
   bool stop = false;
+  // every thread waits for the MMA round itself (no block barrier): the readers then load their
+  // rows, and before a compensation pass every thread knows that the operands are free again; a
+  // wait that runs out is seen by all at the next barrier
   auto wait_mma = [&]() {
-    if (tid == 0 && !tc::wait_parity(&s_mbar, phase)) atomicOr(&s_timeout, 1u);
+    if (!tc::wait_parity(&s_mbar, phase)) atomicOr(&s_timeout, 1u);
     phase ^= 1u;
-    tc::fence_before();
-    __syncthreads();
     tc::fence_after();
   };
   // pencil-task geometry of the final stage
