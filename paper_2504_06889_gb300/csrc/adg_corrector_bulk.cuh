@@ -80,10 +80,13 @@ __global__ void __launch_bounds__(C::THREADS, MINB) k_corrector_bulk(const __gri
   static_assert(std::is_same<TS, float>::value || std::is_same<TS, double>::value, "bulk corrector: FP32 or FP64 traces");
   // face speeds are non-negative, so their bit patterns order like their values
   using Key = typename std::conditional<std::is_same<TS, double>::value, unsigned long long, unsigned>::type;
+  // FP64 face speeds of a nonlinear PDE (division and square root in FP64) through FP32 estimates
+  constexpr bool kEst = std::is_same<TS, double>::value && !Ph::linear;
   extern __shared__ __align__(128) unsigned char cb_smem[];
   __shared__ __align__(8) uint64_t s_tbar[NT], s_qbar[NQ];
   __shared__ unsigned long long s_lam;
   __shared__ unsigned int s_bad, s_last, s_l32, s_timeout;
+  __shared__ unsigned int s_face32[2 * C::D];  // (FP64 traces) running maximum FP32 face speed
   __shared__ double s_dt;
   if (a.sc->bad) return;
   const int tid = threadIdx.x, i = tid, warp = tid >> 5, lane = tid & 31;
@@ -97,7 +100,10 @@ __global__ void __launch_bounds__(C::THREADS, MINB) k_corrector_bulk(const __gri
     for (int s = 0; s < NQ; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(&s_qbar[s])));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
-  if (tid < 2 * D) sSmax[tid] = 0;
+  if (tid < 2 * D) {
+    sSmax[tid] = 0;
+    s_face32[tid] = 0u;
+  }
   TC* sG = reinterpret_cast<TC*>(cb_smem + L::G_OFF);
   TC* sCoef = reinterpret_cast<TC*>(cb_smem + L::COEF_OFF);
   for (int t = tid; t < 2 * D * n; t += blockDim.x) {
@@ -182,6 +188,13 @@ __global__ void __launch_bounds__(C::THREADS, MINB) k_corrector_bulk(const __gri
       const int it = base + i;
       int f = 2 * D;  // (no face)
       Key sbits = 0;
+      // (FP64 traces: the FP32 estimates of the two speeds, whether each is unreliable, and the
+      // node's two states)
+      float em = 0.0f, ep = 0.0f;
+      unsigned e32 = 0u;
+      bool rm = false, rp = false;
+      double qm64[kEst ? V : 1], qp64[kEst ? V : 1];
+      int nb64 = 0;
       if (it < 2 * D * NF) {
         const int j = it % NF;
         f = it / NF;
@@ -194,18 +207,66 @@ __global__ void __launch_bounds__(C::THREADS, MINB) k_corrector_bulk(const __gri
           qm[v] = tm[v * NF + j];
           qp[v] = tp[v * NF + j];
         }
-        const PP<TR> ppN = make_pp<TR>(a.pp, neighbour(a, cell, dir, side));
-        const TR sm = side ? Ph::speed(ppL, qm, dir) : Ph::speed(ppN, qm, dir);
-        const TR sp = side ? Ph::speed(ppN, qp, dir) : Ph::speed(ppL, qp, dir);
-        const TR smax = tmax(sm, sp);
-        if constexpr (std::is_same<TS, double>::value)
-          sbits = (Key)__double_as_longlong(smax);
-        else
-          sbits = __float_as_uint(smax);
+        const int nb = neighbour(a, cell, dir, side);
+        if constexpr (kEst) {
+          // FP32 estimates of both speeds first; the FP64 ones only where they can be the face's
+          // maximum (below)
+          float qmf[V], qpf[V];
+#pragma unroll
+          for (int v = 0; v < V; ++v) {
+            qmf[v] = f64_to_f32_rn(qm[v]);
+            qpf[v] = f64_to_f32_rn(qp[v]);
+          }
+          const PP<float> pLf = make_pp<float>(a.pp, cell), pNf = make_pp<float>(a.pp, nb);
+          em = side ? Ph::speed(pLf, qmf, dir) : Ph::speed(pNf, qmf, dir);
+          ep = side ? Ph::speed(pNf, qpf, dir) : Ph::speed(pLf, qpf, dir);
+          rm = !(em < 3.0e38f) || Ph::speed_is_ill_conditioned(qmf);
+          rp = !(ep < 3.0e38f) || Ph::speed_is_ill_conditioned(qpf);
+          e32 = __float_as_uint(fmaxf(rm ? 0.0f : em, rp ? 0.0f : ep)) & 0x7fffffffu;
+#pragma unroll
+          for (int v = 0; v < V; ++v) {
+            qm64[v] = qm[v];
+            qp64[v] = qp[v];
+          }
+          nb64 = nb;
+        } else {
+          const PP<TR> ppN = make_pp<TR>(a.pp, nb);
+          const TR sm = side ? Ph::speed(ppL, qm, dir) : Ph::speed(ppN, qm, dir);
+          const TR sp = side ? Ph::speed(ppN, qp, dir) : Ph::speed(ppL, qp, dir);
+          if constexpr (std::is_same<TS, double>::value)
+            sbits = (Key)__double_as_longlong(tmax(sm, sp)) & 0x7fffffffffffffffull;
+          else
+            sbits = __float_as_uint(tmax(sm, sp));
+        }
       }
       // the lanes of one face are consecutive: reduce over them, the lowest lane holds the result
       const unsigned same = __match_any_sync(wmask, f);
       Key m;
+      if constexpr (kEst) {
+        // the face's running maximum FP32 estimate (never above its final one): the exact FP64
+        // speed of a node side is evaluated only if its estimate is within 1e-4 of it, or
+        // unreliable; the FP32 relative error is far below 1e-4 for well-conditioned states, so
+        // the face's FP64 maximum is among the node sides evaluated
+        const unsigned g32 = __reduce_max_sync(same, e32);
+        const int leader = __ffs(same) - 1;
+        unsigned old = 0u;
+        if (f < 2 * D && lane == leader) old = atomicMax(&s_face32[f], g32);
+        old = __shfl_sync(wmask, old, leader);
+        const float thr = fmaxf(__uint_as_float(old), __uint_as_float(g32)) * (1.0f - 1.0e-4f);
+        if (f < 2 * D) {
+          const int dir = f / 2, side = f % 2;
+          double sv = 0.0;
+          if (rm || em >= thr) {
+            const PP<double> p = make_pp<double>(a.pp, side ? cell : nb64);
+            sv = fmax(sv, Ph::speed(p, qm64, dir));
+          }
+          if (rp || ep >= thr) {
+            const PP<double> p = make_pp<double>(a.pp, side ? nb64 : cell);
+            sv = fmax(sv, Ph::speed(p, qp64, dir));
+          }
+          sbits = (Key)__double_as_longlong(sv) & 0x7fffffffffffffffull;
+        }
+      }
       if constexpr (std::is_same<TS, double>::value) {
         const int last = 31 - __clz(same);
         m = sbits;
@@ -240,7 +301,10 @@ __global__ void __launch_bounds__(C::THREADS, MINB) k_corrector_bulk(const __gri
     }
     __syncthreads();  // B3: sG is complete; the trace stage and the face speeds are free
     if (tid == 0) {
-      for (int f = 0; f < 2 * D; ++f) sSmax[f] = 0;
+      for (int f = 0; f < 2 * D; ++f) {
+        sSmax[f] = 0;
+        s_face32[f] = 0u;
+      }
       issue_t(k + NT);
     }
     // surface integral and update: Q_i -= dt sum_dir (1/h)(psi1[i_dir] G+ - psi0[i_dir] G-)/w[i_dir]
