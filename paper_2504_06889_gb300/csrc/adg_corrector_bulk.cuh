@@ -13,7 +13,9 @@
 // the arithmetic.  Three barriers per cell: the per-face maximum speed is reduced within each warp
 // over the lanes of the same face and then by one shared atomic per face and warp, and the
 // candidates for the exact FP64 lambda are chosen against the block's running maximum estimate,
-// which needs no barrier (see below).
+// which needs no barrier (see below).  With FP64 traces of a nonlinear PDE the face speeds (FP64
+// division and square root) are chosen the same way: FP32 estimates of all, the FP64 value only
+// where it can be the face's maximum, which is therefore exactly the FP64 maximum of all.
 //
 // Copies complete an mbarrier (expected bytes); every wait is bounded (about one second of wall
 // time).  A wait that runs out records DevScalars::timeout, the block stops taking cells, waits

@@ -11,7 +11,6 @@ void register_euler() {
   {
     Entry e = make_entry<2, 3, 5, false>();
     add_tc<2, 3, 5>(e);
-    add_tcs<2, 5>(e);
     // bf16 and fp16: the plane form (all three directions of a sweep in one accumulator tile)
     e.predictor_tc[0][P32] = launch_predictor_tcp<Cfg<2, 3, 5>, float>;
     e.predictor_tc[0][P64] = launch_predictor_tcp<Cfg<2, 3, 5>, double>;
