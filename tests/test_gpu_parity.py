@@ -202,6 +202,48 @@ def test_anisotropic_box_fp32(adg, oracle_mod, wl, lo, hi):
     assert rel_l2(M, Qg, Qo) <= 1e-5
 
 
+def test_unreliable_speed_estimates_take_the_fp64_values(adg, oracle_mod):
+    """A fast, cold flow (|u| = 10, p = 0.01: the internal energy is 5e-4 of the total energy)
+    makes every FP32 speed estimate unreliable, so lambda and the FP64 face speeds are evaluated
+    in FP64 on every node.  FP64: the step matches the oracle elementwise and both steps' dt are
+    the oracle's; the FP32 mix: the second step's dt is the oracle's dt of the GPU's own state
+    after the first (lambda of the new state exact in FP64).  The oracle and the kernels form the
+    sound speed with a different order of operations; here the internal energy E - |m|^2/(2 rho)
+    cancels, which amplifies that rounding difference by E/(E - |m|^2/(2 rho)) (about 2000), and
+    the share c/lambda of the sound speed in lambda damps it (about 0.012): the dt comparisons
+    allow 1e-15 times that condition number (about 26 here)."""
+    from dataclasses import replace
+
+    wl = replace(I.euler3d_wave(N=5).with_cells((4, 3, 2), 2), sp=I.euler_wave(u=(10.0, 0.5, 0.2), p0=0.01))
+    M = oracle_mod.Mesh(wl.dim, wl.N, wl.cells, wl.pde, wl.params, cfl=wl.cfl)
+    Q0 = M.interpolate(wl.scenario, wl.sp)
+    dt0 = M.dt(Q0)
+    Q1 = Q0.copy()
+    M.step(Q1, dt0)  # (in place)
+
+    def cond(Q):
+        q = Q.transpose(0, 2, 1).reshape(-1, 5)
+        ke = 0.5 * np.sum(q[:, 1:4] ** 2, axis=1) / q[:, 0]
+        c = np.sqrt(1.4 * 0.4 * (q[:, 4] - ke) / q[:, 0])
+        lam = np.max(np.abs(q[:, 1:4]), axis=1) / q[:, 0] + c
+        return max(1.0, float(np.max(c / lam * q[:, 4] / (q[:, 4] - ke))))
+
+    f64 = {"picard": "fp64", "predictor": "fp64", "riemann": "fp64", "corrector": "fp64"}
+    f32 = {"picard": "fp32", "predictor": "fp32", "riemann": "fp32", "corrector": "fp32"}
+    for prec in (f64, f32):
+        s = adg.Solver(wl.dim, wl.N, wl.cells, wl.pde, wl.params, cfl=wl.cfl, precision=prec)
+        s.set_state(Q0, 0.0)
+        _, dtg = s.step(1)
+        assert abs(dtg - dt0) <= 1e-15 * cond(Q0) * dt0
+        Qg = s.state()
+        if prec is f64:
+            np.testing.assert_allclose(Qg, Q1, rtol=0, atol=1e-12 * np.abs(Q1).max())
+        _, dtg2 = s.step(1)
+        dt1 = M.dt(Qg)
+        assert abs(dtg2 - dt1) <= 1e-15 * cond(Qg) * dt1, (prec["picard"], dtg2, dt1)
+        s.close()
+
+
 def test_set_state_roundtrip_and_l2_diff(adg, oracle_mod):
     wl = I.euler3d_wave(N=5).with_cells((2, 2, 2))
     M = oracle_mod.Mesh(wl.dim, wl.N, wl.cells, wl.pde, wl.params, cfl=wl.cfl)
