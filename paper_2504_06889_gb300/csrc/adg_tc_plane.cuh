@@ -157,7 +157,8 @@ __global__ void __launch_bounds__(TpCfg<C>::THREADS, 2) k_predictor_tcp(const __
   extern __shared__ __align__(1024) unsigned char tp_smem[];
   __shared__ __align__(8) uint64_t s_mbar;
   __shared__ uint32_t s_tmem, s_timeout;
-  __shared__ float s_fc[3][C::V];
+  constexpr int NFC = (3 * C::V + 3) / 4 * 4;  // the flux offset F_c [dir * V + v], padded to float4
+  __shared__ __align__(16) float s_fc[NFC];
   __shared__ uint32_t s_fmax[3];
   __shared__ double s_dt;
   if (a.sc->bad) return;
@@ -300,7 +301,8 @@ __global__ void __launch_bounds__(TpCfg<C>::THREADS, 2) k_predictor_tcp(const __
 #pragma unroll
       for (int d = 0; d < 3; ++d)
 #pragma unroll
-        for (int v = 0; v < V; ++v) s_fc[d][v] = F[d][v];
+        for (int v = 0; v < V; ++v) s_fc[d * V + v] = F[d][v];
+      for (int j = 3 * V; j < NFC; ++j) s_fc[j] = 0.0f;
       s_fmax[0] = s_fmax[1] = s_fmax[2] = 0u;
     }
     __syncthreads();
@@ -311,7 +313,7 @@ __global__ void __launch_bounds__(TpCfg<C>::THREADS, 2) k_predictor_tcp(const __
 #pragma unroll
       for (int d = 0; d < 3; ++d)
 #pragma unroll
-        for (int v = 0; v < V; ++v) m = fmaxf(m, fabsf(F[d][v] - s_fc[d][v]));
+        for (int v = 0; v < V; ++v) m = fmaxf(m, fabsf(F[d][v] - s_fc[d * V + v]));
       atomicMax(&s_fmax[2], __float_as_uint(m));
       __syncthreads();
     }
@@ -344,10 +346,19 @@ __global__ void __launch_bounds__(TpCfg<C>::THREADS, 2) k_predictor_tcp(const __
           if (first && k > 0) break;
           float F[3][V];
           Ph::flux(pp, q[k], F);
+          float fc[NFC];  // F_c, in 16-byte loads
+#pragma unroll
+          for (int j = 0; j < NFC / 4; ++j) {
+            const float4 f4 = reinterpret_cast<const float4*>(s_fc)[j];
+            fc[4 * j] = f4.x;
+            fc[4 * j + 1] = f4.y;
+            fc[4 * j + 2] = f4.z;
+            fc[4 * j + 3] = f4.w;
+          }
 #pragma unroll
           for (int v = 0; v < V; ++v) {
             const int g = k * V + v, tile = g / G::GPT, gl = g % G::GPT, row = gl * n + iz;
-            float fx = F[0][v] - s_fc[0][v], fy = F[1][v] - s_fc[1][v], fz = F[2][v] - s_fc[2][v];
+            float fx = F[0][v] - fc[v], fy = F[1][v] - fc[V + v], fz = F[2][v] - fc[2 * V + v];
             if (per_cell_scale) {
               if (pass == 0) fmx = fmaxf(fmx, fmaxf(fabsf(fx), fmaxf(fabsf(fy), fabsf(fz))));
               fx *= scF;
