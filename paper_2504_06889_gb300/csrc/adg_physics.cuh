@@ -264,7 +264,14 @@ template <int D> struct Phys<2, D> {
     for (int dir = 0; dir < D; ++dir) {
       F[dir][0] = q[1 + dir];
 #pragma unroll
-      for (int a = 0; a < D; ++a) F[dir][1 + a] = q[1 + a] * u[dir];
+      for (int a = 0; a < D; ++a) {
+        // the momentum flux rho u_a u_dir is symmetric: in FP32 one product serves both
+        // entries (in FP64 each is formed as written, like the oracle's)
+        if (std::is_same<T, float>::value && a < dir)
+          F[dir][1 + a] = F[a][1 + dir];
+        else
+          F[dir][1 + a] = q[1 + a] * u[dir];
+      }
       F[dir][1 + dir] += pr;
       F[dir][1 + D] = u[dir] * Ep;
     }
