@@ -17,7 +17,8 @@
 // N = 5: two tiles, 126 + 54 rows).  Each accumulator row is read back by the thread of its lane
 // and exchanged through shared memory (R_s[p][r]: a conflict-free store by row and a
 // conflict-free load by plane position) to the thread that owns the node, which holds its whole
-// time column and applies dt P in FP32 registers.
+// time column and applies dt P in FP32 registers (with bf16 operands dt is part of the constant
+// operators, which then hold dt D / h, and the rows arrive as dt R).
 //
 // The derivative of a constant is zero, so the operands hold F - F_c, with F_c the flux at the
 // cell's first node (the 16-bit rounding applies to the variation of the flux over the cell).  In
@@ -182,8 +183,13 @@ __global__ void __launch_bounds__(TpCfg<C>::THREADS, 2) k_predictor_tcp(const __
 
   // ---- set-up: zero the operand buffers, the constant B_xy (hi, lo), barrier, tensor memory ---
   for (int t = tid; t < G::BXY_OFF / 16; t += blockDim.x) reinterpret_cast<uint4*>(tp_smem)[t] = make_uint4(0u, 0u, 0u, 0u);
+  // bf16 (the exponent range of FP32) takes dt into the constant operators, so that the rows come
+  // back as dt R; fp16 keeps the operators at D / h (dt D / h can fall below its normal range) and
+  // multiplies the rows by dt
+  constexpr bool kDtInOp = std::is_same<E, __nv_bfloat16>::value;
+  const float dt_op = kDtInOp ? (float)dt : 1.0f;
   {
-    const float ihx = (float)a.invh[0], ihy = (float)a.invh[1];
+    const float ihx = (float)a.invh[0] * dt_op, ihy = (float)a.invh[1] * dt_op;
     for (int e = tid; e < NCOL * G::KXY; e += blockDim.x) {
       const int po = e / G::KXY, c = e % G::KXY;
       float val = 0.0f;
@@ -217,7 +223,7 @@ __global__ void __launch_bounds__(TpCfg<C>::THREADS, 2) k_predictor_tcp(const __
   // 0..3 write their lane quarter, two 16-bit values per 32-bit column (the lower K index in the low half)
   if (warp < 4) {
     const int r = warp * 32 + lane;
-    const float ihz = (float)a.invh[2];
+    const float ihz = (float)a.invh[2] * dt_op;
     const uint32_t tl = (uint32_t)(warp * 32) << 16;
 #pragma unroll 1
     for (int part = 0; part < 2; ++part) {
@@ -444,7 +450,7 @@ __global__ void __launch_bounds__(TpCfg<C>::THREADS, 2) k_predictor_tcp(const __
         for (int v = 0; v < V; ++v) {
           const float R0 = Rs[p * G::PS + v * n + iz];
 #pragma unroll
-          for (int k = 0; k < n; ++k) q[k][v] = fmaf(-dtf * a.tab.fProw[k], R0, Qh[v]);
+          for (int k = 0; k < n; ++k) q[k][v] = fmaf(-(kDtInOp ? 1.0f : dtf) * a.tab.fProw[k], R0, Qh[v]);
         }
       } else {
         // the last sweep of the FP64 form keeps the correction (dt P R)_k, not the iterate
@@ -453,15 +459,30 @@ __global__ void __launch_bounds__(TpCfg<C>::THREADS, 2) k_predictor_tcp(const __
         for (int k = 0; k < n; ++k)
 #pragma unroll
           for (int v = 0; v < V; ++v) q[k][v] = keep_delta ? 0.0f : Qh[v];
-        const float sgn = keep_delta ? 1.0f : -1.0f;
+        // (dt R_l: the rows as they come back for bf16, times dt for fp16)
+        auto dtR = [&](int l, int v) {
+          const float R = Rs[p * G::PS + (l * V + v) * n + iz];
+          return kDtInOp ? R : dtf * R;
+        };
+        if (keep_delta) {
 #pragma unroll
-        for (int l = 0; l < n; ++l)
+          for (int l = 0; l < n; ++l)
 #pragma unroll
-          for (int v = 0; v < V; ++v) {
-            const float Rl = sgn * dtf * Rs[p * G::PS + (l * V + v) * n + iz];
+            for (int v = 0; v < V; ++v) {
+              const float Rl = dtR(l, v);
 #pragma unroll
-            for (int k = 0; k < n; ++k) q[k][v] = fmaf(a.tab.fP[k][l], Rl, q[k][v]);
-          }
+              for (int k = 0; k < n; ++k) q[k][v] = fmaf(a.tab.fP[k][l], Rl, q[k][v]);
+            }
+        } else {
+#pragma unroll
+          for (int l = 0; l < n; ++l)
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+              const float Rl = dtR(l, v);
+#pragma unroll
+              for (int k = 0; k < n; ++k) q[k][v] = fmaf(-a.tab.fP[k][l], Rl, q[k][v]);
+            }
+        }
       }
     }
     if (stop) break;
