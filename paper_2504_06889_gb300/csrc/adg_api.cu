@@ -180,6 +180,8 @@ bool build_tables(int n, Tables* T) {
     T->fpsi0[k] = (float)T->psi0[k];
     T->fpsi1[k] = (float)T->psi1[k];
   }
+  for (int l = 0; l < n; ++l)
+    for (int j = 0; j < n / 2; ++j) T->fPn2[l][j] = make_float2(-T->fP[2 * j][l], -T->fP[2 * j + 1][l]);
   for (int k = 0; k < n; ++k) {
     double r = 0.0;
     for (int l = 0; l < n; ++l) r += T->P[k][l];

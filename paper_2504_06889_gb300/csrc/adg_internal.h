@@ -27,6 +27,8 @@ struct Tables {
   float fDe[kMaxN1 / 2][kMaxN1 / 2], fDo[kMaxN1 / 2][kMaxN1 / 2];
   // the same pairs interleaved, {fDo[i][m], fDe[i][m]}, for two-lane FMAs
   float2 fDoe[kMaxN1 / 2][kMaxN1 / 2];
+  // column l of -P in time-node pairs, {-fP[2j][l], -fP[2j + 1][l]}, for two-lane FMAs
+  float2 fPn2[kMaxN1][kMaxN1 / 2];
   // row sums of P (the first Picard sweep, every time node at Q), summed in FP64
   float fProw[kMaxN1];
 };

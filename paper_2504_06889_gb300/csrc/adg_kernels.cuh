@@ -805,12 +805,25 @@ __device__ __forceinline__ void picard_pt(T (&q)[C::n][C::V], const T (&Qh)[C::V
     return rv;
   };
   // qn -= dt P[:, l] R_l (slice l's column of the time operator)
-  auto consume = [&](const T* sR, int l, T (&qn)[n][V]) {
+  // The new iterate keeps its time nodes in pairs (2j, 2j + 1): one two-lane FMA updates both
+  // with the pair (-P[2j][l], -P[2j + 1][l]), each lane as the scalar FMA would (an odd n keeps
+  // its last time node alone).
+  constexpr int NP2 = n / 2;
+  struct Iter {
+    float2 p[NP2][V];
+    float s[n % 2 ? V : 1];
+    __device__ __forceinline__ float get(int k, int v) const {
+      return (n % 2 == 1 && k == n - 1) ? s[v] : ((k % 2) ? p[k / 2][v].y : p[k / 2][v].x);
+    }
+  };
+  auto consume = [&](const T* sR, int l, Iter& qn) {
 #pragma unroll
     for (int v = 0; v < V; ++v) {
       const T drv = dt_deriv(sR, v);
+      const float2 d2 = make_float2(drv, drv);
 #pragma unroll
-      for (int kk = 0; kk < n; ++kk) qn[kk][v] = fmaf(-tab.fP[kk][l], drv, qn[kk][v]);
+      for (int j = 0; j < NP2; ++j) qn.p[j][v] = __ffma2_rn(tab.fPn2[l][j], d2, qn.p[j][v]);
+      if constexpr (n % 2 == 1) qn.s[v] = fmaf(-tab.fP[n - 1][l], drv, qn.s[v]);
     }
   };
   if (iters <= 0) return;
@@ -834,11 +847,13 @@ __device__ __forceinline__ void picard_pt(T (&q)[C::n][C::V], const T (&Qh)[C::V
   if (stop.end(0)) return;
   for (int r = 1; r < iters; ++r) {
     stop.begin(r);
-    T qn[n][V];
+    Iter qn;
 #pragma unroll
-    for (int k = 0; k < n; ++k)
+    for (int v = 0; v < V; ++v) {
 #pragma unroll
-      for (int v = 0; v < V; ++v) qn[k][v] = Qh[v];
+      for (int j = 0; j < NP2; ++j) qn.p[j][v] = make_float2(Qh[v], Qh[v]);
+      if constexpr (n % 2 == 1) qn.s[v] = Qh[v];
+    }
     write_slice(sF0, q[0]);
     __syncthreads();
 #pragma unroll
@@ -854,14 +869,14 @@ __device__ __forceinline__ void picard_pt(T (&q)[C::n][C::V], const T (&Qh)[C::V
 #pragma unroll
       for (int k = 0; k < n; ++k)
 #pragma unroll
-        for (int v = 0; v < V; ++v) ch = fmaxf(ch, fabsf(qn[k][v] - q[k][v]));
+        for (int v = 0; v < V; ++v) ch = fmaxf(ch, fabsf(qn.get(k, v) - q[k][v]));
       stop.record(r, lc, (double)ch);
     }
     if (!stop.frozen(lc)) {
 #pragma unroll
       for (int k = 0; k < n; ++k)
 #pragma unroll
-        for (int v = 0; v < V; ++v) q[k][v] = qn[k][v];
+        for (int v = 0; v < V; ++v) q[k][v] = qn.get(k, v);
     }
     if (stop.end(r)) return;
   }
