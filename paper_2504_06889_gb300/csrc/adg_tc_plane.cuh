@@ -453,36 +453,38 @@ __global__ void __launch_bounds__(TpCfg<C>::THREADS, 2) k_predictor_tcp(const __
           for (int k = 0; k < n; ++k) q[k][v] = fmaf(-(kDtInOp ? 1.0f : dtf) * a.tab.fProw[k], R0, Qh[v]);
         }
       } else {
-        // the last sweep of the FP64 form keeps the correction (dt P R)_k, not the iterate
+        // the last sweep of the FP64 form keeps the correction (dt P R)_k, not the iterate.  The
+        // time nodes go in pairs (2k, 2k + 1) through two-lane FMAs with the pair (-P[2k][l],
+        // -P[2k + 1][l]), each lane as the scalar FMA (+P R by negating R, which is exact)
         const bool keep_delta = F64 && r == a.picard_iters - 1;
+        static_assert(n % 2 == 0, "plane-form time operator: time-node pairs");
+        float2 qp[n / 2][V];
 #pragma unroll
-        for (int k = 0; k < n; ++k)
+        for (int j = 0; j < n / 2; ++j)
 #pragma unroll
-          for (int v = 0; v < V; ++v) q[k][v] = keep_delta ? 0.0f : Qh[v];
+          for (int v = 0; v < V; ++v) qp[j][v] = keep_delta ? make_float2(0.0f, 0.0f) : make_float2(Qh[v], Qh[v]);
         // (dt R_l: the rows as they come back for bf16, times dt for fp16)
         auto dtR = [&](int l, int v) {
           const float R = Rs[p * G::PS + (l * V + v) * n + iz];
           return kDtInOp ? R : dtf * R;
         };
-        if (keep_delta) {
+        const float rsign = keep_delta ? -1.0f : 1.0f;  // (exact)
 #pragma unroll
-          for (int l = 0; l < n; ++l)
+        for (int l = 0; l < n; ++l)
 #pragma unroll
-            for (int v = 0; v < V; ++v) {
-              const float Rl = dtR(l, v);
+          for (int v = 0; v < V; ++v) {
+            const float Rl = rsign * dtR(l, v);
+            const float2 r2 = make_float2(Rl, Rl);
 #pragma unroll
-              for (int k = 0; k < n; ++k) q[k][v] = fmaf(a.tab.fP[k][l], Rl, q[k][v]);
-            }
-        } else {
+            for (int j = 0; j < n / 2; ++j) qp[j][v] = __ffma2_rn(a.tab.fPn2[l][j], r2, qp[j][v]);
+          }
 #pragma unroll
-          for (int l = 0; l < n; ++l)
+        for (int j = 0; j < n / 2; ++j)
 #pragma unroll
-            for (int v = 0; v < V; ++v) {
-              const float Rl = dtR(l, v);
-#pragma unroll
-              for (int k = 0; k < n; ++k) q[k][v] = fmaf(-a.tab.fP[k][l], Rl, q[k][v]);
-            }
-        }
+          for (int v = 0; v < V; ++v) {
+            q[2 * j][v] = qp[j][v].x;
+            q[2 * j + 1][v] = qp[j][v].y;
+          }
       }
     }
     if (stop) break;
