@@ -310,8 +310,7 @@ ADG_API int adg_nvar(int pde, int dim);
  *    ADG_NOALLOC_SCRATCH_BYTES - 256; larger meshes return ADG_ENOMEM before any work;
  *  - every call looks up the array's device address on the current device
  *    (cudaGetSymbolAddress), so a device reset between calls is handled; the first call on a
- *    device also loads the library's device code there: make that first call before any stream
- *    capture;
+ *    device also loads the library's device code there;
  *  - all calls share the array and it keeps the last call's contents; each call clears the
  *    scalars it needs before using them.  Calls that overlap on the GPU (other streams or
  *    threads) race on the array: serialise them;
