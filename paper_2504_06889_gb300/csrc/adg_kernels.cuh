@@ -221,6 +221,21 @@ __host__ __device__ constexpr PtLayout pt_layout(int D, int n, int ncmb) {
                                             : PtLayout{0, 0, NP + 2, ((n - 1) * (NP + 2) + NP + 3) / 4 * 4};
 }
 
+// Thread order of the nodes of a cell (one cell per block) where the natural order makes the
+// node threads' accesses conflict: thread 32 w + l takes node l + 32 K, K the bits l of the
+// words 3 w, 3 w + 1 and 3 w + 2 (weights 1, 2, 4).  For 3D Euler at N = 5 (layout {1, 1, 36,
+// 228}) the x and z offsets of node t are congruent to t modulo 32, but the y offsets
+// (z + 6 x + 36 y) of a warp's 32 consecutive nodes meet up to three times on one bank (13
+// wavefronts per flux component instead of 7).  In this order every warp's nodes occupy 32
+// distinct banks in all three directions, which takes the bank model from 504 to 444 wavefronts
+// per cell and slice.  The words come from node_order in tests/pencil_layout_model.py (an edge
+// colouring of the bipartite graph of x and y banks); a CPU test parses them from here and
+// replays the accesses.
+static __constant__ unsigned kNodeOrderEuler3N5[21] = {
+    0x038f5820u, 0x0289b001u, 0x08008472u, 0xfcd05fdbu, 0x02026000u, 0x156d3896u, 0x4550a040u,
+    0xb1fdadadu, 0x400253c5u, 0xbc7c36e5u, 0xbd248efeu, 0x4210290bu, 0x5223629eu, 0x485e0178u,
+    0xa69cca21u, 0xabaf8d03u, 0x44005bd7u, 0xb9ffe678u, 0x0000813cu, 0x00f35602u, 0x00e3158cu};
+
 template <class C> struct PencilTasks {
   using Ph = Phys<C::PDE, C::D>;
   static constexpr int n = C::n, D = C::D, V = C::V, NP = C::NF;
@@ -253,6 +268,19 @@ template <class C> struct PencilTasks {
   // slot j holds task threadIdx.x + j THREADS of all of them.
   static_assert(!XPM || C::CPB * max_ncd() * NP <= C::THREADS, "x pencil-major needs one slot per direction");
   static constexpr int NSLOT = XPM ? D : (C::CPB * NT + C::THREADS - 1) / C::THREADS;
+  // node of thread t: the natural order, or kNodeOrderEuler3N5 for 3D Euler N=5
+  static constexpr bool NODE_ORDER = D == 3 && n == 6 && NCMB == 15;
+  static_assert(!NODE_ORDER || (C::CPB == 1 && C::NS == 216 && LAY.xpm == 1 && LAY.ord1 == 1 && LAY.MS == 36),
+                "the node order belongs to the layout it was built for");
+  __device__ static __forceinline__ int node_of_thread(int t) {
+    if constexpr (NODE_ORDER) {
+      const int w = t >> 5, l = t & 31;
+      const unsigned* k = kNodeOrderEuler3N5 + 3 * w;
+      return l + 32 * (int)(((k[0] >> l) & 1u) | (((k[1] >> l) & 1u) << 1) | (((k[2] >> l) & 1u) << 2));
+    } else {
+      return t % C::NS;
+    }
+  }
   // pencil of node (x, y, z) along d (its other coordinates)
   __device__ static __forceinline__ int pen(const int* idx, int d) {
     return d == 0 ? idx[1] + n * idx[2]
@@ -1083,7 +1111,11 @@ __global__ void __launch_bounds__(C::THREADS, PredMinBlocks<C, T, CK>::value) k_
     sdtProw[t] = dtT * rs;
   }
 
-  const int lc = threadIdx.x / NS, i = threadIdx.x % NS;
+  // the node of this thread (in the order of the pencil-task layout where that has one)
+  constexpr bool kLay = kPT || (CK && UseCkPt<C, T>::value);
+  const int lc = threadIdx.x / NS;
+  int i = threadIdx.x % NS;
+  if constexpr (kLay) i = PencilTasks<C>::node_of_thread(threadIdx.x);
   const int cell = blockIdx.x * CPB + lc;
   const bool valid = cell < a.ncells;
   const int cl = valid ? cell : 0;

@@ -86,16 +86,32 @@ class Config:
                 yield j, [((t // NT), (t % NT) // NP, t % NP) if t < CPB * NT else None
                           for t in (i + j * TH for i in range(TH))]
 
-    def count(self, lay):
+    def node_off(self, lay, i, d):
+        """Offset of node i inside a combo region of direction d (the kernel's node_off)."""
         xpm, ord1, MS, CS = lay
+        p, m = self.pencil(i, d, ord1)
+        return p * self.SF0 + m if (xpm and d == 0) else p + m * MS
+
+    def node_of(self, tid, order=None):
+        """Node of thread tid in its cell: the identity, or order[tid] (one cell per block)."""
+        return tid % self.NS if order is None else order[tid]
+
+    def count_nodes(self, lay, order=None):
+        """Wavefronts of the node threads' accesses, one flux component of each combo."""
+        ord1 = lay[1]
         node = 0
         for w in range(0, self.THREADS, 32):
             lanes = [w + l if w + l < self.THREADS else None for l in range(32)]
             for c in range(self.NC):
                 d = self.dir_of[c]
                 node += wavefronts32([None if t is None else
-                                      self.addr(lay, t // self.NS, c, *self.pencil(t % self.NS, d, ord1))
+                                      self.addr(lay, t // self.NS, c, *self.pencil(self.node_of(t, order), d, ord1))
                                       for t in lanes])
+        return node
+
+    def count(self, lay, order=None):
+        xpm, ord1, MS, CS = lay
+        node = self.count_nodes(lay, order)
         tasks = 0
         for j, tl in self.slots(lay):
             for w in range(0, self.THREADS, 32):
@@ -116,6 +132,75 @@ class Config:
                         tasks += wavefronts32([None if x is None else self.addr(lay, *x, m) for x in po])
         # fluxes and derivatives share the layout: stores and loads cost the same
         return 2 * (node + tasks)
+
+    def node_order(self, lay):
+        """A thread -> node order (one cell per block) in which the nodes of every warp fall in 32
+        distinct banks in every direction's region.  Node t goes to lane t mod 32, so a direction
+        whose node offset is congruent to t mod 32 is conflict-free in any such order; the one
+        other direction's offsets f(t) are handled as an edge colouring of the bipartite
+        multigraph with an edge (t mod 32, f(t) mod 32) per node: every warp takes a matching.
+        With W warps and r lanes in the last, residues below r have W nodes and the others W - 1;
+        when f's residues have W or W - 1 nodes as well, the last warp takes a perfect matching
+        of the W-node residues of both sides, after which the multigraph is (W - 1)-regular and
+        splits into W - 1 perfect matchings (Koenig's theorem), found one by one by augmenting
+        paths.  Among equal choices a node stays in its own warp.  Returns order (thread -> node)
+        or None when the layout is not of this kind."""
+        if self.CPB != 1 or self.D != 3:
+            return None
+        ord1 = lay[1]
+        NS = self.NS
+        offs = [[self.node_off(lay, t, d) for t in range(NS)] for d in range(self.D)]
+        other = [d for d in range(self.D) if any((offs[d][t] - t) % 32 for t in range(NS))]
+        if len(other) != 1:
+            return None
+        f = [o % 32 for o in offs[other[0]]]
+        W = (NS + 31) // 32
+        r = NS - 32 * (W - 1)
+        cnt = [f.count(b) for b in range(32)]
+        if any(c not in (W - 1, W) for c in cnt):
+            return None
+        edges = {}
+        for t in range(NS):
+            edges.setdefault((t % 32, f[t]), []).append(t)
+
+        def matching(w, left, right):
+            adj = {}
+            for a in left:
+                own = [b for b in right if any(t // 32 == w for t in edges.get((a, b), []))]
+                adj[a] = own + [b for b in right if edges.get((a, b)) and b not in own]
+            match = {}
+
+            def augment(a, seen):
+                for b in adj[a]:
+                    if b not in seen:
+                        seen.add(b)
+                        if b not in match or augment(match[b], seen):
+                            match[b] = a
+                            return True
+                return False
+
+            for a in left:
+                if not augment(a, set()):
+                    raise AssertionError("no perfect matching")
+            picked = []
+            for b, a in match.items():
+                ts = edges[(a, b)]
+                t = next((t for t in ts if t // 32 == w), ts[0])
+                ts.remove(t)
+                picked.append(t)
+            return picked
+
+        groups = [None] * W
+        groups[W - 1] = matching(W - 1, [a for a in range(32) if a < r],
+                                 [b for b in range(32) if cnt[b] == W])
+        for w in range(W - 1):
+            groups[w] = matching(w, list(range(32)), list(range(32)))
+        order = [None] * NS
+        for w, g in enumerate(groups):
+            for t in g:
+                order[32 * w + t % 32] = t
+        assert sorted(order) == list(range(NS))
+        return order
 
     def check(self, lay):
         """The kernel's index arithmetic for layout lay, replayed: every node writes its own slot

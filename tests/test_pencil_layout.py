@@ -2,8 +2,9 @@
 CPU: for every configuration the library builds, the shared-memory indices of the node threads and
 of the tasks stay inside their regions, every slot is written once, the tasks read exactly what the
 nodes write and write exactly what they read, and the 8-byte accesses are aligned.  The constants
-are parsed from the kernel source, so a change there is checked before it runs on a GPU.  The
-double-buffered phase schedule of picard_pt and the trace stores of the final stage
+are parsed from the kernel source, so a change there is checked before it runs on a GPU; so is
+the thread order of the 3D Euler N=5 nodes (kNodeOrderEuler3N5).  The double-buffered phase
+schedule of picard_pt and the trace stores of the final stage
 (predictor_final_pt) are replayed as well."""
 import importlib.util
 import os
@@ -66,6 +67,50 @@ def test_default_layout_indices(cfg):
 def test_pipelined_schedule(n, iters):
     # every read sees its slice; n + 1 barriers per sweep after the first (which takes 2)
     assert M.check_schedule(n, iters) == 2 + (iters - 1) * (n + 1)
+
+
+def node_order_words():
+    src = open(os.path.join(CSRC, "adg_kernels.cuh")).read()
+    body = re.search(r"kNodeOrderEuler3N5\[(\d+)\] = \{([^}]*)\}", src)
+    words = [int(w, 16) for w in re.findall(r"0x([0-9a-f]+)u", body.group(2))]
+    assert len(words) == int(body.group(1))
+    return words
+
+
+def kernel_node_order(cfg):
+    # node_of_thread: thread 32 w + l takes node l + 32 K, K the bits l of words 3 w .. 3 w + 2
+    words = node_order_words()
+    order = []
+    for t in range(cfg.NS):
+        w, l = t // 32, t % 32
+        K = sum(((words[3 * w + b] >> l) & 1) << b for b in range(3))
+        order.append(l + 32 * K)
+    return order
+
+
+def test_node_order_is_a_conflict_free_permutation():
+    # the kernel's thread order of the 3D Euler N=5 nodes: every node once, and every warp's node
+    # accesses in 32 distinct banks in all three directions (7 wavefronts per flux component)
+    cfg = [c for c in M.CONFIGS if c.name == "Euler 3D N=5"][0]
+    lay = TABLE[(cfg.D, cfg.n, cfg.NC)]
+    order = kernel_node_order(cfg)
+    assert sorted(order) == list(range(cfg.NS))
+    assert len(node_order_words()) == 3 * ((cfg.NS + 31) // 32)
+    assert cfg.count_nodes(lay) == 135  # the natural order: the y accesses meet on banks
+    assert cfg.count_nodes(lay, order) == cfg.NC * ((cfg.NS + 31) // 32) == 105
+    assert cfg.count(lay, order) == 444 and cfg.count(lay) == 504
+
+
+def test_node_order_construction():
+    # node_order of the model rebuilds a conflict-free order from the layout alone; the
+    # configurations whose offsets it cannot handle keep the natural order
+    cfg = [c for c in M.CONFIGS if c.name == "Euler 3D N=5"][0]
+    lay = TABLE[(cfg.D, cfg.n, cfg.NC)]
+    order = cfg.node_order(lay)
+    assert sorted(order) == list(range(cfg.NS)) and all(order[t] % 32 == t % 32 for t in range(cfg.NS))
+    assert cfg.count_nodes(lay, order) == 105
+    assert order == kernel_node_order(cfg)
+    assert cfg.node_order((1, 1, 38, 228)) is None  # y offsets with 8 nodes on some banks
 
 
 def test_a_wrong_stride_is_caught():
