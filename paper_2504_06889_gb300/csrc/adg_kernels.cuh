@@ -236,6 +236,24 @@ static __constant__ unsigned kNodeOrderEuler3N5[21] = {
     0xb1fdadadu, 0x400253c5u, 0xbc7c36e5u, 0xbd248efeu, 0x4210290bu, 0x5223629eu, 0x485e0178u,
     0xa69cca21u, 0xabaf8d03u, 0x44005bd7u, 0xb9ffe678u, 0x0000813cu, 0x00f35602u, 0x00e3158cu};
 
+// Thread order of the x tasks of the same layout: thread t takes task kXTaskOrderEuler3N5[t] of
+// the x direction (flux component t' / 36, pencil t' % 36) instead of task t.  In the natural
+// order a half-warp that straddles two flux components reads and writes its 8-byte values on the
+// same banks up to twice; here the 16 tasks of every half-warp fall in 16 distinct bank pairs
+// (x_task_order in tests/pencil_layout_model.py: the tasks grouped by bank pair, half-warp h
+// taking the h-th task of each group), which takes the bank model from 444 to 426 wavefronts per
+// cell and slice, the fewest for 7 warps of nodes and 6 of tasks per direction.
+static __constant__ unsigned char kXTaskOrderEuler3N5[180] = {
+    0, 11, 6, 1, 12, 7, 2, 13, 8, 3, 14, 9, 4, 15, 10, 5, 16, 27, 22, 17,
+    28, 23, 18, 29, 24, 19, 30, 25, 20, 31, 26, 21, 32, 41, 36, 33, 42, 37, 34, 43,
+    38, 35, 44, 39, 50, 45, 40, 51, 46, 57, 52, 47, 58, 53, 48, 59, 54, 49, 60, 55,
+    66, 61, 56, 67, 62, 87, 68, 63, 72, 69, 64, 73, 70, 65, 74, 71, 80, 75, 86, 81,
+    76, 103, 82, 77, 88, 83, 78, 89, 84, 79, 90, 85, 96, 91, 102, 97, 92, 117, 98, 93,
+    104, 99, 94, 105, 100, 95, 106, 101, 110, 107, 116, 111, 122, 133, 112, 123, 118, 113, 108, 119,
+    114, 109, 120, 115, 126, 121, 132, 127, 138, 147, 128, 139, 134, 129, 124, 135, 130, 125, 136, 131,
+    142, 137, 146, 143, 152, 163, 158, 153, 148, 159, 140, 149, 144, 141, 150, 145, 156, 151, 162, 157,
+    168, 179, 174, 169, 164, 175, 154, 165, 160, 155, 166, 161, 172, 167, 178, 173, 170, 176, 171, 177};
+
 template <class C> struct PencilTasks {
   using Ph = Phys<C::PDE, C::D>;
   static constexpr int n = C::n, D = C::D, V = C::V, NP = C::NF;
@@ -268,10 +286,14 @@ template <class C> struct PencilTasks {
   // slot j holds task threadIdx.x + j THREADS of all of them.
   static_assert(!XPM || C::CPB * max_ncd() * NP <= C::THREADS, "x pencil-major needs one slot per direction");
   static constexpr int NSLOT = XPM ? D : (C::CPB * NT + C::THREADS - 1) / C::THREADS;
-  // node of thread t: the natural order, or kNodeOrderEuler3N5 for 3D Euler N=5
+  // node of thread t: the natural order, or kNodeOrderEuler3N5 for 3D Euler N=5 (whose x tasks
+  // also take their thread order from kXTaskOrderEuler3N5 in task_of and task_base with XO = true;
+  // the persistent plane-form tensor-core kernel keeps the natural order, XO = false, which
+  // measured 2 % faster there)
   static constexpr bool NODE_ORDER = D == 3 && n == 6 && NCMB == 15;
-  static_assert(!NODE_ORDER || (C::CPB == 1 && C::NS == 216 && LAY.xpm == 1 && LAY.ord1 == 1 && LAY.MS == 36),
-                "the node order belongs to the layout it was built for");
+  static_assert(!NODE_ORDER || (C::CPB == 1 && C::NS == 216 && LAY.xpm == 1 && LAY.ord1 == 1 && LAY.MS == 36 &&
+                                 LAY.CS == 228 && ncd(0) * NP == 180),
+                "the node and x task orders belong to the layout they were built for");
   __device__ static __forceinline__ int node_of_thread(int t) {
     if constexpr (NODE_ORDER) {
       const int w = t >> 5, l = t & 31;
@@ -292,12 +314,14 @@ template <class C> struct PencilTasks {
   }
   // cell (of the block), combo and pencil of this thread's task in slot j (the task of
   // task_base(j)); false if the slot is empty
+  template <bool XO = true>
   __device__ static __forceinline__ bool task_of(int j, int* cl, int* c, int* p) {
     if constexpr (XPM) {
       const int t = threadIdx.x, nt = ncd(j) * NP;
       if (t >= C::CPB * nt) return false;
       *cl = t / nt;
-      const int r = t - *cl * nt;
+      int r = t - *cl * nt;
+      if (XO && NODE_ORDER && j == 0) r = kXTaskOrderEuler3N5[t];  // one cell per block
       *c = cidx(j, 0) + r / NP;
       *p = r % NP;
     } else {
@@ -326,9 +350,10 @@ template <class C> struct PencilTasks {
     return (d == 1 && LAY.ord1) ? p / n + n * (p % n) : p;
   }
   // offset of this thread's task in slot j in either region (its first value), -1 if none
+  template <bool XO = true>
   __device__ static __forceinline__ int task_base(int j) {
     int cl, c, p;
-    if (!task_of(j, &cl, &c, &p)) return -1;
+    if (!task_of<XO>(j, &cl, &c, &p)) return -1;
     return cl * CELL + c * CS + ((XPM && j == 0) ? p * SF0 : p);
   }
 };
@@ -942,8 +967,9 @@ __device__ __forceinline__ void final_task(const T* f, T* o, const Tables& tab, 
 // volume integral to Q in FP64.  The Fbar tasks are the sweeps' (tb); the Qbar tasks are numbered
 // by face node, so their trace stores are contiguous.  sbuf: the pencil-task regions (Fbar in
 // the first, Qbar [cell][v][node] in the second, Vm Fbar in the third); cell0: the mesh cell of
-// the block's first cell slot (lc = 0).
-template <class C, class T, class TS, class TQ>
+// the block's first cell slot (lc = 0); XO: the thread order of the x tasks that tb was built
+// with (PencilTasks::task_base).
+template <class C, class T, class TS, class TQ, bool XO = true>
 __device__ __forceinline__ void predictor_final_pt(const StepArgs& a, const T (*q)[C::V], T* sbuf, const PP<T>& pp,
                                                    const T (&ih)[C::D], double dt, int lc, int i, int cell,
                                                    bool valid, const int (&off)[C::D], int cF,
@@ -988,7 +1014,7 @@ __device__ __forceinline__ void predictor_final_pt(const StepArgs& a, const T (*
 #pragma unroll
   for (int j = 0; j < L::NSLOT; ++j) {
     int tcl, c, p;
-    if (!L::task_of(j, &tcl, &c, &p)) continue;
+    if (!L::template task_of<XO>(j, &tcl, &c, &p)) continue;
     T s0, s1;
     if (L::XPM && j == 0)
       final_task<n, 1>(sFb + tb[j], sVo + tb[j], a.tab, &s0, &s1);

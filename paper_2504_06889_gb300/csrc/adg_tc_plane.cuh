@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(TpCfg<C>::THREADS, 2) k_predictor_tcp(const __
     ih[d] = (float)a.invh[d];
   }
 #pragma unroll
-  for (int j = 0; j < L::NSLOT; ++j) tb[j] = L::task_base(j);
+  for (int j = 0; j < L::NSLOT; ++j) tb[j] = L::template task_base<false>(j);  // natural task order
   const float dtf = (float)dt;
 
   // ---- persistent loop over the cells --------------------------------------------------------
@@ -512,7 +512,7 @@ __global__ void __launch_bounds__(TpCfg<C>::THREADS, 2) k_predictor_tcp(const __
                                                              sp0, sp1, dt, 0, i, cell, true, cell, idx, pb, true);
       }
     } else {
-      predictor_final_pt<C, float, TS, double>(a, q, reinterpret_cast<float*>(tp_smem), pp, ih, dt, 0, i, cell,
+      predictor_final_pt<C, float, TS, double, false>(a, q, reinterpret_cast<float*>(tp_smem), pp, ih, dt, 0, i, cell,
                                                true, off, 0, tb, cell);
     }
   }  // cells

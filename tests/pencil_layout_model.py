@@ -69,17 +69,20 @@ class Config:
         off = p * self.SF0 + m if (xpm and self.dir_of[c] == 0) else p + m * MS
         return cl * self.NC * CS + c * CS + off
 
-    def slots(self, lay):
+    def slots(self, lay, xorder=None):
         """Task slots as the kernel assigns them: with xpm, slot j holds the tasks of direction j
-        (thread i takes task i of that direction); otherwise slot j holds task i + j THREADS of the
-        combo-major list.  Yields (slot, [(cell, combo, pencil) or None per thread])."""
+        (thread i takes task i of that direction, or task xorder[i] of the x direction);
+        otherwise slot j holds task i + j THREADS of the combo-major list.  Yields (slot,
+        [(cell, combo, pencil) or None per thread])."""
         xpm = lay[0]
         NP, TH, CPB = self.NP, self.THREADS, self.CPB
         if xpm:
             for j in range(self.D):
                 combos = [c for c in range(self.NC) if self.dir_of[c] == j]
                 nt = len(combos) * NP
-                yield j, [(t // nt, combos[(t % nt) // NP], t % NP) if t < CPB * nt else None for t in range(TH)]
+                task = (lambda t: xorder[t]) if (j == 0 and xorder is not None) else (lambda t: t % nt)
+                yield j, [(t // nt, combos[task(t) // NP], task(t) % NP) if t < CPB * nt else None
+                          for t in range(TH)]
         else:
             NT = self.NC * NP
             for j in range((CPB * NT + TH - 1) // TH):
@@ -109,11 +112,11 @@ class Config:
                                       for t in lanes])
         return node
 
-    def count(self, lay, order=None):
+    def count(self, lay, order=None, xorder=None):
         xpm, ord1, MS, CS = lay
         node = self.count_nodes(lay, order)
         tasks = 0
-        for j, tl in self.slots(lay):
+        for j, tl in self.slots(lay, xorder):
             for w in range(0, self.THREADS, 32):
                 cp = tl[w:w + 32] + [None] * max(0, w + 32 - self.THREADS)
                 if all(x is None for x in cp):
@@ -202,7 +205,28 @@ class Config:
         assert sorted(order) == list(range(NS))
         return order
 
-    def check(self, lay):
+    def x_task_order(self, lay):
+        """A thread order of the x tasks (x pencil-major layouts, one cell per block, even n) in
+        which every half-warp's 8-byte accesses fall in 16 distinct bank pairs.  The pair of task
+        i is (its first value's word / 2) mod 16, the same for every position; if the H half-warps
+        of the x slot find every pair class of size H - 1 or H, half-warp h < H - 1 takes the h-th
+        task of each class (lane = class) and the last takes the last task of each class of size
+        H.  Returns order (thread -> task of the x direction) or None."""
+        if not lay[0] or self.CPB != 1 or self.n % 2:
+            return None
+        c0, NP = self.dir_of.index(0), self.NP
+        nt = self.dir_of.count(0) * NP
+        pair = [(self.addr(lay, 0, c0 + i // NP, i % NP, 0) // 2) % 16 for i in range(nt)]
+        classes = [[i for i in range(nt) if pair[i] == r] for r in range(16)]
+        H = (nt + 15) // 16
+        if any(len(k) not in (H - 1, H) for k in classes):
+            return None
+        order = [classes[t % 16][t // 16] for t in range(16 * (H - 1))]
+        order += [k[H - 1] for k in classes if len(k) == H]
+        assert sorted(order) == list(range(nt))
+        return order
+
+    def check(self, lay, xorder=None):
         """The kernel's index arithmetic for layout lay, replayed: every node writes its own slot
         of each flux component inside its cell's region; the tasks of all threads read exactly the
         slots the nodes write and write (once each) exactly the slots the nodes read; 8-byte task
@@ -235,6 +259,8 @@ class Config:
                     if tid >= CPB * nt:
                         continue
                     cl, r = tid // nt, tid % nt
+                    if j == 0 and xorder is not None:
+                        r = xorder[tid]
                     c, p = cstart[j] + r // NP, r % NP
                     base, stride = cl * CELL + c * CS + (p * self.SF0 if j == 0 else p), (1 if j == 0 else MS)
                     if j == 0 and n % 2 == 0:
@@ -268,7 +294,7 @@ class Config:
         n = self.n
         return p // n + n * (p % n) if (d == 1 and lay[1]) else p
 
-    def check_final(self, lay):
+    def check_final(self, lay, xorder=None):
         """The final stage's trace stores, replayed: the face index of every task's pencil names
         the same nodes (node_of_face), and every trace value of every cell, [dir][side][Qbar, Fbar.n]
         [v][face node], is written exactly once (Fbar.n by the Fbar tasks, Qbar and the Fbar.n of
@@ -281,7 +307,7 @@ class Config:
                 p, m = self.pencil(i, d, ord1)
                 assert self.node_of_face(d, self.face_of(lay, d, p), m) == i
         count = {}
-        for j, tl in self.slots(lay):
+        for j, tl in self.slots(lay, xorder):
             for x in tl:
                 if x is None:
                     continue

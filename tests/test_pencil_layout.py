@@ -3,7 +3,8 @@ CPU: for every configuration the library builds, the shared-memory indices of th
 of the tasks stay inside their regions, every slot is written once, the tasks read exactly what the
 nodes write and write exactly what they read, and the 8-byte accesses are aligned.  The constants
 are parsed from the kernel source, so a change there is checked before it runs on a GPU; so is
-the thread order of the 3D Euler N=5 nodes (kNodeOrderEuler3N5).  The double-buffered phase
+the thread orders of the 3D Euler N=5 nodes and x tasks (kNodeOrderEuler3N5,
+kXTaskOrderEuler3N5).  The double-buffered phase
 schedule of picard_pt and the trace stores of the final stage
 (predictor_final_pt) are replayed as well."""
 import importlib.util
@@ -111,6 +112,29 @@ def test_node_order_construction():
     assert cfg.count_nodes(lay, order) == 105
     assert order == kernel_node_order(cfg)
     assert cfg.node_order((1, 1, 38, 228)) is None  # y offsets with 8 nodes on some banks
+
+
+def x_task_order_table():
+    src = open(os.path.join(CSRC, "adg_kernels.cuh")).read()
+    body = re.search(r"kXTaskOrderEuler3N5\[(\d+)\] = \{([^}]*)\}", src)
+    vals = [int(v) for v in re.findall(r"\d+", body.group(2))]
+    assert len(vals) == int(body.group(1))
+    return vals
+
+
+def test_x_task_order_is_a_conflict_free_permutation():
+    # the kernel's thread order of the 3D Euler N=5 x tasks: every task once, the index
+    # arithmetic and the trace stores still exact, and with the node order the fewest wavefronts
+    # for 7 warps of nodes and 6 of tasks per direction
+    cfg = [c for c in M.CONFIGS if c.name == "Euler 3D N=5"][0]
+    lay = TABLE[(cfg.D, cfg.n, cfg.NC)]
+    xorder = x_task_order_table()
+    assert sorted(xorder) == list(range(cfg.dir_of.count(0) * cfg.NP))
+    assert xorder == cfg.x_task_order(lay)
+    assert cfg.check(lay, xorder) and cfg.check_final(lay, xorder)
+    order = kernel_node_order(cfg)
+    assert cfg.count(lay, order, xorder) == 426 == 2 * (cfg.NC * 7 + 3 * 6 * 6)
+    assert cfg.count(lay, None, xorder) == 486  # the x task order alone
 
 
 def test_a_wrong_stride_is_caught():
