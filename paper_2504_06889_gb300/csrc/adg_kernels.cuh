@@ -194,7 +194,8 @@ __device__ __forceinline__ float store_to_float(__half x) { return __half2float(
 // position along d; optionally the x pencils pencil-major (p SF0 + m).  A task's addresses are
 // compile-time offsets from one base.  The constants per configuration (pt_layout) come from a
 // bank-conflict model of these accesses; for 3D Euler at N = 5 it counts 504 shared-memory
-// wavefronts per cell and slice, against about 790 for the node-per-thread form.
+// wavefronts per cell and slice (426 with the thread orders of the nodes and x tasks below),
+// against about 790 for the node-per-thread form.
 
 // Layout constants of the pencil-task form per (d, n, flux components), from the bank model
 // tests/pencil_layout_model.py: xpm = 1 stores the x pencils pencil-major (read and

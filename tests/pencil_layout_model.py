@@ -17,6 +17,9 @@ and prints the best against the ideal (no conflicts).  pt_layout in adg_kernels.
 results for the configurations the library builds; others use xpm = 0, ord1 = 0, MS = NP + 2.
 check() replays the kernel's index arithmetic for a layout (bounds, coverage, alignment),
 check_final() the final stage's trace stores, check_schedule() the double-buffered phases.
+node_order() and x_task_order() build the thread orders of the nodes and of the x tasks that
+make the 3D Euler N=5 accesses conflict-free (kNodeOrderEuler3N5 and kXTaskOrderEuler3N5 in
+adg_kernels.cuh); count() takes them as optional arguments.
 
     python tests/pencil_layout_model.py
 """
@@ -414,6 +417,9 @@ if __name__ == "__main__":
     for cfg in CONFIGS:
         default = (0, 0, cfg.NP + 2, ((cfg.n - 1) * (cfg.NP + 2) + cfg.NP + 3) // 4 * 4)
         w, lay = cfg.search()
+        order = cfg.node_order(lay)
+        xorder = cfg.x_task_order(lay) if order is not None else None
+        ordered = f", {cfg.count(lay, order, xorder)} in thread order" if order is not None else ""
         print(f"{cfg.name:18s} D={cfg.D} n={cfg.n} combos={cfg.NC:2d}: best xpm={lay[0]} ord1={lay[1]} "
-              f"MS={lay[2]} CS={lay[3]}: {w} wavefronts (default {cfg.count(default)}, ideal {cfg.ideal():.0f})",
-              flush=True)
+              f"MS={lay[2]} CS={lay[3]}: {w} wavefronts{ordered} (default {cfg.count(default)}, "
+              f"ideal {cfg.ideal():.0f})", flush=True)
