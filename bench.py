@@ -377,6 +377,14 @@ def run_reference(args, wl):
     print(json.dumps(line), flush=True)
 
 
+def uses_volbuf(wl, mix, prec):
+    """Whether the predictor writes its volume term to the FP32 buffer that the corrector adds to
+    the FP64 state (the library's choice: Euler with FP32 predictor and corrector, FP64 storage,
+    no refinement); the predictor then does no FP64 update of the state."""
+    return (wl.pde == I.EULER and prec["predictor"] == "fp32" and prec["corrector"] == "fp32"
+            and prec.get("storage", "fp64") == "fp64" and mix not in MIX_REFINE)
+
+
 def roofline_of(wl, mix, prec, scheme, ms_pred, alu, peaks):
     """Roofline of the predictor launch (the dominant kernel) from algorithmic flops and the
     measured peaks: T_roof = F_tc / P_tc + F_fp32 / P_fp32 + F_fp64 / P_fp64 per cell (one term
@@ -387,21 +395,24 @@ def roofline_of(wl, mix, prec, scheme, ms_pred, alu, peaks):
     V = I.nvar(wl.pde, wl.dim)
     nz = NZ[(wl.pde, wl.dim)]
     f_all = predictor_flops_per_cell(wl.pde, wl.dim, wl.N, scheme=scheme)
-    f64 = 2 * V * NS  # the FP64 volume update of the state: one FMA per DOF
+    # the FP64 update of the state (one FMA per DOF), unless the corrector does it
+    upd = 0 if uses_volbuf(wl, mix, prec) else 2 * V * NS
+    f64 = upd
     f_tc = 0
     if prec["picard"] == "fp64" and prec["predictor"] == "fp64":
-        f64 = f_all
+        f64 = f_all + upd
     elif mix in MIX_REFINE:
         first, sweep, final = predictor_flop_parts(wl.pde, wl.dim, wl.N)
         k = min(MIX_REFINE[mix], n)
         nlo = n - k
         f_lo = (first + (nlo - 1) * sweep) if nlo > 0 else 0
-        f64 = f_all - f_lo
+        f64 = f_all - f_lo + upd
     elif prec["picard"] in ("bf16", "fp16", "fp8") and prec["predictor"] in ("fp32", "fp64"):
         f_tc = NS * nz * 2 * n * (1 + (n - 1) * n)  # contractions of the first and n - 1 further sweeps
         if prec["predictor"] == "fp64":  # the final stage in FP64
             first, sweep, final = predictor_flop_parts(wl.pde, wl.dim, wl.N)
-            f64 = final
+            f64 = final + upd
+    f_all += upd
     f32 = f_all - f_tc - f64
     p_tc = peaks["bf16_tflops"] * (2.0 if prec["picard"] == "fp8" else 1.0)
     t_roof = f_tc / (p_tc * 1e12) + f32 / (alu["fp32"] * 1e12) + f64 / (alu["fp64"] * 1e12)
@@ -473,8 +484,7 @@ def run_mixes(adg, wl, mixes, table, args, ws, local, alu, peaks, headline=None,
         r["roofline"] = roofline_of(wl, mix, prec, scheme, ms_pred / args.steps, alu, peaks)
         tb = {"fp64": 8, "fp32": 4, "bf16": 2}[prec["corrector"]]
         sb = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}[prec.get("storage", "fp64")]
-        volbuf = (wl.pde == I.EULER and prec["predictor"] == "fp32" and prec["corrector"] == "fp32"
-                  and prec.get("storage", "fp64") == "fp64" and mix not in MIX_REFINE)
+        volbuf = uses_volbuf(wl, mix, prec)
         bts = predictor_bytes_per_cell(wl.pde, wl.dim, wl.N, tb, sb, 4 if volbuf else None) * wl.ncells
         r["predictor_gbs"] = bts / (ms_pred / args.steps * 1e-3) / 1e9
         if mix == headline and e2e:
